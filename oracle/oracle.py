@@ -1,0 +1,241 @@
+"""ctypes front end of the FP64 C oracle (``evol_oracle.c``) -- TEST INFRASTRUCTURE ONLY.
+
+The oracle is the force step written out plainly in double precision: root cube, Morton keys,
+stable sort, recursive pre-order octree, node moments by direct summation, bisection for the
+smoothing/softening lengths, and a per-particle tree walk (Sect. 2-3 of the paper).  It shares
+no code with the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "evol_oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle into oracle/liboracle.so (gcc, OpenMP, no FMA contraction)."""
+    with _lock:
+        if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                   "-o", _SO + ".tmp", _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build_oracle()
+        L = C.CDLL(_SO)
+        d = C.c_double
+        for name in ("orc_W", "orc_dWdr", "orc_dWdh", "orc_dWdr_tc", "orc_phi", "orc_dphidr", "orc_dphideps"):
+            getattr(L, name).restype = d
+            getattr(L, name).argtypes = [d, d]
+        L.orc_eta_from_nnei.restype = d
+        L.orc_eta_from_nnei.argtypes = [d]
+        L.orc_hash_id.restype = C.c_uint64
+        L.orc_hash_id.argtypes = [C.c_uint64]
+        L.orc_build.restype = C.c_void_p
+        L.orc_build.argtypes = [C.c_int64, C.c_int64, _f32p, _f32p, _f32p, _f32p, C.c_int]
+        L.orc_free.argtypes = [C.c_void_p]
+        L.orc_nnodes.restype = C.c_int64
+        L.orc_nnodes.argtypes = [C.c_void_p]
+        L.orc_get_cube.argtypes = [C.c_void_p, _f64p, _f64p]
+        L.orc_get_keys.argtypes = [C.c_void_p, _u64p]
+        L.orc_get_perm.argtypes = [C.c_void_p, _i32p]
+        L.orc_get_nodes.argtypes = [C.c_void_p] + [_i32p] * 5
+        L.orc_get_moments.argtypes = [C.c_void_p] + [_f64p] * 8
+        L.orc_solve_lengths.restype = C.c_int
+        L.orc_solve_lengths.argtypes = [C.c_void_p, C.c_int, d, C.c_void_p, C.c_int64, C.c_void_p, C.c_int,
+                                        _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, C.c_void_p]
+        L.orc_forces.argtypes = ([C.c_void_p, d, d, d, d, d, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  _f64p, _f64p] + [_f64p] * 3 + [_f64p] * 3 + [_f64p] * 6 +
+                                 [C.c_void_p, C.c_int64] + [_f64p] * 5 + [C.c_void_p] * 7)
+        L.orc_eos.argtypes = [C.c_int64, d, _f64p, _f64p, _f64p, _f64p]
+        L.orc_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class _Kernels:
+    """The paper's kernel functions, vectorised over numpy arrays (Eqs. spline, softforce,
+    softphi, dphidh and the Thomas-Couchman gradient)."""
+
+    def _vec(self, name, r, L):
+        f = getattr(lib(), name)
+        r, L = np.broadcast_arrays(np.asarray(r, np.float64), np.asarray(L, np.float64))
+        out = np.empty(r.shape)
+        for idx in np.ndindex(r.shape):
+            out[idx] = f(float(r[idx]), float(L[idx]))
+        return out if out.shape else float(out)
+
+    def W(self, r, h): return self._vec("orc_W", r, h)
+    def dWdr(self, r, h): return self._vec("orc_dWdr", r, h)
+    def dWdh(self, r, h): return self._vec("orc_dWdh", r, h)
+    def dWdr_tc(self, r, h): return self._vec("orc_dWdr_tc", r, h)
+    def phi(self, r, e): return self._vec("orc_phi", r, e)
+    def dphidr(self, r, e): return self._vec("orc_dphidr", r, e)
+    def dphideps(self, r, e): return self._vec("orc_dphideps", r, e)
+
+
+kernels = _Kernels()
+
+
+def eta_from_nnei(n_nei: float) -> float:
+    return lib().orc_eta_from_nnei(float(n_nei))
+
+
+def hash_id(i: int) -> int:
+    return int(lib().orc_hash_id(int(i)))
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class OracleTree:
+    """Oracle tree over one particle set (root cube, keys, permutation, pre-order nodes,
+    node moments)."""
+
+    def __init__(self, x, y, z, m, n_gas: int, leaf: int):
+        self.n = int(len(x))
+        self.n_gas = int(n_gas)
+        self._keep = [_c(a, np.float32) for a in (x, y, z, m)]
+        self.ptr = lib().orc_build(self.n, self.n_gas, *self._keep, int(leaf))
+        if not self.ptr:
+            raise ValueError("oracle tree build failed (bad arguments or out of memory)")
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            lib().orc_free(self.ptr)
+            self.ptr = None
+
+    @property
+    def nnodes(self) -> int:
+        return int(lib().orc_nnodes(self.ptr))
+
+    def cube(self):
+        c = np.zeros(3)
+        s = np.zeros(1)
+        lib().orc_get_cube(self.ptr, c, s)
+        return c, float(s[0])
+
+    def keys(self):
+        k = np.empty(self.n, np.uint64)
+        lib().orc_get_keys(self.ptr, k)
+        return k
+
+    def perm(self):
+        p = np.empty(self.n, np.int32)
+        lib().orc_get_perm(self.ptr, p)
+        return p
+
+    def nodes(self):
+        nn = self.nnodes
+        a = [np.empty(nn, np.int32) for _ in range(5)]
+        lib().orc_get_nodes(self.ptr, *a)
+        return dict(zip(("begin", "end", "level", "next", "nchild"), a))
+
+    def moments(self):
+        nn = self.nnodes
+        M, com, Q = np.empty(nn), np.empty((nn, 3)), np.empty((nn, 6))
+        delta, bmin, bmax, cgeo, l = np.empty(nn), np.empty((nn, 3)), np.empty((nn, 3)), np.empty((nn, 3)), np.empty(nn)
+        lib().orc_get_moments(self.ptr, M, com, Q, delta, bmin, bmax, cgeo, l)
+        return dict(M=M, com=com, Q=Q, delta=delta, bmin=bmin, bmax=bmax, cgeo=cgeo, l=l)
+
+    def _period(self, params):
+        lo = _c(getattr(params, "periodic_lo", (0, 0, 0)), np.float64)
+        hi = _c(getattr(params, "periodic_hi", (1, 1, 1)), np.float64)
+        return int(getattr(params, "periodic_mask", 0)), lo, hi
+
+    def solve_lengths(self, mode: int, n_nei: float, guess=None, idx=None, params=None):
+        """mode 0: gas h -> (h, n, rho, Omega*, zeta); mode 1: eps -> (eps, n, Upsilon, X)."""
+        n = self.n
+        outs = [np.zeros(n) for _ in range(5)]
+        pm, lo, hi = self._period(params)
+        g = _c(guess, np.float32) if guess is not None else None
+        ix = _c(idx, np.int64) if idx is not None else None
+        rc = lib().orc_solve_lengths(self.ptr, int(mode), float(n_nei),
+                                     ix.ctypes.data if ix is not None else None,
+                                     int(len(ix)) if ix is not None else 0,
+                                     g.ctypes.data if g is not None else None,
+                                     pm, lo, hi, *outs[:4], outs[4].ctypes.data)
+        if rc != 0:
+            raise RuntimeError(f"oracle length solve failed (code {rc})")
+        return outs
+
+    def forces(self, params, state: dict, idx=None, use_tc=None):
+        n = self.n
+        z = np.zeros(n)
+        g = lambda k: _c(state.get(k, z), np.float64)
+        pm, lo, hi = self._period(params)
+        ix = _c(idx, np.int64) if idx is not None else None
+        out = [np.zeros(n) for _ in range(5)]
+        hashes = [np.zeros(n, np.uint64) for _ in range(3)]
+        counts = [np.zeros(n, np.int64) for _ in range(3)]
+        margin = np.full(n, np.inf)
+        tc = params.use_tc_gradient if use_tc is None else use_tc
+        lib().orc_forces(self.ptr, float(params.theta), float(params.G), float(params.gamma),
+                         float(params.alpha), float(params.beta), int(params.gravity), int(params.sph),
+                         int(params.adaptive_softening), int(tc), pm, lo, hi,
+                         g("vx"), g("vy"), g("vz"), g("eps"), g("ups"), g("X"),
+                         g("h"), g("rho"), g("P"), g("c"), g("omega"), g("zeta"),
+                         ix.ctypes.data if ix is not None else None, int(len(ix)) if ix is not None else 0,
+                         *out, *[a.ctypes.data for a in hashes], *[a.ctypes.data for a in counts],
+                         margin.ctypes.data)
+        res = dict(zip(("ax", "ay", "az", "pot", "dudt"), out))
+        res.update(zip(("hfar", "hnear", "hsph"), hashes))
+        res.update(zip(("nfar", "npp", "nsph"), counts))
+        res["margin"] = margin
+        return res
+
+
+def force_step(w, params=None, idx=None, use_tc=None, tree=None, fixed_lengths=None):
+    """The whole force step on workload `w` in FP64: tree, eps solve (adaptive softening, all
+    particles), h solve (gas), equation of state, and the force pass for the particles in idx
+    (all if None).  Returns a dict of original-order float64 arrays."""
+    p = params or w.params
+    t = tree or OracleTree(w.x, w.y, w.z, w.m, w.n_gas, p.leaf_size)
+    n = w.n
+    st = {"vx": w.vx.astype(np.float64), "vy": w.vy.astype(np.float64), "vz": w.vz.astype(np.float64)}
+    res = {}
+    if fixed_lengths is not None:
+        st.update(fixed_lengths)
+    else:
+        if p.gravity:
+            if p.adaptive_softening:
+                eps, neps, ups, X, _ = t.solve_lengths(1, p.n_nei_grav, guess=w.eps, params=p)
+            else:
+                eps, neps, ups, X = w.eps.astype(np.float64), np.zeros(n), np.ones(n), np.zeros(n)
+            st.update(eps=eps, ups=ups, X=X)
+            res.update(eps=eps, n_eps=neps, ups=ups, X=X)
+        if p.sph and w.n_gas > 0:
+            gidx = np.arange(w.n_gas, dtype=np.int64)
+            h, nh, rho, om, zeta = t.solve_lengths(0, p.n_nei_sph, guess=w.h, idx=gidx, params=p)
+            P, c = np.zeros(n), np.zeros(n)
+            lib().orc_eos(n, float(p.gamma), _c(rho, np.float64), _c(w.u.astype(np.float64), np.float64), P, c)
+            P[w.n_gas:] = 0
+            c[w.n_gas:] = 0
+            st.update(h=h, rho=rho, omega=om, zeta=zeta, P=P, c=c)
+            res.update(h=h, n_h=nh, rho=rho, omega=om, zeta=zeta, P=P, c=c)
+    f = t.forces(p, st, idx=idx, use_tc=use_tc)
+    res.update(f)
+    res["tree"] = t
+    res["state"] = st
+    return res
