@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark of the tree + SPH force step on GB300 (one JSON line on stdout).
+
+Default workload: the mixed-species system -- 2^21 Hernquist dark-matter particles plus 2^20
+gas particles in a rho ~ 1/r sphere (gas fraction 0.1, u = 0.05, theta = 0.5, 50 neighbours),
+one full force step (tree build + eps solve + h solve + gravity/SPH walk) per step, synthetic
+seeded data.  `value` = particles per second of the whole step with inputs resident in HBM;
+`e2e` = the same through evol_step_host with host buffers (copies inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c1|c2|c3|c4|c5] [--precision plain|mixed]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload on its own GPU
+(the single-system step does not shard); the reported value is the sum over ranks divided by
+the slowest rank's time.  --impl reference times the FP64 CPU oracle on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Algorithmic FP32 operations per interaction of the force walk, counted from the source
+# (FFMA = 2, FADD/FMUL = 1, MUFU = 1): far node monopole + quadrupole + potential; gravity
+# particle pair (symmetrised softened force, potential, adaptive correction); SPH pair
+# (pressure + grad-h factors, Monaghan viscosity, du/dt).
+FLOPS_FAR = 54
+FLOPS_PP = 60
+FLOPS_SPH = 85
+FP32_LANES_PER_SM = 128
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def make_workload(name: str):
+    from paper_0912_1786_gb300 import workloads as W
+    if name == "c1":
+        return W.evrard_sphere(4096, seed=1), "evrard_sphere_4096"
+    if name == "c2":
+        return W.plummer(1 << 20, seed=2, params=W.Params(theta=0.6, sph=0, n_nei_grav=32.0, leaf_size=8)), \
+            "plummer_2^20_theta0.6_gravity_only"
+    if name == "c3":
+        return W.hernquist_gas(n_dm=1 << 21, n_gas=1 << 20, seed=3), "hernquist_2^21_dm+2^20_gas"
+    if name == "c4":
+        return W.shock_tube(seed=4), "shock_tube_1046250_periodic_yz"
+    if name == "c5":
+        return W.ensemble(64, seed=5), "ensemble_64_spheres"
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd[1:1] = ["-i", self.gpu_id]
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, flags in rows for k, v in enumerate(flags) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_uuid(torch, dev):
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+def oracle_sample(w, budget_s=25.0, seed=7):
+    """Bounded timing of the FP64 oracle on workload w: a full tree build, the eps and h solves
+    on seeded samples of particles and the force walk on a seeded sample, each scaled to its
+    per-particle rate.  Returns (particles/s, cores, description)."""
+    import oracle
+    from paper_0912_1786_gb300 import workloads as W
+    p = w.params
+    lib = oracle.lib()
+    cores = int(lib.orc_num_threads())
+    t0 = time.perf_counter()
+    tree = oracle.OracleTree(w.x, w.y, w.z, w.m, w.n_gas, p.leaf_size)
+    t_build = time.perf_counter() - t0
+    n, ng = w.n, w.n_gas
+    rng = np.random.default_rng(seed)
+    per = 0.0
+    desc = [f"tree build of all {n} particles {t_build:.2f}s"]
+    s_e = min(n, 60000)
+    s_h = min(ng, 30000)
+    if p.gravity and p.adaptive_softening:
+        idx = np.sort(rng.choice(n, s_e, replace=False))
+        t0 = time.perf_counter()
+        tree.solve_lengths(1, p.n_nei_grav, guess=w.eps, idx=idx, params=p)
+        te = time.perf_counter() - t0
+        per += te / s_e * n
+        desc.append(f"eps solve {s_e} sampled ({te:.2f}s)")
+    if p.sph and ng:
+        idx = np.sort(rng.choice(ng, s_h, replace=False))
+        t0 = time.perf_counter()
+        tree.solve_lengths(0, p.n_nei_sph, guess=w.h, idx=idx, params=p)
+        th = time.perf_counter() - t0
+        per += th / s_h * ng
+        desc.append(f"h solve {s_h} sampled ({th:.2f}s)")
+    # neighbour lengths for the force sample come from the oracle's own solve of every particle
+    # (setup, not timed)
+    st = {}
+    if p.gravity and p.adaptive_softening:
+        eps, _, ups, X, _ = tree.solve_lengths(1, p.n_nei_grav, guess=w.eps, params=p)
+        st.update(eps=eps, ups=ups, X=X)
+    elif p.gravity:
+        st.update(eps=w.eps.astype(np.float64), ups=np.ones(n), X=np.zeros(n))
+    if p.sph and ng:
+        h, _, rho, om, zeta = tree.solve_lengths(0, p.n_nei_sph, guess=w.h, idx=np.arange(ng), params=p)
+        P, c = np.zeros(n), np.zeros(n)
+        lib.orc_eos(n, float(p.gamma), np.ascontiguousarray(rho), np.ascontiguousarray(w.u, np.float64), P, c)
+        P[ng:] = 0
+        c[ng:] = 0
+        st.update(h=h, rho=rho, omega=om, zeta=zeta, P=P, c=c)
+    st.update(vx=w.vx.astype(np.float64), vy=w.vy.astype(np.float64), vz=w.vz.astype(np.float64))
+    s_f = min(n, 2000)
+    idx = np.sort(rng.choice(n, s_f, replace=False))
+    t0 = time.perf_counter()
+    tree.forces(p, st, idx=idx)
+    tf = time.perf_counter() - t0
+    # grow the force sample while the budget allows
+    if tf < budget_s / 4 and s_f < n:
+        s_f2 = int(min(n, s_f * max(2.0, budget_s / 4 / max(tf, 1e-3))))
+        idx = np.sort(rng.choice(n, s_f2, replace=False))
+        t0 = time.perf_counter()
+        tree.forces(p, st, idx=idx)
+        tf = time.perf_counter() - t0
+        s_f = s_f2
+    per += tf / s_f * n
+    desc.append(f"force walk {s_f} sampled ({tf:.2f}s)")
+    total = t_build + per
+    return n / total, cores, "; ".join(desc) + f"; scaled to {n} particles: {total:.1f}s per step"
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle, as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w, wname = make_workload(args.workload)
+    vals = []
+    desc = ""
+    cores = 1
+    for k in range(args.warmup + args.steps):
+        v, cores, desc = oracle_sample(w, budget_s=args.ref_budget, seed=100 + k)
+        if k >= args.warmup:
+            vals.append(v)
+    v = statistics.mean(vals)
+    line = {"metric": "force-step particles/s (tree gravity+SPH)", "value": v, "unit": "particles/s",
+            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "n": w.n, "n_gas": w.n_gas, "theta": w.params.theta,
+                       "n_nei": w.params.n_nei_sph},
+            "cpu_baseline": {"value": v, "unit": "particles/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "vs_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--precision", default="plain", choices=["plain", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_0912_1786_gb300 import build, evol as E
+    from paper_0912_1786_gb300.device import DeviceSet
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    build.build()
+
+    w, wname = make_workload(args.workload)
+    prec = E.EVOL_FP32_MIXED if args.precision == "mixed" else E.EVOL_FP32_PLAIN
+    ds = DeviceSet(w, device=str(dev), precision=prec)
+    stream = torch.cuda.current_stream(dev)
+    ctx = E.evol_create(w.n, stream.cuda_stream)
+
+    def one_step():
+        ds.reset_lengths()
+        E.evol_step(ctx, ds.particles, ds.params, ds.outputs)
+
+    for _ in range(args.warmup):
+        one_step()
+    E.evol_sync(ctx)
+
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    sampler.start()
+    time.sleep(0.5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    walk_ms, phase = [], []
+    t_start.record(stream)
+    for _ in range(args.steps):
+        one_step()
+        rc = E.evol_sync(ctx)                     # per-step status; also lets the phase events be read
+        tm = E.evol_get_timings(ctx)
+        walk_ms.append(tm[3])
+        phase.append(tm)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end)
+    clocks = sampler.stop()
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    diag = E.evol_get_diagnostics(ctx)
+    n_total = w.n * world
+    value = n_total * args.steps / (ms_max / 1e3)
+
+    # ---- e2e through the host-buffer entry point (pinned host memory) ----
+    e2e = None
+    if not args.no_e2e:
+        host_in = {}
+        for k, a in w.arrays().items():
+            t = torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
+            host_in[k] = t
+        host_out = {k: torch.zeros(w.n_gas if k in ("rho", "P", "c", "omega", "zeta", "dudt") else w.n,
+                                   dtype=torch.float32).pin_memory()
+                    for k in ("ax", "ay", "az", "pot", "rho", "P", "c", "omega", "zeta", "dudt")}
+        hp = E.make_particles(w.n, w.n_gas, host_in)
+        ho = E.make_outputs(host_out)
+        h2d = sum(w.n_gas * 4 if k in ("u", "h") else w.n * 4 for k in host_in)
+        d2h = sum(int(t.numel()) * 4 for t in host_out.values()) + (w.n_gas + w.n) * 4
+        ke = max(1, min(args.steps, 5))
+        h0, e0 = host_in["h"].clone(), host_in["eps"].clone()
+        E.evol_step_host(ctx, hp, ds.params, ho)           # warm (captures the host-path graph)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            host_in["h"].copy_(h0)
+            host_in["eps"].copy_(e0)
+            E.evol_step_host(ctx, hp, ds.params, ho)
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": n_total * ke / te, "unit": "particles/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ke}
+
+    # ---- roofline of the dominant kernel (the force walk) ----
+    far, pp, sph = diag[12], diag[13], diag[14]
+    flops = far * FLOPS_FAR + pp * FLOPS_PP + sph * FLOPS_SPH
+    walk_s = statistics.mean(walk_ms) / 1e3
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak_max = sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    achieved = flops / walk_s / 1e12
+    clk = clocks["sm_mhz"] if clocks else None
+    roofline = {"bound": "alu", "kernel": "k_walk (gravity + SPH force walk)", "achieved": achieved,
+                "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max, "traffic": None,
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                "frac_at_sampled_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12)) if clk else None,
+                "walk_ms": walk_s * 1e3,
+                "interactions_per_step": {"far": far, "pp": pp, "sph": sph},
+                "flops_per_interaction": {"far": FLOPS_FAR, "pp": FLOPS_PP, "sph": FLOPS_SPH}}
+    ph = np.mean(np.array(phase), axis=0).tolist()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            v, cores, desc = oracle_sample(w)
+            cpu = {"value": v, "unit": "particles/s", "cores": cores, "kind": "oracle", "sample": desc}
+        except Exception as ex:     # the baseline is reported, never required
+            cpu = {"value": None, "unit": "particles/s", "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    E.evol_destroy(ctx)
+    if rank == 0:
+        line = {"metric": "force-step particles/s (tree gravity+SPH)", "value": value, "unit": "particles/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "precision": args.precision, "data": "synthetic",
+                "config": {"workload": wname, "n": w.n, "n_gas": w.n_gas, "theta": w.params.theta,
+                           "n_nei": w.params.n_nei_sph, "leaf_size": w.params.leaf_size,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "working set > L2 (inputs 40 B/particle x 3.1M + tree), no flush"},
+                "phase_ms": {"build": ph[0], "eps_solve": ph[1], "h_solve": ph[2], "walk": ph[3], "total": ph[4]},
+                "interactions_per_s": {"far": far / walk_s, "pp": pp / walk_s, "sph": sph / walk_s},
+                "status_last_step": rc,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": None}
+        line["gpu_launches"] = launches_per_step(w) * args.steps
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def launches_per_step(w):
+    """Kernels of ours per evol_step: bbox 2, keys 1, 8 radix passes x (hist + 3 scan + scatter),
+    permute, lcp, count, 3 scan, fill, link, moments, eps solve, h solve, pack, node-lengths 2,
+    walk, unpermute, diagnostics 2."""
+    p = w.params
+    k = 2 + 1 + 8 * 5 + 1 + 1 + 1 + 3 + 1 + 1 + 1
+    k += 1 if (p.gravity and p.adaptive_softening) else 0
+    k += 1 if (p.sph and w.n_gas) else 0
+    k += 1 + 2 + 1 + 1 + 2
+    return k
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * evol.h -- C ABI of the GB300 (sm_103a) tree + SPH force step of EvoL
+ * (Merlin et al., arXiv:0912.1786, "EvoL: the new Padova T-SPH parallel code").
+ *
+ * One call of evol_step computes, for N particles of which the first n_gas are SPH gas:
+ *   - the Barnes-Hut oct-tree of cubes with monopole + quadrupole node moments (Sect. 2.2),
+ *   - adaptive softening lengths eps_i = eta n_i^{-1/3} with the correction terms Upsilon, X
+ *     (Sect. 2.1, Eqs. rho0, etan, zeta; App. B),
+ *   - smoothing lengths h_i = eta n_i^{-1/3} from the gas number density, the mass density
+ *     rho_i and the variable-mass grad-h terms Omega*_i, zeta_i (Sect. 3, Eqs. hn, nsum,
+ *     densitySPH, drhodr),
+ *   - the gravitational acceleration by a tree walk with the opening criterion
+ *     r > l/theta + delta (Eq. opcrit), symmetrised softened pair forces and the adaptive
+ *     softening correction (Eq. dLgravdr; App. B),
+ *   - the SPH pressure + artificial-viscosity acceleration and du/dt (Eqs. motionvarmass1,
+ *     thermalvarmass1, mu_visc; App. B), with the Thomas-Couchman kernel gradient (Sect. 3
+ *     footnote) and nearest-image periodic axes (Sect. 4.3).
+ *
+ * Conventions common to every entry point:
+ *   - All particle and output pointers are DEVICE pointers (cudaMalloc'd or torch tensors),
+ *     float32, structure-of-arrays, in the caller's order, owned by the caller.  The one
+ *     exception is evol_step_host, which takes host pointers.
+ *   - Gas particles are the first n_gas entries of every per-particle array.
+ *   - Calls are asynchronous on the stream given to evol_create.  A call returns EVOL_OK or
+ *     an argument / launch error at once; errors found on the device (list overflow,
+ *     no root for a length, NaN) are recorded in the context and returned by evol_sync.
+ *   - A context is not thread-safe.  There is no host (CPU) fallback: a context can only be
+ *     created on a CUDA device.
+ */
+#ifndef EVOL_H
+#define EVOL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define EVOL_OK          0
+#define EVOL_EINVAL     -1   /* bad argument (NULL pointer, n out of range, bad parameter) */
+#define EVOL_ENOMEM     -2   /* n exceeds the context capacity, or device allocation failed */
+#define EVOL_ECUDA      -3   /* a CUDA runtime call failed */
+#define EVOL_EOVERFLOW  -4   /* a fixed-capacity device list (nodes, neighbour candidates) overflowed */
+#define EVOL_ENOCONV    -5   /* a smoothing/softening length has no root or did not converge */
+#define EVOL_ETIMEOUT   -6   /* a bounded device wait gave up */
+#define EVOL_ENAN       -7   /* a non-finite value was produced */
+#define EVOL_ESTATE     -8   /* call order violated (e.g. forces before density) */
+
+/* ---- precision forms -------------------------------------------------------------- */
+#define EVOL_FP32_PLAIN  0   /* FP32 moments and FP32 accumulation of per-particle sums */
+#define EVOL_FP32_MIXED  1   /* FP64 multipole/centre-of-mass accumulation and FP64 totals of
+                                blocked FP32 partial sums; the walk arithmetic stays FP32 */
+
+typedef struct evol_ctx evol_ctx;   /* opaque; owns every device scratch buffer */
+
+/* Particles (Sect. 1: each particle carries mass, position, velocity, plus for gas the
+ * internal energy; Sect. 3.2: gas carries both eps and h).  Length n (u: n_gas). */
+typedef struct {
+    int64_t n;             /* number of particles, 0 <= n <= the context capacity */
+    int64_t n_gas;         /* the first n_gas particles are gas, 0 <= n_gas <= n */
+    const float *x, *y, *z;
+    const float *vx, *vy, *vz;
+    const float *m;        /* masses, > 0 */
+    const float *u;        /* specific internal energy of gas particles (length n_gas) */
+    float *h;              /* in: starting guess (> 0) for gas; out: solved smoothing length */
+    float *eps;            /* in: softening (fixed) or starting guess (adaptive); out: solved */
+} evol_particles;
+
+/* Parameters (Sect. 5 lists the paper's choices: eta, alpha, beta, gamma, theta). */
+typedef struct {
+    float theta;               /* opening angle of Eq. opcrit; 0 opens every node (direct sum) */
+    float n_nei_sph;           /* target neighbour number N_nei = 4/3 pi (2 eta)^3 for h */
+    float n_nei_grav;          /* target neighbour number for the adaptive eps */
+    float gamma;               /* adiabatic index of P = (gamma - 1) rho u */
+    float alpha, beta;         /* Monaghan viscosity parameters (Eq. mu_visc) */
+    float G;                   /* gravitational constant */
+    int gravity;               /* 1: compute gravity */
+    int sph;                   /* 1: compute SPH density and forces for the gas */
+    int adaptive_softening;    /* 1: eps solved with correction terms; 0: eps fixed as given */
+    int use_tc_gradient;       /* 1: Thomas-Couchman gradient in the SPH force and du/dt */
+    int periodic_mask;         /* bit a set: axis a periodic (SPH only; gravity must be off) */
+    float periodic_lo[3], periodic_hi[3];
+    int precision;             /* EVOL_FP32_PLAIN or EVOL_FP32_MIXED */
+    int leaf_size;             /* a cube is split while it holds more than leaf_size particles
+                                  (1..64; 0 = default 8).  Changes cost, not the definition. */
+    int group_size;            /* particles per warp group in the walks: 0 or 32 */
+} evol_params;
+
+/* Outputs, caller order.  Any pointer may be NULL (not written). */
+typedef struct {
+    float *ax, *ay, *az;       /* length n: total acceleration (gravity + SPH) */
+    float *pot;                /* length n: Phi_i = G sum_j m_j phi(r_ij, eps_i), self term included */
+    float *rho;                /* length n_gas: mass density (Eq. densitySPH) */
+    float *P, *c;              /* length n_gas: pressure and sound speed */
+    float *omega, *zeta;       /* length n_gas: Omega*_i and zeta_i (Eq. drhodr) */
+    float *dudt;               /* length n_gas: du/dt (Eq. thermalvarmass1) */
+    float *ups, *X;            /* length n: Upsilon_i and X_i (adaptive softening) */
+} evol_outputs;
+
+/* Create a context for up to max_n particles on the current CUDA device; every device
+ * buffer is allocated here (about 1 KB per particle of capacity).  stream: a cudaStream_t
+ * (NULL = the legacy default stream).  Returns EVOL_EINVAL, EVOL_ENOMEM or EVOL_ECUDA on
+ * failure, with *ctx set to NULL. */
+int evol_create(evol_ctx **ctx, int64_t max_n, void *stream);
+int evol_destroy(evol_ctx *ctx);
+
+/* Tree build (Sect. 2.2): root cube, 63-bit Morton keys (21 bits per axis), stable radix sort,
+ * pre-order node list (a cube is split into its non-empty octants while it holds more than
+ * leaf_size particles, down to level 21), node moments (mass, centre of mass, traceless
+ * quadrupole about it, delta = |geometric centre - centre of mass|, particle bounding box). */
+int evol_build_tree(evol_ctx *ctx, const evol_particles *p, const evol_params *prm);
+
+/* SPH density (Sect. 3, Eqs. hn, nsum, densitySPH, drhodr; Sect. 3.1 gather view): solves
+ * h_i^3 n_i(h_i) = eta^3 for every gas particle by Newton iteration with a bisection bracket
+ * on a cached candidate list, then rho, Omega*, zeta, P and c.  Builds the tree first if
+ * evol_build_tree was not called for these particles.  Writes p->h and the density outputs. */
+int evol_sph_density(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outputs *out);
+
+/* Gravity (Sect. 2.1-2.2; App. B): with adaptive softening solves eps for every particle and
+ * Upsilon, X; then the tree walk.  OVERWRITES ax, ay, az and pot. */
+int evol_gravity(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outputs *out);
+
+/* SPH forces (Eqs. motionvarmass1, thermalvarmass1; App. B): pairs with
+ * r_ij < 2 max(h_i, h_j).  ADDS the SPH acceleration to ax, ay, az and writes dudt.
+ * Requires evol_sph_density on the same particles first (else EVOL_ESTATE). */
+int evol_sph_forces(evol_ctx *ctx, const evol_particles *p, const evol_params *prm, evol_outputs *out);
+
+/* The whole force step: build + eps solve + h solve + one fused walk for gravity and SPH
+ * forces (Sect. 3.1: "the gravitational force is evaluated together with the construction
+ * of the neighbour list").  Recorded once into a CUDA graph per (pointers, n, parameters)
+ * and replayed afterwards; no host synchronisation inside. */
+int evol_step(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outputs *out);
+
+/* evol_step on HOST buffers: copies the inputs host -> device into context-owned buffers,
+ * runs the step and copies every non-NULL output (and h, eps) back, then synchronises.
+ * The particle and output pointers of this call are host pointers (pinned memory is
+ * fastest).  Returns the step status (as evol_sync). */
+int evol_step_host(evol_ctx *ctx, evol_particles *p_host, const evol_params *prm, evol_outputs *out_host);
+
+/* Wait for the context stream and return the first device-side error recorded since the
+ * previous evol_sync (then clear it), or EVOL_OK. */
+int evol_sync(evol_ctx *ctx);
+
+/* FP64 totals of the last step (valid after evol_sync): [0..2] sum m v, [3..5] sum m a,
+ * [6] kinetic energy, [7] thermal energy sum m u, [8] potential energy 1/2 sum m Phi,
+ * [9] sum m (v.a + du/dt) over gas (SPH energy balance), [10] sum m, [11] node count,
+ * [12] far-node interactions, [13] particle-particle pairs, [14] SPH pairs,
+ * [15] length-solve iterations (sum over particles). */
+int evol_get_diagnostics(evol_ctx *ctx, double out[16]);
+
+/* Debug copies of internal state (valid after evol_sync), into host memory of cap bytes.
+ * Returns the number of ELEMENTS available (whatever cap), or a negative status.
+ *   EVOL_DBG_KEYS   uint64[n]   Morton keys in sorted order
+ *   EVOL_DBG_PERM   int32[n]    sorted position -> caller index
+ *   EVOL_DBG_NODES  int32[5*nn] begin[nn], end[nn], level[nn], next[nn], nchild[nn] (pre-order)
+ *   EVOL_DBG_CUBE   double[4]   root corner x, y, z and side
+ *   EVOL_DBG_MOMENTS float[20*nn] per node: M, com xyz, Q xx yy zz xy xz yz, delta,
+ *                              bbox min xyz, bbox max xyz, 2 epsmax, 2 hmax (-1: no gas),
+ *                              (l/theta + delta)^2
+ *   EVOL_DBG_HASHES uint64[3*n] caller order: far-node set, near-leaf set, SPH neighbour set
+ *   EVOL_DBG_COUNTS int32[3*n]  caller order: far nodes, particle pairs, SPH pairs
+ * Hashes and per-particle counts are written only while check mode is on. */
+#define EVOL_DBG_KEYS     1
+#define EVOL_DBG_PERM     2
+#define EVOL_DBG_NODES    3
+#define EVOL_DBG_CUBE     4
+#define EVOL_DBG_MOMENTS  5
+#define EVOL_DBG_HASHES   6
+#define EVOL_DBG_COUNTS   7
+int64_t evol_get_debug(evol_ctx *ctx, int what, void *host_dst, int64_t cap_bytes);
+
+/* Check mode (0/1): the walks also record, per particle, order-independent 64-bit hashes
+ * (splitmix64 of the id, summed) of the accepted-node set, the opened-leaf set and the SPH
+ * neighbour set, and their sizes.  Slower; off by default. */
+int evol_set_check_mode(evol_ctx *ctx, int on);
+
+/* Event timings (ms) of the phases of the last evol_step: [0] build, [1] eps solve,
+ * [2] h solve, [3] force walk, [4] total. Valid after evol_sync. */
+int evol_get_timings(evol_ctx *ctx, float out[5]);
+
+const char *evol_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EVOL_H */

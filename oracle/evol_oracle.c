@@ -640,6 +640,7 @@ typedef struct {
     uint64_t hfar, hnear, hsph;
     int64_t nfar, npp, nsph;
     double margin;      /* smallest relative distance of any decision from its threshold */
+    double aabs, duabs; /* sums of the magnitudes of the individual contributions to a and du/dt */
 } orc_result;
 
 static void orc_margin(orc_result *res, double v, double thr)
@@ -670,6 +671,7 @@ static void orc_pair(const orc_tree *t, const orc_params *pr, const orc_state *s
                                      (mj / mi) * st->X[j] / st->ups[j] * orc_dWdr(r, ej)) / r;
             }
             for (int a = 0; a < 3; ++a) res->a[a] += f * rv[a];
+            res->aabs += fabs(f) * r;
         }
     }
     if (pr->sph && i < t->n_gas && j < t->n_gas) {
@@ -706,9 +708,11 @@ static void orc_pair(const orc_tree *t, const orc_params *pr, const orc_state *s
                     res->a[a] += s * rv[a];
                     res->ahyd[a] += s * rv[a];
                 }
+                res->aabs += fabs(s) * r;
                 /* Reading: Eq. thermalvarmass with (v_i - v_j) so that compression heats;
                  * viscous heating 1/2 Pi v_ij . gradbar W >= 0. */
                 res->dudt += mj * (Pi_ * fi * gi + 0.5 * Pi_visc * gbar) * vr / r;
+                res->duabs += fabs(mj * (Pi_ * fi * gi + 0.5 * Pi_visc * gbar) * vr / r);
             }
         }
     }
@@ -728,9 +732,13 @@ static void orc_far(const orc_tree *t, const orc_params *pr, int64_t id, const d
                     q[3] * d[0] + q[1] * d[1] + q[5] * d[2],
                     q[4] * d[0] + q[5] * d[1] + q[2] * d[2]};
     double dQd = d[0] * Qd[0] + d[1] * Qd[1] + d[2] * Qd[2];
-    double M = t->M[id];
-    for (int a = 0; a < 3; ++a)
-        res->a[a] += pr->G * (-M * d[a] * di3 + Qd[a] * di5 - 2.5 * dQd * d[a] * di7);
+    double M = t->M[id], mag = 0;
+    for (int a = 0; a < 3; ++a) {
+        double c = pr->G * (-M * d[a] * di3 + Qd[a] * di5 - 2.5 * dQd * d[a] * di7);
+        res->a[a] += c;
+        mag += c * c;
+    }
+    res->aabs += sqrt(mag);
     res->pot += pr->G * (-M * di - 0.5 * dQd * di5);
 }
 
@@ -809,7 +817,8 @@ void orc_forces(orc_tree *t, double theta, double G, double gamma, double alpha,
                 const int64_t *idx, int64_t nidx,
                 double *ax, double *ay, double *az, double *pot, double *dudt,
                 uint64_t *hfar, uint64_t *hnear, uint64_t *hsph,
-                int64_t *nfar, int64_t *npp, int64_t *nsph, double *margin)
+                int64_t *nfar, int64_t *npp, int64_t *nsph, double *margin,
+                double *aabs, double *duabs)
 {
     orc_params pr = {theta, G, gamma, alpha, beta, gravity, sph, adaptive, use_tc};
     orc_state st = {vx, vy, vz, eps, ups, X, h, rho, P, c, om, zeta};
@@ -833,6 +842,8 @@ void orc_forces(orc_tree *t, double theta, double G, double gamma, double alpha,
         if (npp) npp[i] = res.npp;
         if (nsph) nsph[i] = res.nsph;
         if (margin) margin[i] = res.margin;
+        if (aabs) aabs[i] = res.aabs;
+        if (duabs) duabs[i] = res.duabs;
     }
 }
 

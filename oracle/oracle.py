@@ -66,7 +66,7 @@ def lib():
                                         _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, C.c_void_p]
         L.orc_forces.argtypes = ([C.c_void_p, d, d, d, d, d, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                   _f64p, _f64p] + [_f64p] * 3 + [_f64p] * 3 + [_f64p] * 6 +
-                                 [C.c_void_p, C.c_int64] + [_f64p] * 5 + [C.c_void_p] * 7)
+                                 [C.c_void_p, C.c_int64] + [_f64p] * 5 + [C.c_void_p] * 9)
         L.orc_eos.argtypes = [C.c_int64, d, _f64p, _f64p, _f64p, _f64p]
         L.orc_num_threads.restype = C.c_int
         _lib = L
@@ -190,6 +190,7 @@ class OracleTree:
         hashes = [np.zeros(n, np.uint64) for _ in range(3)]
         counts = [np.zeros(n, np.int64) for _ in range(3)]
         margin = np.full(n, np.inf)
+        aabs, duabs = np.zeros(n), np.zeros(n)
         tc = params.use_tc_gradient if use_tc is None else use_tc
         lib().orc_forces(self.ptr, float(params.theta), float(params.G), float(params.gamma),
                          float(params.alpha), float(params.beta), int(params.gravity), int(params.sph),
@@ -198,11 +199,13 @@ class OracleTree:
                          g("h"), g("rho"), g("P"), g("c"), g("omega"), g("zeta"),
                          ix.ctypes.data if ix is not None else None, int(len(ix)) if ix is not None else 0,
                          *out, *[a.ctypes.data for a in hashes], *[a.ctypes.data for a in counts],
-                         margin.ctypes.data)
+                         margin.ctypes.data, aabs.ctypes.data, duabs.ctypes.data)
         res = dict(zip(("ax", "ay", "az", "pot", "dudt"), out))
         res.update(zip(("hfar", "hnear", "hsph"), hashes))
         res.update(zip(("nfar", "npp", "nsph"), counts))
         res["margin"] = margin
+        res["aabs"] = aabs
+        res["duabs"] = duabs
         return res
 
 

@@ -1,0 +1,512 @@
+// C ABI of the force-step library (include/evol.h): context management, argument checks,
+// phase sequencing, CUDA-graph capture of the whole step, host-buffer step, diagnostics and
+// debug copies.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "evol_internal.cuh"
+
+int evol_launch_pack(evol_ctx *c, const evol_particles *p, const evol_params *prm, int do_grav, int do_sph);
+int evol_launch_unpermute_ex(evol_ctx *c, const evol_particles *p, const evol_outputs *o, int what, int add_acc);
+int evol_lengths_warps_per_block();
+
+namespace {
+
+constexpr int64_t CAND_CAP = 4096;       // candidate leaves per warp in the length solve
+constexpr int64_t NODE_FACTOR = 3;       // node capacity = 3 * particles + 64
+
+template <typename T>
+int dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, count * sizeof(T)) == cudaSuccess ? EVOL_OK : EVOL_ENOMEM;
+}
+
+void free_all(evol_ctx *c)
+{
+    evol_dev &d = c->d;
+    void *ptrs[] = {d.pos, d.vel, d.grav, d.hydro, d.snd, d.vah, d.orig, d.len_h, d.len_eps, d.nh, d.omega,
+                    d.zeta, d.rho, d.neps, d.ups, d.X, d.acc, d.dudt, d.keys_a, d.keys_b, d.vals_a, d.vals_b,
+                    d.hist, d.lcp, d.cnt, d.base, d.scan_part, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
+                    d.nnch, d.narrive, d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nM64, d.nC64, d.nQ64, d.nBmin,
+                    d.nBmax, d.nI, d.cand_leaf, d.cand_mask, d.diag_part, d.diag, d.counters, d.err, d.nnodes,
+                    d.cube, d.fcube, d.bbox_part, d.hash3, d.cnt3, c->stage};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (int k = 0; k < 6; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+}
+
+int check_args(evol_ctx *c, const evol_particles *p, const evol_params *prm)
+{
+    if (!c || !p || !prm) return EVOL_EINVAL;
+    if (p->n < 0 || p->n_gas < 0 || p->n_gas > p->n) return EVOL_EINVAL;
+    if (p->n > c->cap) return EVOL_ENOMEM;
+    if (p->n == 0) return EVOL_OK;
+    if (!p->x || !p->y || !p->z || !p->m) return EVOL_EINVAL;
+    if (!(prm->theta >= 0.f)) return EVOL_EINVAL;
+    if (prm->leaf_size < 0 || prm->leaf_size > 64) return EVOL_EINVAL;
+    if (prm->group_size != 0 && prm->group_size != 32) return EVOL_EINVAL;
+    if (prm->precision != EVOL_FP32_PLAIN && prm->precision != EVOL_FP32_MIXED) return EVOL_EINVAL;
+    if (prm->gravity) {
+        if (!p->eps) return EVOL_EINVAL;
+        if (prm->periodic_mask) return EVOL_EINVAL;          // no Ewald summation: periodic gravity unsupported
+        if (prm->adaptive_softening && !(prm->n_nei_grav > 0.f)) return EVOL_EINVAL;
+    }
+    if (prm->sph && p->n_gas > 0) {
+        if (!p->u || !p->h) return EVOL_EINVAL;
+        if (!(prm->n_nei_sph > 0.f) || !(prm->gamma > 1.f)) return EVOL_EINVAL;
+    }
+    if (prm->periodic_mask & ~7) return EVOL_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (((prm->periodic_mask >> a) & 1) && !(prm->periodic_hi[a] > prm->periodic_lo[a])) return EVOL_EINVAL;
+    return EVOL_OK;
+}
+
+// FNV-1a over the bytes that define a captured step
+uint64_t fnv(uint64_t h, const void *data, size_t len)
+{
+    const unsigned char *b = (const unsigned char *)data;
+    for (size_t i = 0; i < len; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+void reset_counters(evol_ctx *c)
+{
+    cudaMemsetAsync(c->d.counters, 0, 8 * sizeof(unsigned long long), c->stream);
+}
+
+int ensure_tree(evol_ctx *c, const evol_particles *p, const evol_params *prm)
+{
+    if (c->built_n == p->n && c->built_ngas == p->n_gas && c->built_x == (const void *)p->x) return EVOL_OK;
+    int rc = evol_launch_build(c, p, prm);
+    if (rc) return rc;
+    c->built_n = p->n;
+    c->built_ngas = p->n_gas;
+    c->built_x = p->x;
+    c->density_done = 0;
+    c->eps_done = 0;
+    return EVOL_OK;
+}
+
+int set_err(evol_ctx *c, int rc)
+{
+    if (rc && !c->host_err) c->host_err = rc;
+    return rc;
+}
+
+// The sequence of one full step (captured into the graph).
+int record_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out)
+{
+    int rc;
+    const bool grav = prm->gravity != 0, sph = prm->sph != 0 && p->n_gas > 0;
+    cudaEventRecord(c->ev[0], c->stream);
+    reset_counters(c);
+    if ((rc = evol_launch_build(c, p, prm))) return rc;
+    c->built_n = p->n;
+    c->built_ngas = p->n_gas;
+    c->built_x = p->x;
+    cudaEventRecord(c->ev[1], c->stream);
+    if (grav && prm->adaptive_softening)
+        if ((rc = evol_launch_lengths(c, p, prm, 1))) return rc;
+    cudaEventRecord(c->ev[2], c->stream);
+    if (sph)
+        if ((rc = evol_launch_lengths(c, p, prm, 0))) return rc;
+    if ((rc = evol_launch_pack(c, p, prm, grav, sph))) return rc;
+    if ((rc = evol_launch_node_lengths(c, prm, 0))) return rc;
+    cudaEventRecord(c->ev[3], c->stream);
+    if ((rc = evol_launch_walk(c, p, prm, grav, sph))) return rc;
+    cudaEventRecord(c->ev[4], c->stream);
+    int what = EVOL_UNPERM_ACC | (grav ? EVOL_UNPERM_EPSOUT : 0) |
+               (sph ? (EVOL_UNPERM_LENGTHS | EVOL_UNPERM_DENSITY | EVOL_UNPERM_DUDT) : 0);
+    if ((rc = evol_launch_unpermute(c, p, out, what))) return rc;
+    if ((rc = evol_launch_diagnostics(c, p, prm))) return rc;
+    cudaEventRecord(c->ev[5], c->stream);
+    c->density_done = sph;
+    c->eps_done = grav;
+    return EVOL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *evol_strerror(int code)
+{
+    switch (code) {
+    case EVOL_OK: return "ok";
+    case EVOL_EINVAL: return "invalid argument";
+    case EVOL_ENOMEM: return "capacity exceeded or device allocation failed";
+    case EVOL_ECUDA: return "CUDA runtime error";
+    case EVOL_EOVERFLOW: return "fixed-capacity device list overflowed";
+    case EVOL_ENOCONV: return "smoothing/softening length has no root or did not converge";
+    case EVOL_ETIMEOUT: return "bounded device wait gave up";
+    case EVOL_ENAN: return "non-finite value produced";
+    case EVOL_ESTATE: return "call order violated";
+    default: return "unknown status";
+    }
+}
+
+int evol_create(evol_ctx **out, int64_t max_n, void *stream)
+{
+    if (!out) return EVOL_EINVAL;
+    *out = nullptr;
+    if (max_n < 1 || max_n > (int64_t)0x3fffffff) return EVOL_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return EVOL_ECUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return EVOL_ECUDA;
+    evol_ctx *c = (evol_ctx *)calloc(1, sizeof(evol_ctx));
+    if (!c) return EVOL_ENOMEM;
+    c->cap = max_n;
+    c->node_cap = NODE_FACTOR * max_n + 64;
+    c->device = dev;
+    c->num_sms = prop.multiProcessorCount;
+    c->stream = (cudaStream_t)stream;
+    c->sort_blocks = (max_n + 4095) / 4096;
+    c->bbox_blocks = c->num_sms * 2;
+    c->diag_blocks = c->num_sms * 2;
+    c->cand_cap = CAND_CAP;
+    c->cand_slots = (int64_t)c->num_sms * 8 * evol_lengths_warps_per_block();
+    int64_t n = max_n, nn = c->node_cap;
+    int64_t scan_parts = (256 * c->sort_blocks > n + 1 ? 256 * c->sort_blocks : n + 1) / 4096 + 2;
+    evol_dev &d = c->d;
+    int rc = 0;
+    rc |= dalloc(&d.pos, n); rc |= dalloc(&d.vel, n); rc |= dalloc(&d.grav, n); rc |= dalloc(&d.hydro, n);
+    rc |= dalloc(&d.snd, n); rc |= dalloc(&d.vah, n); rc |= dalloc(&d.orig, n);
+    rc |= dalloc(&d.len_h, n); rc |= dalloc(&d.len_eps, n); rc |= dalloc(&d.nh, n); rc |= dalloc(&d.omega, n);
+    rc |= dalloc(&d.zeta, n); rc |= dalloc(&d.rho, n); rc |= dalloc(&d.neps, n); rc |= dalloc(&d.ups, n);
+    rc |= dalloc(&d.X, n); rc |= dalloc(&d.acc, n); rc |= dalloc(&d.dudt, n);
+    rc |= dalloc(&d.keys_a, n); rc |= dalloc(&d.keys_b, n); rc |= dalloc(&d.vals_a, n); rc |= dalloc(&d.vals_b, n);
+    rc |= dalloc(&d.hist, 256 * c->sort_blocks + 1);
+    rc |= dalloc(&d.lcp, n); rc |= dalloc(&d.cnt, n + 1); rc |= dalloc(&d.base, n + 1);
+    rc |= dalloc(&d.scan_part, scan_parts);
+    rc |= dalloc(&d.nbeg, nn); rc |= dalloc(&d.nend, nn); rc |= dalloc(&d.nlev, nn); rc |= dalloc(&d.nnext, nn);
+    rc |= dalloc(&d.nparent, nn); rc |= dalloc(&d.nnch, nn); rc |= dalloc(&d.narrive, nn);
+    rc |= dalloc(&d.nA, nn); rc |= dalloc(&d.nB, nn); rc |= dalloc(&d.nC, nn); rc |= dalloc(&d.nQ0, nn);
+    rc |= dalloc(&d.nQ1, nn); rc |= dalloc(&d.nM64, nn); rc |= dalloc(&d.nC64, 3 * nn); rc |= dalloc(&d.nQ64, 6 * nn);
+    rc |= dalloc(&d.nBmin, nn); rc |= dalloc(&d.nBmax, nn); rc |= dalloc(&d.nI, nn);
+    rc |= dalloc(&d.cand_leaf, 2 * c->cand_slots * c->cand_cap);
+    rc |= dalloc(&d.cand_mask, c->cand_slots * c->cand_cap);
+    rc |= dalloc(&d.diag_part, 16 * c->diag_blocks); rc |= dalloc(&d.diag, 16);
+    rc |= dalloc(&d.counters, 8); rc |= dalloc(&d.err, 1); rc |= dalloc(&d.nnodes, 1);
+    rc |= dalloc(&d.cube, 4); rc |= dalloc(&d.fcube, 4); rc |= dalloc(&d.bbox_part, 6 * c->bbox_blocks);
+    rc |= dalloc(&d.hash3, 3 * n); rc |= dalloc(&d.cnt3, 3 * n);
+    rc |= dalloc(&c->stage, 24 * n);
+    for (int k = 0; k < 6 && !rc; ++k)
+        if (cudaEventCreate(&c->ev[k]) != cudaSuccess) rc = EVOL_ECUDA;
+    if (!rc) {
+        cudaMemset(d.err, 0, sizeof(int));
+        cudaMemset(d.counters, 0, 8 * sizeof(unsigned long long));
+        cudaMemset(d.nnodes, 0, sizeof(int32_t));
+        cudaMemset(d.diag, 0, 16 * sizeof(double));
+        if (cudaDeviceSynchronize() != cudaSuccess) rc = EVOL_ECUDA;
+    }
+    if (rc) {
+        cudaGetLastError();
+        free_all(c);
+        free(c);
+        return rc < 0 ? (rc == EVOL_ECUDA ? EVOL_ECUDA : EVOL_ENOMEM) : EVOL_ENOMEM;
+    }
+    c->built_n = -1;
+    *out = c;
+    return EVOL_OK;
+}
+
+int evol_destroy(evol_ctx *c)
+{
+    if (!c) return EVOL_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    free(c);
+    return EVOL_OK;
+}
+
+int evol_set_check_mode(evol_ctx *c, int on)
+{
+    if (!c) return EVOL_EINVAL;
+    c->check_mode = on ? 1 : 0;
+    return EVOL_OK;
+}
+
+int evol_build_tree(evol_ctx *c, const evol_particles *p, const evol_params *prm)
+{
+    int rc = check_args(c, p, prm);
+    if (rc || p->n == 0) return rc;
+    c->built_n = -1;
+    reset_counters(c);
+    return set_err(c, ensure_tree(c, p, prm));
+}
+
+int evol_sph_density(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out)
+{
+    int rc = check_args(c, p, prm);
+    if (rc || p->n == 0) return rc;
+    if (!prm->sph) return EVOL_EINVAL;
+    if ((rc = ensure_tree(c, p, prm))) return set_err(c, rc);
+    if (p->n_gas == 0) return EVOL_OK;
+    if ((rc = evol_launch_lengths(c, p, prm, 0))) return set_err(c, rc);
+    if ((rc = evol_launch_pack(c, p, prm, c->eps_done, 1))) return set_err(c, rc);
+    if ((rc = evol_launch_unpermute(c, p, out, EVOL_UNPERM_LENGTHS | EVOL_UNPERM_DENSITY))) return set_err(c, rc);
+    c->density_done = 1;
+    return EVOL_OK;
+}
+
+int evol_gravity(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out)
+{
+    int rc = check_args(c, p, prm);
+    if (rc || p->n == 0) return rc;
+    if (!prm->gravity) return EVOL_EINVAL;
+    if ((rc = ensure_tree(c, p, prm))) return set_err(c, rc);
+    if (prm->adaptive_softening)
+        if ((rc = evol_launch_lengths(c, p, prm, 1))) return set_err(c, rc);
+    c->eps_done = 1;
+    if ((rc = evol_launch_pack(c, p, prm, 1, c->density_done))) return set_err(c, rc);
+    if ((rc = evol_launch_node_lengths(c, prm, 0))) return set_err(c, rc);
+    if ((rc = evol_launch_walk(c, p, prm, 1, 0))) return set_err(c, rc);
+    if ((rc = evol_launch_unpermute(c, p, out, EVOL_UNPERM_ACC | EVOL_UNPERM_EPSOUT))) return set_err(c, rc);
+    return EVOL_OK;
+}
+
+int evol_sph_forces(evol_ctx *c, const evol_particles *p, const evol_params *prm, evol_outputs *out)
+{
+    int rc = check_args(c, p, prm);
+    if (rc || p->n == 0) return rc;
+    if (!prm->sph) return EVOL_EINVAL;
+    if (c->built_n != p->n || c->built_x != (const void *)p->x || !c->density_done) return EVOL_ESTATE;
+    if (p->n_gas == 0) return EVOL_OK;
+    if ((rc = evol_launch_node_lengths(c, prm, 0))) return set_err(c, rc);
+    if ((rc = evol_launch_walk(c, p, prm, 0, 1))) return set_err(c, rc);
+    if ((rc = evol_launch_unpermute_ex(c, p, out, EVOL_UNPERM_ACC | EVOL_UNPERM_DUDT, 1))) return set_err(c, rc);
+    return EVOL_OK;
+}
+
+int evol_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out)
+{
+    int rc = check_args(c, p, prm);
+    if (rc || p->n == 0) return rc;
+    evol_outputs zero{};
+    if (!out) out = &zero;
+    uint64_t sig = 1469598103934665603ull;
+    sig = fnv(sig, p, sizeof *p);
+    sig = fnv(sig, prm, sizeof *prm);
+    sig = fnv(sig, out, sizeof *out);
+    sig = fnv(sig, &c->check_mode, sizeof c->check_mode);
+    sig = fnv(sig, &c->stream, sizeof c->stream);
+    if (!c->graph_exec || sig != c->graph_sig) {
+        if (c->graph_exec) {
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+        }
+        cudaStream_t cap_stream = c->stream;
+        bool own = false;
+        if (!cap_stream) {          // the legacy stream cannot be captured: record on a private stream
+            if (cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+                return set_err(c, EVOL_ECUDA);
+            own = true;
+        }
+        cudaStream_t saved = c->stream;
+        c->stream = cap_stream;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            c->stream = saved;
+            if (own) cudaStreamDestroy(cap_stream);
+            return set_err(c, EVOL_ECUDA);
+        }
+        int rrc = record_step(c, p, prm, out);
+        cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
+        c->stream = saved;
+        if (own) cudaStreamDestroy(cap_stream);
+        if (rrc || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return set_err(c, rrc ? rrc : EVOL_ECUDA);
+        }
+        e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c->graph_exec = nullptr;
+            cudaGetLastError();
+            return set_err(c, EVOL_ECUDA);
+        }
+        c->graph_sig = sig;
+    }
+    if (cudaGraphLaunch(c->graph_exec, c->stream) != cudaSuccess) return set_err(c, EVOL_ECUDA);
+    c->built_n = p->n;
+    c->built_ngas = p->n_gas;
+    c->built_x = p->x;
+    c->density_done = prm->sph && p->n_gas > 0;
+    c->eps_done = prm->gravity;
+    return EVOL_OK;
+}
+
+int evol_step_host(evol_ctx *c, evol_particles *ph, const evol_params *prm, evol_outputs *oh)
+{
+    int rc = check_args(c, ph, prm);
+    if (rc || ph->n == 0) return rc;
+    int64_t n = ph->n, ng = ph->n_gas;
+    float *st = c->stage;
+    float *in[10];
+    for (int k = 0; k < 10; ++k) in[k] = st + (int64_t)k * c->cap;
+    const float *src[10] = {ph->x, ph->y, ph->z, ph->vx, ph->vy, ph->vz, ph->m, ph->u, ph->h, ph->eps};
+    int64_t len[10] = {n, n, n, n, n, n, n, ng, ng, n};
+    for (int k = 0; k < 10; ++k)
+        if (src[k] && len[k] > 0)
+            if (cudaMemcpyAsync(in[k], src[k], len[k] * sizeof(float), cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess)
+                return set_err(c, EVOL_ECUDA);
+    evol_particles pd = *ph;
+    pd.x = in[0]; pd.y = in[1]; pd.z = in[2];
+    pd.vx = ph->vx ? in[3] : nullptr; pd.vy = ph->vy ? in[4] : nullptr; pd.vz = ph->vz ? in[5] : nullptr;
+    pd.m = in[6];
+    pd.u = ph->u ? in[7] : nullptr;
+    pd.h = ph->h ? in[8] : nullptr;
+    pd.eps = ph->eps ? in[9] : nullptr;
+    evol_outputs zero{};
+    if (!oh) oh = &zero;
+    float *outp[12];
+    for (int k = 0; k < 12; ++k) outp[k] = st + (int64_t)(10 + k) * c->cap;
+    float *hdst[12] = {oh->ax, oh->ay, oh->az, oh->pot, oh->rho, oh->P, oh->c, oh->omega, oh->zeta, oh->dudt,
+                       oh->ups, oh->X};
+    int64_t olen[12] = {n, n, n, n, ng, ng, ng, ng, ng, ng, n, n};
+    evol_outputs od{};
+    float **odp[12] = {&od.ax, &od.ay, &od.az, &od.pot, &od.rho, &od.P, &od.c, &od.omega, &od.zeta, &od.dudt,
+                       &od.ups, &od.X};
+    for (int k = 0; k < 12; ++k) *odp[k] = hdst[k] ? outp[k] : nullptr;
+    if ((rc = evol_step(c, &pd, prm, &od))) return rc;
+    for (int k = 0; k < 12; ++k)
+        if (hdst[k] && olen[k] > 0)
+            cudaMemcpyAsync(hdst[k], outp[k], olen[k] * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (ph->h && ng > 0) cudaMemcpyAsync(ph->h, in[8], ng * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (ph->eps) cudaMemcpyAsync(ph->eps, in[9], n * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    return evol_sync(c);
+}
+
+int evol_sync(evol_ctx *c)
+{
+    if (!c) return EVOL_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return EVOL_ECUDA;
+    }
+    int e = 0;
+    if (cudaMemcpy(&e, c->d.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return EVOL_ECUDA;
+    if (e) cudaMemset(c->d.err, 0, sizeof(int));
+    int h = c->host_err;
+    c->host_err = 0;
+    return h ? h : e;
+}
+
+int evol_get_diagnostics(evol_ctx *c, double out[16])
+{
+    if (!c || !out) return EVOL_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return EVOL_ECUDA;
+    return cudaMemcpy(out, c->d.diag, 16 * sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess ? EVOL_OK
+                                                                                                 : EVOL_ECUDA;
+}
+
+int evol_get_timings(evol_ctx *c, float out[5])
+{
+    if (!c || !out) return EVOL_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return EVOL_ECUDA;
+    const int pairs[5][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {0, 5}};
+    for (int k = 0; k < 5; ++k) {
+        float ms = -1.f;
+        if (cudaEventElapsedTime(&ms, c->ev[pairs[k][0]], c->ev[pairs[k][1]]) != cudaSuccess) {
+            cudaGetLastError();
+            ms = -1.f;
+        }
+        out[k] = ms;
+    }
+    return EVOL_OK;
+}
+
+int64_t evol_get_debug(evol_ctx *c, int what, void *dst, int64_t cap)
+{
+    if (!c) return EVOL_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return EVOL_ECUDA;
+    int64_t n = c->built_n > 0 ? c->built_n : 0;
+    int32_t nn = 0;
+    cudaMemcpy(&nn, c->d.nnodes, sizeof nn, cudaMemcpyDeviceToHost);
+    auto copy = [&](const void *src, int64_t bytes) -> bool {
+        if (!dst || cap < bytes) return false;
+        return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
+    };
+    switch (what) {
+    case EVOL_DBG_KEYS:
+        copy(c->d.keys_a, n * 8);
+        return n;
+    case EVOL_DBG_PERM:
+        copy(c->d.orig, n * 4);
+        return n;
+    case EVOL_DBG_CUBE:
+        copy(c->d.cube, 32);
+        return 4;
+    case EVOL_DBG_NODES: {
+        if (dst && cap >= (int64_t)nn * 20) {
+            int32_t *o = (int32_t *)dst;
+            cudaMemcpy(o, c->d.nbeg, nn * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(o + nn, c->d.nend, nn * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(o + 2 * nn, c->d.nlev, nn * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(o + 3 * nn, c->d.nnext, nn * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(o + 4 * nn, c->d.nnch, nn * 4, cudaMemcpyDeviceToHost);
+        }
+        return (int64_t)nn * 5;
+    }
+    case EVOL_DBG_MOMENTS: {
+        if (dst && cap >= (int64_t)nn * 80) {
+            std::vector<float4> A(nn), B(nn), C(nn), Q0(nn), Q1(nn), bl(nn), bh(nn);
+            cudaMemcpy(A.data(), c->d.nA, nn * 16, cudaMemcpyDeviceToHost);
+            cudaMemcpy(B.data(), c->d.nB, nn * 16, cudaMemcpyDeviceToHost);
+            cudaMemcpy(C.data(), c->d.nC, nn * 16, cudaMemcpyDeviceToHost);
+            cudaMemcpy(Q0.data(), c->d.nQ0, nn * 16, cudaMemcpyDeviceToHost);
+            cudaMemcpy(Q1.data(), c->d.nQ1, nn * 16, cudaMemcpyDeviceToHost);
+            cudaMemcpy(bl.data(), c->d.nBmin, nn * 16, cudaMemcpyDeviceToHost);
+            cudaMemcpy(bh.data(), c->d.nBmax, nn * 16, cudaMemcpyDeviceToHost);
+            float *o = (float *)dst;
+            for (int32_t i = 0; i < nn; ++i) {
+                float v[20] = {Q0[i].w, A[i].x,  A[i].y,  A[i].z,  Q0[i].x, Q0[i].y, Q0[i].z,
+                               Q1[i].x, Q1[i].y, Q1[i].z, Q1[i].w, bl[i].x, bl[i].y, bl[i].z,
+                               bh[i].x, bh[i].y, bh[i].z, C[i].w,  B[i].w,  A[i].w};
+                memcpy(o + 20 * (int64_t)i, v, sizeof v);
+            }
+        }
+        return (int64_t)nn * 20;
+    }
+    case EVOL_DBG_HASHES:
+    case EVOL_DBG_COUNTS: {
+        int64_t esz = what == EVOL_DBG_HASHES ? 8 : 4;
+        if (dst && cap >= 3 * n * esz) {
+            std::vector<int32_t> orig(n);
+            cudaMemcpy(orig.data(), c->d.orig, n * 4, cudaMemcpyDeviceToHost);
+            if (what == EVOL_DBG_HASHES) {
+                std::vector<unsigned long long> hs(3 * n);
+                cudaMemcpy(hs.data(), c->d.hash3, 3 * n * 8, cudaMemcpyDeviceToHost);
+                unsigned long long *o = (unsigned long long *)dst;
+                for (int64_t s = 0; s < n; ++s)
+                    for (int k = 0; k < 3; ++k) o[3 * (int64_t)orig[s] + k] = hs[3 * s + k];
+            } else {
+                std::vector<int32_t> hs(3 * n);
+                cudaMemcpy(hs.data(), c->d.cnt3, 3 * n * 4, cudaMemcpyDeviceToHost);
+                int32_t *o = (int32_t *)dst;
+                for (int64_t s = 0; s < n; ++s)
+                    for (int k = 0; k < 3; ++k) o[3 * (int64_t)orig[s] + k] = hs[3 * s + k];
+            }
+        }
+        return 3 * n;
+    }
+    default:
+        return EVOL_EINVAL;
+    }
+}
+
+}  // extern "C"

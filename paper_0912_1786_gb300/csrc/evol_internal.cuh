@@ -1,0 +1,185 @@
+// Internal declarations of the GB300 force-step library: context layout, FP32 kernel
+// functions and small device helpers.  Not part of the C ABI (see include/evol.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/evol.h"
+
+#define EVOL_MAXLEVEL 21          // 21 bits per axis, 63-bit Morton keys
+#define EVOL_WARP 32
+#define EVOL_PI_F 3.14159265358979f
+
+// ---- device error word: first error wins ------------------------------------------------
+__device__ __forceinline__ void evol_flag(int *err, int code)
+{
+    atomicCAS(err, 0, code);
+}
+
+// ---- sorted per-particle state packed for the walks --------------------------------------
+// pos  : x, y, z, m
+// grav : 1/eps, X/Upsilon, h (0 for non-gas), zeta/Omega* (0 for non-gas)
+// hydro: vx, vy, vz, P/rho^2
+// snd  : c, rho, 1/h (0 for non-gas), unused
+struct evol_dev {
+    // particles, sorted order
+    float4 *pos, *vel, *grav, *hydro, *snd;
+    float *vah;              // v . a_hyd per particle (energy balance diagnostic)
+    int32_t *orig;           // sorted -> caller index
+    float *len_h, *len_eps;  // solved lengths, sorted
+    float *nh, *omega, *zeta, *rho;     // gas outputs (sorted; n entries, non-gas unused)
+    float *neps, *ups, *X;              // softening outputs (sorted)
+    float4 *acc;             // ax, ay, az, pot (sorted)
+    float *dudt;             // sorted
+    // sort
+    uint64_t *keys_a, *keys_b;
+    int32_t *vals_a, *vals_b;
+    uint32_t *hist;          // 256 * nblocks
+    // tree construction
+    uint8_t *lcp;            // d_i: common octal digits of keys i-1, i
+    int32_t *cnt, *base;     // nodes beginning at each sorted position, and its exclusive scan
+    int32_t *scan_part;      // scan block partials
+    // nodes (pre-order)
+    int32_t *nbeg, *nend, *nlev, *nnext, *nparent, *nnch, *narrive;
+    float4 *nA;              // com x, y, z, ropen^2 with ropen = l/theta + delta (Eq. opcrit)
+    float4 *nB;              // bbox centre x, y, z, 2 hmax (-1: no gas; 0 until lengths are known)
+    float4 *nC;              // bbox half widths x, y, z, 2 epsmax
+    float4 *nQ0;             // Qxx, Qyy, Qzz, M
+    float4 *nQ1;             // Qxy, Qxz, Qyz, delta
+    double *nM64, *nC64, *nQ64;         // FP64 moments (mixed precision): M, com[3], Q[6]
+    float4 *nBmin, *nBmax;              // particle bounding box (w of nBmin: node holds gas)
+    int4 *nI;                           // walk copy: level | leaf << 8, next, begin, end
+    // length solve scratch: per resident warp candidate lists
+    int32_t *cand_leaf;
+    uint32_t *cand_mask;
+    // reductions / counters
+    double *diag_part;       // per-block partials of diagnostics
+    double *diag;            // 16
+    unsigned long long *counters;   // [0] far [1] pp [2] sph [3] iters [4] work queue [5] q2 [6] q3
+    int *err;
+    int32_t *nnodes;         // device node count
+    double *cube;            // corner x, y, z, side
+    float *fcube;            // corner x, y, z (float), side (float)
+    float *bbox_part;        // per-block min/max partials
+    // check mode
+    unsigned long long *hash3;   // 3 per particle (sorted)
+    int32_t *cnt3;               // 3 per particle (sorted)
+};
+
+struct evol_ctx {
+    int64_t cap;             // particle capacity
+    int64_t node_cap;
+    int device, num_sms;
+    cudaStream_t stream;
+    evol_dev d;
+    int64_t sort_blocks;
+    int64_t bbox_blocks;
+    int64_t cand_slots, cand_cap;
+    int64_t diag_blocks;
+    int host_err;            // first error seen on the host side
+    int check_mode;
+    // state of the last build / density
+    int64_t built_n, built_ngas;
+    const void *built_x;
+    int density_done, eps_done;
+    // graph cache for evol_step
+    cudaGraphExec_t graph_exec;
+    uint64_t graph_sig;
+    // events for phase timings
+    cudaEvent_t ev[6];
+    // host staging for evol_step_host (device buffers)
+    float *stage;            // 10 * cap floats (inputs) + 14 * cap floats (outputs)
+};
+
+// ---- host-side launch helpers (defined in evol_api.cu / tree.cu / walks) ------------------
+int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *prm);
+int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params *prm, int mode);
+int evol_launch_walk(evol_ctx *c, const evol_particles *p, const evol_params *prm, int do_grav, int do_sph);
+int evol_launch_node_lengths(evol_ctx *c, const evol_params *prm, int mode_mask);
+int evol_launch_unpermute(evol_ctx *c, const evol_particles *p, const evol_outputs *o, int what);
+int evol_launch_diagnostics(evol_ctx *c, const evol_particles *p, const evol_params *prm);
+
+#define EVOL_UNPERM_LENGTHS 1
+#define EVOL_UNPERM_DENSITY 2
+#define EVOL_UNPERM_ACC     4
+#define EVOL_UNPERM_DUDT    8
+#define EVOL_UNPERM_EPSOUT  16
+
+static inline int evol_cuda_ok(cudaError_t e) { return e == cudaSuccess ? EVOL_OK : EVOL_ECUDA; }
+
+// ---- FP32 kernel functions (Eqs. spline, softforce, softphi, dphidh; TC gradient) -------
+// M4 spline w(u) = 1/4 (2-u)_+^3 - (1-u)_+^3 and its derivative dw/du; W = w / (pi h^3).
+__device__ __forceinline__ void evol_w_dw(float u, float &w, float &dw)
+{
+    float a = fmaxf(2.f - u, 0.f), b = fmaxf(1.f - u, 0.f);
+    float a2 = a * a, b2 = b * b;
+    w = 0.25f * a2 * a - b2 * b;
+    dw = -0.75f * a2 + 3.f * b2;
+}
+
+// Softened force kernel divided by r, times eps^3:  eps^3 phi'(r, eps) / r, for u < 2.
+__device__ __forceinline__ float evol_gsoft_over_r(float u)
+{
+    float u2 = u * u;
+    if (u < 1.f) return 4.f / 3.f - 1.2f * u2 + 0.5f * u2 * u;
+    float u3 = u2 * u;
+    return 8.f / 3.f - 3.f * u + 1.2f * u2 - u3 / 6.f - 1.f / (15.f * u3);
+}
+
+// Softened potential times eps: eps phi(r, eps), for u < 2.
+__device__ __forceinline__ float evol_phisoft(float u)
+{
+    float u2 = u * u;
+    if (u < 1.f) return (2.f / 3.f) * u2 - 0.3f * u2 * u2 + 0.1f * u2 * u2 * u - 1.4f;
+    return (4.f / 3.f) * u2 - u2 * u + 0.3f * u2 * u2 - u2 * u2 * u / 30.f - 1.6f + 1.f / (15.f * u);
+}
+
+// dphi/deps times eps^2, for u < 2 (Eq. dphidh with the -3/2 u^4 sign of the outer branch).
+__device__ __forceinline__ float evol_dphideps(float u)
+{
+    float u2 = u * u;
+    if (u < 1.f) return -2.f * u2 + 1.5f * u2 * u2 - 0.6f * u2 * u2 * u + 1.4f;
+    if (u < 2.f) return -4.f * u2 + 4.f * u2 * u - 1.5f * u2 * u2 + 0.2f * u2 * u2 * u + 1.6f;
+    return 0.f;
+}
+
+// (dW/dr) / r times pi h^5, exact spline derivative: w'(u)/u.
+__device__ __forceinline__ float evol_dw_over_u(float u)
+{
+    if (u < 1.f) return -3.f + 2.25f * u;
+    float a = fmaxf(2.f - u, 0.f);
+    return -0.75f * a * a / u;
+}
+
+// Thomas-Couchman gradient: (dW/dr)/r times pi h^5 (Sect. 3 footnote).
+__device__ __forceinline__ float evol_tc_over_u(float u)
+{
+    if (u < 2.f / 3.f) return -1.f / u;
+    if (u < 1.f) return -0.75f * (4.f - 3.f * u);
+    float a = fmaxf(2.f - u, 0.f);
+    return -0.75f * a * a / u;
+}
+
+// splitmix64 finaliser (Steele, Lea & Flood 2014), for interaction-set hashes in check mode.
+__device__ __forceinline__ unsigned long long evol_mix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float evol_wrap(float d, float len, int periodic)
+{
+    return periodic ? d - len * rintf(d / len) : d;
+}
+
+// Walk parameters passed by value to kernels.
+struct evol_kparams {
+    float theta, G, gamma, alpha, beta;
+    float eta_h, eta_e;
+    int gravity, sph, adaptive, use_tc, periodic_mask, mixed;
+    float plen[3];
+    int n, n_gas, leaf;
+};

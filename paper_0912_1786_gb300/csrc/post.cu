@@ -1,0 +1,169 @@
+// Per-particle packing between the phases (equation of state, walk operands), un-permutation
+// of results into the caller's order, and FP64 global diagnostics.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "evol_internal.cuh"
+
+namespace {
+
+// Walk operands.  grav = (1/eps, X/Upsilon, h, zeta/Omega*), hydro = (v, P/rho^2),
+// snd = (c, rho, 1/h, P).  Ideal gas (App. B): P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u).
+__global__ void k_pack(int n, int n_gas, int do_grav, int adaptive, int do_sph, float gamma, evol_dev d)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (do_grav) {
+        float e = d.len_eps[s];
+        g.x = 1.f / e;
+        if (adaptive) {
+            g.y = d.X[s] / d.ups[s];
+        } else {
+            d.ups[s] = 1.f;
+            d.X[s] = 0.f;
+        }
+    }
+    float4 v = d.vel[s];
+    float4 hy = make_float4(v.x, v.y, v.z, 0.f);
+    float4 sn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (do_sph && d.orig[s] < n_gas) {
+        float h = d.len_h[s], rho = d.rho[s], u = v.w;
+        float P = (gamma - 1.f) * rho * u;
+        g.z = h;
+        g.w = d.zeta[s] / d.omega[s];
+        hy.w = P / (rho * rho);
+        sn = make_float4(sqrtf(gamma * (gamma - 1.f) * u), rho, 1.f / h, P);
+    }
+    d.grav[s] = g;
+    d.hydro[s] = hy;
+    d.snd[s] = sn;
+}
+
+__global__ void k_unpermute(int n, int n_gas, int what, int add_acc, evol_dev d, float *h, float *eps, float *ax,
+                            float *ay, float *az, float *pot, float *rho, float *P, float *c, float *omega,
+                            float *zeta, float *dudt, float *ups, float *X)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int j = d.orig[s];
+    bool gas = j < n_gas;
+    if (what & EVOL_UNPERM_LENGTHS) {
+        if (h && gas) h[j] = d.len_h[s];
+    }
+    if (what & EVOL_UNPERM_EPSOUT) {
+        if (eps) eps[j] = d.len_eps[s];
+        if (ups) ups[j] = d.ups[s];
+        if (X) X[j] = d.X[s];
+    }
+    if ((what & EVOL_UNPERM_DENSITY) && gas) {
+        float4 sn = d.snd[s];
+        if (rho) rho[j] = d.rho[s];
+        if (P) P[j] = sn.w;
+        if (c) c[j] = sn.x;
+        if (omega) omega[j] = d.omega[s];
+        if (zeta) zeta[j] = d.zeta[s];
+    }
+    if (what & EVOL_UNPERM_ACC) {
+        float4 a = d.acc[s];
+        if (add_acc) {
+            if (ax) ax[j] += a.x;
+            if (ay) ay[j] += a.y;
+            if (az) az[j] += a.z;
+        } else {
+            if (ax) ax[j] = a.x;
+            if (ay) ay[j] = a.y;
+            if (az) az[j] = a.z;
+            if (pot) pot[j] = a.w;
+        }
+    }
+    if ((what & EVOL_UNPERM_DUDT) && gas) {
+        if (dudt) dudt[j] = d.dudt[s];
+    }
+}
+
+constexpr int DG_THREADS = 256;
+constexpr int DG_N = 11;
+
+__global__ void k_diag_partial(int n, int n_gas, int have_sph, evol_dev d, double *part)
+{
+    double v[DG_N];
+    for (int k = 0; k < DG_N; ++k) v[k] = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        float4 p = d.pos[s], ve = d.vel[s], a = d.acc[s];
+        double m = p.w;
+        v[0] += m * ve.x; v[1] += m * ve.y; v[2] += m * ve.z;
+        v[3] += m * a.x; v[4] += m * a.y; v[5] += m * a.z;
+        v[6] += 0.5 * m * ((double)ve.x * ve.x + (double)ve.y * ve.y + (double)ve.z * ve.z);
+        bool gas = d.orig[s] < n_gas;
+        if (gas) v[7] += m * ve.w;
+        v[8] += 0.5 * m * a.w;
+        if (gas && have_sph) v[9] += m * ((double)d.vah[s] + (double)d.dudt[s]);
+        v[10] += m;
+    }
+    __shared__ double sh[DG_THREADS / 32][DG_N];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = 0; k < DG_N; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[w][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < DG_N) {
+        double x = 0.0;
+        for (int k = 0; k < DG_THREADS / 32; ++k) x += sh[k][threadIdx.x];
+        part[blockIdx.x * DG_N + threadIdx.x] = x;
+    }
+}
+
+__global__ void k_diag_final(int nparts, const double *part, const int32_t *nnodes,
+                             const unsigned long long *counters, double *diag)
+{
+    int k = threadIdx.x;
+    if (k < DG_N) {
+        double x = 0.0;
+        for (int b = 0; b < nparts; ++b) x += part[b * DG_N + k];
+        diag[k] = x;
+    }
+    if (k == 0) {
+        diag[11] = (double)*nnodes;
+        diag[12] = (double)counters[0];
+        diag[13] = (double)counters[1];
+        diag[14] = (double)counters[2];
+        diag[15] = (double)counters[3];
+    }
+}
+
+}  // namespace
+
+int evol_launch_pack(evol_ctx *c, const evol_particles *p, const evol_params *prm, int do_grav, int do_sph)
+{
+    int n = (int)p->n;
+    k_pack<<<(n + 255) / 256, 256, 0, c->stream>>>(n, (int)p->n_gas, do_grav, prm->adaptive_softening, do_sph,
+                                                   prm->gamma, c->d);
+    return evol_cuda_ok(cudaGetLastError());
+}
+
+int evol_launch_unpermute_ex(evol_ctx *c, const evol_particles *p, const evol_outputs *o, int what, int add_acc)
+{
+    int n = (int)p->n;
+    evol_outputs z{};
+    const evol_outputs *q = o ? o : &z;
+    k_unpermute<<<(n + 255) / 256, 256, 0, c->stream>>>(n, (int)p->n_gas, what, add_acc, c->d, p->h, p->eps, q->ax,
+                                                        q->ay, q->az, q->pot, q->rho, q->P, q->c, q->omega, q->zeta,
+                                                        q->dudt, q->ups, q->X);
+    return evol_cuda_ok(cudaGetLastError());
+}
+
+int evol_launch_unpermute(evol_ctx *c, const evol_particles *p, const evol_outputs *o, int what)
+{
+    return evol_launch_unpermute_ex(c, p, o, what, 0);
+}
+
+int evol_launch_diagnostics(evol_ctx *c, const evol_particles *p, const evol_params *prm)
+{
+    int nb = (int)c->diag_blocks;
+    k_diag_partial<<<nb, DG_THREADS, 0, c->stream>>>((int)p->n, (int)p->n_gas, prm->sph, c->d, c->d.diag_part);
+    k_diag_final<<<1, 32, 0, c->stream>>>(nb, c->d.diag_part, c->d.nnodes, c->d.counters, c->d.diag);
+    return evol_cuda_ok(cudaGetLastError());
+}

@@ -1,0 +1,52 @@
+"""Device buffers for one particle set: torch CUDA tensors for the inputs and outputs, wrapped
+into the C structs of evol.py.  Allocation and copies only; the computation is in libevol.so."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import evol as E
+
+OUT_LEN_GAS = {"rho", "P", "c", "omega", "zeta", "dudt"}
+
+
+class DeviceSet:
+    """Inputs of a workload on `device` plus output tensors, and the matching C structs."""
+
+    def __init__(self, w, params=None, device="cuda:0", outputs=None, precision=None, pinned_host=False):
+        self.w = w
+        self.n, self.n_gas = w.n, w.n_gas
+        p = params or w.params
+        self.params_py = p
+        self.params = E.make_params(p)
+        if precision is not None:
+            self.params.precision = int(precision)
+        self.device = torch.device(device)
+        self.inp = {}
+        for k, a in w.arrays().items():
+            t = torch.from_numpy(np.ascontiguousarray(a, np.float32))
+            if k in ("u", "h"):
+                t = t[: max(self.n_gas, 1)].clone() if self.n_gas > 0 else t[:1].clone()
+            self.inp[k] = t.to(self.device)
+        names = outputs if outputs is not None else E.OUTPUT_FIELDS
+        self.out = {}
+        for k in names:
+            ln = self.n_gas if k in OUT_LEN_GAS else self.n
+            self.out[k] = torch.zeros(max(ln, 1), dtype=torch.float32, device=self.device)
+        self.particles = E.make_particles(self.n, self.n_gas, self.inp)
+        self.outputs = E.make_outputs(self.out)
+
+    def reset_lengths(self):
+        """Restore the caller's starting guesses for h and eps (the step overwrites them)."""
+        for k in ("h", "eps"):
+            a = np.ascontiguousarray(getattr(self.w, k), np.float32)
+            if k == "h":
+                a = a[: max(self.n_gas, 1)]
+            self.inp[k].copy_(torch.from_numpy(a))
+
+    def numpy(self) -> dict:
+        res = {k: v.detach().cpu().numpy().astype(np.float64)[: (self.n_gas if k in OUT_LEN_GAS else self.n)]
+               for k, v in self.out.items()}
+        res["h"] = self.inp["h"].cpu().numpy().astype(np.float64)[: self.n_gas]
+        res["eps"] = self.inp["eps"].cpu().numpy().astype(np.float64)
+        return res

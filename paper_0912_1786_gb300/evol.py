@@ -1,0 +1,226 @@
+"""Thin ctypes binding of the C ABI in include/evol.h (argument marshalling only).
+
+Every computation runs in libevol.so's CUDA kernels; this module only fills the C structs
+with the device pointers of torch tensors (or host pointers for ``evol_step_host``) and
+checks status codes.  If the library is missing the calls raise: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libevol.so")
+
+EVOL_OK, EVOL_EINVAL, EVOL_ENOMEM, EVOL_ECUDA = 0, -1, -2, -3
+EVOL_EOVERFLOW, EVOL_ENOCONV, EVOL_ETIMEOUT, EVOL_ENAN, EVOL_ESTATE = -4, -5, -6, -7, -8
+EVOL_FP32_PLAIN, EVOL_FP32_MIXED = 0, 1
+EVOL_DBG_KEYS, EVOL_DBG_PERM, EVOL_DBG_NODES, EVOL_DBG_CUBE = 1, 2, 3, 4
+EVOL_DBG_MOMENTS, EVOL_DBG_HASHES, EVOL_DBG_COUNTS = 5, 6, 7
+
+_fp = C.POINTER(C.c_float)
+
+
+class EvolParticles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_gas", C.c_int64),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p),
+                ("m", C.c_void_p), ("u", C.c_void_p), ("h", C.c_void_p), ("eps", C.c_void_p)]
+
+
+class EvolParams(C.Structure):
+    _fields_ = [("theta", C.c_float), ("n_nei_sph", C.c_float), ("n_nei_grav", C.c_float),
+                ("gamma", C.c_float), ("alpha", C.c_float), ("beta", C.c_float), ("G", C.c_float),
+                ("gravity", C.c_int), ("sph", C.c_int), ("adaptive_softening", C.c_int),
+                ("use_tc_gradient", C.c_int), ("periodic_mask", C.c_int),
+                ("periodic_lo", C.c_float * 3), ("periodic_hi", C.c_float * 3),
+                ("precision", C.c_int), ("leaf_size", C.c_int), ("group_size", C.c_int)]
+
+
+class EvolOutputs(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("ax", "ay", "az", "pot", "rho", "P", "c", "omega", "zeta",
+                                           "dudt", "ups", "X")]
+
+
+OUTPUT_FIELDS = [f[0] for f in EvolOutputs._fields_]
+PARTICLE_FIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "eps"]
+
+_lib = None
+
+
+def lib():
+    """Load libevol.so (raises if it has not been built: no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_0912_1786_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, pp = C.c_void_p, C.POINTER
+        L.evol_create.argtypes = [pp(vp), C.c_int64, vp]
+        L.evol_destroy.argtypes = [vp]
+        for name in ("evol_build_tree",):
+            getattr(L, name).argtypes = [vp, pp(EvolParticles), pp(EvolParams)]
+        for name in ("evol_sph_density", "evol_gravity", "evol_sph_forces", "evol_step", "evol_step_host"):
+            getattr(L, name).argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs)]
+        L.evol_sync.argtypes = [vp]
+        L.evol_get_diagnostics.argtypes = [vp, pp(C.c_double)]
+        L.evol_get_timings.argtypes = [vp, pp(C.c_float)]
+        L.evol_get_debug.argtypes = [vp, C.c_int, vp, C.c_int64]
+        L.evol_get_debug.restype = C.c_int64
+        L.evol_set_check_mode.argtypes = [vp, C.c_int]
+        L.evol_strerror.argtypes = [C.c_int]
+        L.evol_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+class EvolError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {lib().evol_strerror(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(code, where):
+    if code != EVOL_OK:
+        raise EvolError(code, where)
+    return code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):           # numpy (host) arrays for evol_step_host
+        return t.ctypes.data
+    return int(t)
+
+
+def make_params(p) -> EvolParams:
+    """EvolParams from any object with the fields of workloads.Params."""
+    e = EvolParams()
+    for k in ("theta", "n_nei_sph", "n_nei_grav", "gamma", "alpha", "beta", "G"):
+        setattr(e, k, float(getattr(p, k)))
+    e.gravity = int(p.gravity)
+    e.sph = int(p.sph)
+    e.adaptive_softening = int(p.adaptive_softening)
+    e.use_tc_gradient = int(getattr(p, "use_tc_gradient", 1))
+    e.periodic_mask = int(getattr(p, "periodic_mask", 0))
+    e.periodic_lo = (C.c_float * 3)(*[float(v) for v in getattr(p, "periodic_lo", (0, 0, 0))])
+    e.periodic_hi = (C.c_float * 3)(*[float(v) for v in getattr(p, "periodic_hi", (1, 1, 1))])
+    e.precision = int(getattr(p, "precision", EVOL_FP32_PLAIN))
+    e.leaf_size = int(getattr(p, "leaf_size", 8))
+    e.group_size = int(getattr(p, "group_size", 32))
+    return e
+
+
+def make_particles(n, n_gas, arrays: dict) -> EvolParticles:
+    e = EvolParticles()
+    e.n, e.n_gas = int(n), int(n_gas)
+    for k in PARTICLE_FIELDS:
+        setattr(e, k, _ptr(arrays.get(k)))
+    return e
+
+
+def make_outputs(outputs: dict | None) -> EvolOutputs:
+    e = EvolOutputs()
+    for k in OUTPUT_FIELDS:
+        setattr(e, k, _ptr((outputs or {}).get(k)))
+    return e
+
+
+# ---- the C entry points, same names -------------------------------------------------------
+def evol_create(max_n: int, stream=None):
+    ctx = C.c_void_p()
+    s = None if stream is None else _ptr_stream(stream)
+    _check(lib().evol_create(C.byref(ctx), int(max_n), s), "evol_create")
+    return ctx
+
+
+def _ptr_stream(stream):
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def evol_destroy(ctx):
+    _check(lib().evol_destroy(ctx), "evol_destroy")
+
+
+def evol_build_tree(ctx, particles: EvolParticles, params: EvolParams):
+    return _check(lib().evol_build_tree(ctx, C.byref(particles), C.byref(params)), "evol_build_tree")
+
+
+def evol_sph_density(ctx, particles, params, outputs):
+    return _check(lib().evol_sph_density(ctx, C.byref(particles), C.byref(params), C.byref(outputs)),
+                  "evol_sph_density")
+
+
+def evol_gravity(ctx, particles, params, outputs):
+    return _check(lib().evol_gravity(ctx, C.byref(particles), C.byref(params), C.byref(outputs)), "evol_gravity")
+
+
+def evol_sph_forces(ctx, particles, params, outputs):
+    return _check(lib().evol_sph_forces(ctx, C.byref(particles), C.byref(params), C.byref(outputs)),
+                  "evol_sph_forces")
+
+
+def evol_step(ctx, particles, params, outputs):
+    return _check(lib().evol_step(ctx, C.byref(particles), C.byref(params), C.byref(outputs)), "evol_step")
+
+
+def evol_step_host(ctx, particles, params, outputs):
+    return _check(lib().evol_step_host(ctx, C.byref(particles), C.byref(params), C.byref(outputs)),
+                  "evol_step_host")
+
+
+def evol_sync(ctx, raise_on_error=True):
+    rc = lib().evol_sync(ctx)
+    if raise_on_error:
+        _check(rc, "evol_sync")
+    return rc
+
+
+def evol_get_diagnostics(ctx):
+    out = (C.c_double * 16)()
+    _check(lib().evol_get_diagnostics(ctx, out), "evol_get_diagnostics")
+    return list(out)
+
+
+def evol_get_timings(ctx):
+    out = (C.c_float * 5)()
+    _check(lib().evol_get_timings(ctx, out), "evol_get_timings")
+    return list(out)
+
+
+def evol_set_check_mode(ctx, on: bool):
+    _check(lib().evol_set_check_mode(ctx, int(bool(on))), "evol_set_check_mode")
+
+
+def evol_get_debug(ctx, what: int, dtype):
+    """Copy one debug array; dtype is the numpy element type of `what`."""
+    import numpy as np
+    cnt = lib().evol_get_debug(ctx, int(what), None, 0)
+    if cnt < 0:
+        raise EvolError(int(cnt), "evol_get_debug")
+    out = np.empty(int(cnt), dtype=dtype)
+    rc = lib().evol_get_debug(ctx, int(what), out.ctypes.data, out.nbytes)
+    if rc < 0:
+        raise EvolError(int(rc), "evol_get_debug")
+    return out
+
+
+@dataclass
+class Step:
+    """Convenience holder: one context plus the marshalled structs for one particle set."""
+
+    ctx: object
+    particles: EvolParticles
+    params: EvolParams
+    outputs: EvolOutputs
+    keep: tuple = ()
+
+    def run(self):
+        evol_step(self.ctx, self.particles, self.params, self.outputs)
+
+    def sync(self, raise_on_error=True):
+        return evol_sync(self.ctx, raise_on_error)
