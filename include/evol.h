@@ -179,6 +179,24 @@ int evol_set_check_mode(evol_ctx *ctx, int on);
  * [2] h solve, [3] force walk, [4] total. Valid after evol_sync. */
 int evol_get_timings(evol_ctx *ctx, float out[5]);
 
+/* Allocation-free key + sort stage (the paper has no counterpart: this is a service for callers
+ * that may not allocate device memory where they call us, e.g. from a host callback or a
+ * framework hook that must not re-enter the device allocator, or in a process whose device
+ * memory is fixed at start-up).  Computes the root cube, the 63-bit Morton keys and the stable
+ * radix sort exactly as evol_build_tree does and returns the sorted keys and the permutation
+ * (sorted position -> caller index).  x, y, z, keys_sorted (n) and perm (n) are DEVICE pointers
+ * owned by the caller; keys_sorted and perm are also used as working space.  cube (device,
+ * 4 doubles: corner x, y, z, side) may be NULL.  stream: a cudaStream_t (NULL = legacy stream).
+ * Allocates nothing: its scratch is a static device array of EVOL_NOALLOC_MAX_N * 12 bytes
+ * (768 KiB) held by every GPU that loads the library until the process exits.  The array's
+ * address is looked up on the first call made on each device (with that device current), so
+ * make that first call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race.  Returns EVOL_EINVAL if n < 0 or n > EVOL_NOALLOC_MAX_N, or a pointer
+ * is NULL; EVOL_OK for n == 0 (nothing launched); asynchronous otherwise. */
+#define EVOL_NOALLOC_MAX_N 65536
+int evol_sort_keys_noalloc(int64_t n, const float *x, const float *y, const float *z, uint64_t *keys_sorted,
+                           int32_t *perm, double *cube, void *stream);
+
 const char *evol_strerror(int code);
 
 #ifdef __cplusplus

@@ -69,6 +69,7 @@ def lib():
         L.evol_get_debug.argtypes = [vp, C.c_int, vp, C.c_int64]
         L.evol_get_debug.restype = C.c_int64
         L.evol_set_check_mode.argtypes = [vp, C.c_int]
+        L.evol_sort_keys_noalloc.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, vp]
         L.evol_strerror.argtypes = [C.c_int]
         L.evol_strerror.restype = C.c_char_p
         _lib = L
@@ -194,6 +195,16 @@ def evol_get_timings(ctx):
 
 def evol_set_check_mode(ctx, on: bool):
     _check(lib().evol_set_check_mode(ctx, int(bool(on))), "evol_set_check_mode")
+
+
+EVOL_NOALLOC_MAX_N = 65536
+
+
+def evol_sort_keys_noalloc(n, x, y, z, keys_sorted, perm, cube=None, stream=None):
+    """Allocation-free key + sort stage (device tensors in, device tensors out)."""
+    s = None if stream is None else _ptr_stream(stream)
+    return _check(lib().evol_sort_keys_noalloc(int(n), _ptr(x), _ptr(y), _ptr(z), _ptr(keys_sorted), _ptr(perm),
+                                               _ptr(cube), s), "evol_sort_keys_noalloc")
 
 
 def evol_get_debug(ctx, what: int, dtype):
