@@ -366,6 +366,7 @@ def main():
                            "l2": "working set > L2 (inputs 40 B/particle x 3.1M + tree), no flush"},
                 "phase_ms": {"build": ph[0], "eps_solve": ph[1], "h_solve": ph[2], "walk": ph[3], "total": ph[4]},
                 "interactions_per_s": {"far": far / walk_s, "pp": pp / walk_s, "sph": sph / walk_s},
+                "length_iterations_per_particle": diag[15] / max(1, w.n + w.n_gas),
                 "status_last_step": rc,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": None}

@@ -18,6 +18,7 @@ namespace {
 
 constexpr int64_t CAND_CAP = 4096;       // candidate leaves per warp in the length solve
 constexpr int64_t NODE_FACTOR = 3;       // node capacity = 3 * particles + 64
+constexpr int64_t WSTACK_CAP = 4096;     // traversal stack entries per warp in the force walk
 
 template <typename T>
 int dalloc(T **p, size_t count)
@@ -34,13 +35,14 @@ void free_all(evol_ctx *c)
                     d.zeta, d.rho, d.neps, d.ups, d.X, d.acc, d.dudt, d.keys_a, d.keys_b, d.vals_a, d.vals_b,
                     d.hist, d.lcp, d.cnt, d.base, d.scan_part, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
                     d.nnch, d.narrive, d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nM64, d.nC64, d.nQ64, d.nBmin,
-                    d.nBmax, d.nI, d.cand_leaf, d.cand_mask, d.diag_part, d.diag, d.counters, d.err, d.nnodes,
+                    d.nBmax, d.nI, d.nK0, d.nK1, d.wstack, d.cand_leaf, d.cand_mask, d.diag_part, d.diag, d.counters, d.err, d.nnodes,
                     d.cube, d.fcube, d.bbox_part, d.hash3, d.cnt3, c->stage};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 6; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    for (int k = 0; k < 8; ++k)
+        if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
 }
 
 int check_args(evol_ctx *c, const evol_particles *p, const evol_params *prm)
@@ -104,36 +106,39 @@ int set_err(evol_ctx *c, int rc)
     return rc;
 }
 
-// The sequence of one full step (captured into the graph).
-int record_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out)
+// The phases of one full step; each is captured into its own graph so that the timing
+// events can be recorded between graph launches.
+constexpr int NPHASE = 5;   // build | eps solve | h solve + pack + node maxima | walk | un-permute + diagnostics
+
+int record_phase(evol_ctx *c, int k, evol_particles *p, const evol_params *prm, evol_outputs *out)
 {
-    int rc;
+    int rc = EVOL_OK;
     const bool grav = prm->gravity != 0, sph = prm->sph != 0 && p->n_gas > 0;
-    cudaEventRecord(c->ev[0], c->stream);
-    reset_counters(c);
-    if ((rc = evol_launch_build(c, p, prm))) return rc;
-    c->built_n = p->n;
-    c->built_ngas = p->n_gas;
-    c->built_x = p->x;
-    cudaEventRecord(c->ev[1], c->stream);
-    if (grav && prm->adaptive_softening)
-        if ((rc = evol_launch_lengths(c, p, prm, 1))) return rc;
-    cudaEventRecord(c->ev[2], c->stream);
-    if (sph)
-        if ((rc = evol_launch_lengths(c, p, prm, 0))) return rc;
-    if ((rc = evol_launch_pack(c, p, prm, grav, sph))) return rc;
-    if ((rc = evol_launch_node_lengths(c, prm, 0))) return rc;
-    cudaEventRecord(c->ev[3], c->stream);
-    if ((rc = evol_launch_walk(c, p, prm, grav, sph))) return rc;
-    cudaEventRecord(c->ev[4], c->stream);
-    int what = EVOL_UNPERM_ACC | (grav ? EVOL_UNPERM_EPSOUT : 0) |
-               (sph ? (EVOL_UNPERM_LENGTHS | EVOL_UNPERM_DENSITY | EVOL_UNPERM_DUDT) : 0);
-    if ((rc = evol_launch_unpermute(c, p, out, what))) return rc;
-    if ((rc = evol_launch_diagnostics(c, p, prm))) return rc;
-    cudaEventRecord(c->ev[5], c->stream);
-    c->density_done = sph;
-    c->eps_done = grav;
-    return EVOL_OK;
+    switch (k) {
+    case 0:
+        reset_counters(c);
+        rc = evol_launch_build(c, p, prm);
+        break;
+    case 1:
+        if (grav && prm->adaptive_softening) rc = evol_launch_lengths(c, p, prm, 1);
+        break;
+    case 2:
+        if (sph) rc = evol_launch_lengths(c, p, prm, 0);
+        if (!rc) rc = evol_launch_pack(c, p, prm, grav, sph);
+        if (!rc) rc = evol_launch_node_lengths(c, prm, (int)p->n_gas);
+        break;
+    case 3:
+        rc = evol_launch_walk(c, p, prm, grav, sph);
+        break;
+    case 4: {
+        int what = EVOL_UNPERM_ACC | (grav ? EVOL_UNPERM_EPSOUT : 0) |
+                   (sph ? (EVOL_UNPERM_LENGTHS | EVOL_UNPERM_DENSITY | EVOL_UNPERM_DUDT) : 0);
+        rc = evol_launch_unpermute(c, p, out, what);
+        if (!rc) rc = evol_launch_diagnostics(c, p, prm);
+        break;
+    }
+    }
+    return rc;
 }
 
 }  // namespace
@@ -177,6 +182,8 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     c->diag_blocks = c->num_sms * 2;
     c->cand_cap = CAND_CAP;
     c->cand_slots = (int64_t)c->num_sms * 8 * evol_lengths_warps_per_block();
+    c->wstack_slots = (int64_t)c->num_sms * 64;      // at most 64 resident warps per SM
+    c->wstack_cap = WSTACK_CAP;
     int64_t n = max_n, nn = c->node_cap;
     int64_t scan_parts = (256 * c->sort_blocks > n + 1 ? 256 * c->sort_blocks : n + 1) / 4096 + 2;
     evol_dev &d = c->d;
@@ -195,6 +202,8 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.nA, nn); rc |= dalloc(&d.nB, nn); rc |= dalloc(&d.nC, nn); rc |= dalloc(&d.nQ0, nn);
     rc |= dalloc(&d.nQ1, nn); rc |= dalloc(&d.nM64, nn); rc |= dalloc(&d.nC64, 3 * nn); rc |= dalloc(&d.nQ64, 6 * nn);
     rc |= dalloc(&d.nBmin, nn); rc |= dalloc(&d.nBmax, nn); rc |= dalloc(&d.nI, nn);
+    rc |= dalloc(&d.nK0, nn); rc |= dalloc(&d.nK1, nn);
+    rc |= dalloc(&d.wstack, c->wstack_slots * c->wstack_cap);
     rc |= dalloc(&d.cand_leaf, 2 * c->cand_slots * c->cand_cap);
     rc |= dalloc(&d.cand_mask, c->cand_slots * c->cand_cap);
     rc |= dalloc(&d.diag_part, 16 * c->diag_blocks); rc |= dalloc(&d.diag, 16);
@@ -271,7 +280,7 @@ int evol_gravity(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_ou
         if ((rc = evol_launch_lengths(c, p, prm, 1))) return set_err(c, rc);
     c->eps_done = 1;
     if ((rc = evol_launch_pack(c, p, prm, 1, c->density_done))) return set_err(c, rc);
-    if ((rc = evol_launch_node_lengths(c, prm, 0))) return set_err(c, rc);
+    if ((rc = evol_launch_node_lengths(c, prm, (int)p->n_gas))) return set_err(c, rc);
     if ((rc = evol_launch_walk(c, p, prm, 1, 0))) return set_err(c, rc);
     if ((rc = evol_launch_unpermute(c, p, out, EVOL_UNPERM_ACC | EVOL_UNPERM_EPSOUT))) return set_err(c, rc);
     return EVOL_OK;
@@ -284,7 +293,7 @@ int evol_sph_forces(evol_ctx *c, const evol_particles *p, const evol_params *prm
     if (!prm->sph) return EVOL_EINVAL;
     if (c->built_n != p->n || c->built_x != (const void *)p->x || !c->density_done) return EVOL_ESTATE;
     if (p->n_gas == 0) return EVOL_OK;
-    if ((rc = evol_launch_node_lengths(c, prm, 0))) return set_err(c, rc);
+    if ((rc = evol_launch_node_lengths(c, prm, (int)p->n_gas))) return set_err(c, rc);
     if ((rc = evol_launch_walk(c, p, prm, 0, 1))) return set_err(c, rc);
     if ((rc = evol_launch_unpermute_ex(c, p, out, EVOL_UNPERM_ACC | EVOL_UNPERM_DUDT, 1))) return set_err(c, rc);
     return EVOL_OK;
@@ -302,11 +311,12 @@ int evol_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outpu
     sig = fnv(sig, out, sizeof *out);
     sig = fnv(sig, &c->check_mode, sizeof c->check_mode);
     sig = fnv(sig, &c->stream, sizeof c->stream);
-    if (!c->graph_exec || sig != c->graph_sig) {
-        if (c->graph_exec) {
-            cudaGraphExecDestroy(c->graph_exec);
-            c->graph_exec = nullptr;
-        }
+    if (!c->graph_exec[0] || sig != c->graph_sig) {
+        for (int k = 0; k < NPHASE; ++k)
+            if (c->graph_exec[k]) {
+                cudaGraphExecDestroy(c->graph_exec[k]);
+                c->graph_exec[k] = nullptr;
+            }
         cudaStream_t cap_stream = c->stream;
         bool own = false;
         if (!cap_stream) {          // the legacy stream cannot be captured: record on a private stream
@@ -316,31 +326,41 @@ int evol_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outpu
         }
         cudaStream_t saved = c->stream;
         c->stream = cap_stream;
-        cudaGraph_t graph = nullptr;
-        if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-            c->stream = saved;
-            if (own) cudaStreamDestroy(cap_stream);
-            return set_err(c, EVOL_ECUDA);
+        int prc = EVOL_OK;
+        for (int k = 0; k < NPHASE && !prc; ++k) {
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                prc = EVOL_ECUDA;
+                break;
+            }
+            int rrc = record_phase(c, k, p, prm, out);
+            cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
+            if (rrc || e != cudaSuccess || !graph) {
+                prc = rrc ? rrc : EVOL_ECUDA;
+            } else if (cudaGraphInstantiate(&c->graph_exec[k], graph, 0) != cudaSuccess) {
+                c->graph_exec[k] = nullptr;
+                prc = EVOL_ECUDA;
+            }
+            if (graph) cudaGraphDestroy(graph);
         }
-        int rrc = record_step(c, p, prm, out);
-        cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
         c->stream = saved;
         if (own) cudaStreamDestroy(cap_stream);
-        if (rrc || e != cudaSuccess || !graph) {
-            if (graph) cudaGraphDestroy(graph);
+        if (prc) {
             cudaGetLastError();
-            return set_err(c, rrc ? rrc : EVOL_ECUDA);
-        }
-        e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            c->graph_exec = nullptr;
-            cudaGetLastError();
-            return set_err(c, EVOL_ECUDA);
+            for (int k = 0; k < NPHASE; ++k)
+                if (c->graph_exec[k]) {
+                    cudaGraphExecDestroy(c->graph_exec[k]);
+                    c->graph_exec[k] = nullptr;
+                }
+            return set_err(c, prc);
         }
         c->graph_sig = sig;
     }
-    if (cudaGraphLaunch(c->graph_exec, c->stream) != cudaSuccess) return set_err(c, EVOL_ECUDA);
+    for (int k = 0; k < NPHASE; ++k) {
+        cudaEventRecord(c->ev[k], c->stream);
+        if (cudaGraphLaunch(c->graph_exec[k], c->stream) != cudaSuccess) return set_err(c, EVOL_ECUDA);
+    }
+    cudaEventRecord(c->ev[NPHASE], c->stream);
     c->built_n = p->n;
     c->built_ngas = p->n_gas;
     c->built_x = p->x;
@@ -418,6 +438,7 @@ int evol_get_timings(evol_ctx *c, float out[5])
 {
     if (!c || !out) return EVOL_EINVAL;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return EVOL_ECUDA;
+    // build | eps solve | h solve (+ pack, node maxima) | walk | total
     const int pairs[5][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {0, 5}};
     for (int k = 0; k < 5; ++k) {
         float ms = -1.f;

@@ -50,6 +50,8 @@ struct evol_dev {
     double *nM64, *nC64, *nQ64;         // FP64 moments (mixed precision): M, com[3], Q[6]
     float4 *nBmin, *nBmax;              // particle bounding box (w of nBmin: node holds gas)
     int4 *nI;                           // walk copy: level | leaf << 8, next, begin, end
+    int4 *nK0, *nK1;                    // child ids (up to 8, -1 padded) of internal nodes
+    int2 *wstack;                       // per-warp traversal stacks of the force walk
     // length solve scratch: per resident warp candidate lists
     int32_t *cand_leaf;
     uint32_t *cand_mask;
@@ -76,6 +78,7 @@ struct evol_ctx {
     int64_t sort_blocks;
     int64_t bbox_blocks;
     int64_t cand_slots, cand_cap;
+    int64_t wstack_slots, wstack_cap;
     int64_t diag_blocks;
     int host_err;            // first error seen on the host side
     int check_mode;
@@ -84,7 +87,7 @@ struct evol_ctx {
     const void *built_x;
     int density_done, eps_done;
     // graph cache for evol_step
-    cudaGraphExec_t graph_exec;
+    cudaGraphExec_t graph_exec[8];   // one per phase of evol_step
     uint64_t graph_sig;
     // events for phase timings
     cudaEvent_t ev[6];
@@ -96,7 +99,7 @@ struct evol_ctx {
 int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *prm);
 int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params *prm, int mode);
 int evol_launch_walk(evol_ctx *c, const evol_particles *p, const evol_params *prm, int do_grav, int do_sph);
-int evol_launch_node_lengths(evol_ctx *c, const evol_params *prm, int mode_mask);
+int evol_launch_node_lengths(evol_ctx *c, const evol_params *prm, int n_gas);
 int evol_launch_unpermute(evol_ctx *c, const evol_particles *p, const evol_outputs *o, int what);
 int evol_launch_diagnostics(evol_ctx *c, const evol_particles *p, const evol_params *prm);
 
@@ -182,4 +185,5 @@ struct evol_kparams {
     int gravity, sph, adaptive, use_tc, periodic_mask, mixed;
     float plen[3];
     int n, n_gas, leaf;
+    int stack_cap;
 };

@@ -394,7 +394,8 @@ __global__ void k_fill(int n, const uint64_t *__restrict__ keys, const uint8_t *
 __global__ void k_link(const int32_t *__restrict__ nnodes, int leaf, const int32_t *__restrict__ nbeg,
                        const int32_t *__restrict__ nend, const int32_t *__restrict__ nlev,
                        const int32_t *__restrict__ nnext, int32_t *__restrict__ nparent, int32_t *__restrict__ nnch,
-                       int32_t *__restrict__ narrive, int4 *__restrict__ nI)
+                       int32_t *__restrict__ narrive, int4 *__restrict__ nI, int4 *__restrict__ nK0,
+                       int4 *__restrict__ nK1)
 {
     int nn = *nnodes;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += gridDim.x * blockDim.x) {
@@ -403,14 +404,18 @@ __global__ void k_link(const int32_t *__restrict__ nnodes, int leaf, const int32
         int e = nend[id];
         bool internal = (e - nbeg[id] > leaf) && nlev[id] < EVOL_MAXLEVEL;
         int k = 0;
+        int ch[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
         if (internal) {
             int c = id + 1;
-            while (c < nn && nbeg[c] < e) {
+            while (c < nn && nbeg[c] < e && k < 8) {
                 nparent[c] = id;
+                ch[k] = c;
                 ++k;
                 c = nnext[c];
             }
         }
+        nK0[id] = make_int4(ch[0], ch[1], ch[2], ch[3]);
+        nK1[id] = make_int4(ch[4], ch[5], ch[6], ch[7]);
         nnch[id] = k;
         nI[id] = make_int4(nlev[id] | ((internal ? 0 : 1) << 8), nnext[id], nbeg[id], e);
     }
@@ -692,7 +697,8 @@ int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *p
     k_fill<<<gb, tb, 0, st>>>(n, d.keys_a, d.lcp, d.base, leaf, c->node_cap, d.nbeg, d.nend, d.nlev, d.nnext,
                               d.nnodes, d.err);
     int ng = c->num_sms * 8;
-    k_link<<<ng, 256, 0, st>>>(d.nnodes, leaf, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent, d.nnch, d.narrive, d.nI);
+    k_link<<<ng, 256, 0, st>>>(d.nnodes, leaf, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent, d.nnch, d.narrive, d.nI,
+                               d.nK0, d.nK1);
     NodeOut o{d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nBmin, d.nBmax, d.nM64, d.nC64, d.nQ64};
     float theta = prm->theta;
     if (prm->precision == EVOL_FP32_MIXED)
@@ -704,13 +710,13 @@ int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *p
     return evol_cuda_ok(cudaGetLastError());
 }
 
-int evol_launch_node_lengths(evol_ctx *c, const evol_params *prm, int /*mode_mask*/)
+int evol_launch_node_lengths(evol_ctx *c, const evol_params *prm, int n_gas)
 {
     evol_dev &d = c->d;
     int ng = c->num_sms * 8;
     (void)prm;
     k_zero_i32<<<ng, 256, 0, c->stream>>>(d.nnodes, d.narrive);
-    k_node_lengths<<<ng, 128, 0, c->stream>>>(d.nnodes, (int)c->built_ngas, d.nbeg, d.nend, d.nnext, d.nparent,
+    k_node_lengths<<<ng, 128, 0, c->stream>>>(d.nnodes, n_gas, d.nbeg, d.nend, d.nnext, d.nparent,
                                               d.nnch, d.narrive, d.orig, d.len_eps, d.len_h, d.nB, d.nC);
     return evol_cuda_ok(cudaGetLastError());
 }

@@ -2,18 +2,22 @@
 // (Sect. 3, Eqs. motionvarmass1, thermalvarmass1, mu_visc) in one traversal of the tree, as
 // the paper does its second walk (Sect. 3.1).
 //
-// A warp owns 32 consecutive particles in key order and walks the pre-order node list once.
-// Every lane applies its own opening test to each node the warp visits, so the result is the
-// per-particle tree walk: node A is a far node for particle i iff
+// A warp owns 32 consecutive particles in key order (a compact group).  Node A is a far node
+// for particle i iff
 //     |r_i - com_A| > l_A/theta + delta_A                                     (Eq. opcrit)
 // and A's particle box lies farther than R_iA = 2 max(eps_i, epsmax_A) (and, for gas i and a
-// node holding gas, farther than 2 max(h_i, hmax_A)); otherwise it is opened.  A ballot gives
-// the accept mask and the open mask; the open mask of each level is kept in lane `level` of a
-// register so that descending and skipping need no stack.  Far nodes (with their accept mask)
-// and the particles of opened leaves (with their open mask) are staged in shared memory and
-// evaluated in batches: far nodes by monopole + traceless quadrupole about the centre of mass,
-// near particles by the symmetrised softened pair force plus the adaptive-softening
-// correction, and, for gas pairs with r < 2 max(h_i, h_j), the SPH terms.
+// node holding gas, farther than 2 max(h_i, hmax_A)); otherwise it is opened.  The warp keeps a
+// stack of (node, mask of lanes that still need the node) and pops up to 32 entries at a time,
+// one per lane, so the node loads of a batch are issued together.  Each popped node is first
+// classified against the group's bounding box: if every lane must accept it, or every lane must
+// open it, by bounds that hold with a relative margin of 1e-5 over the FP32 rounding of the
+// per-lane test, the decision is taken for the whole mask; only the remaining ("mixed") nodes
+// are tested lane by lane.  The per-particle decisions are therefore exactly those of a
+// per-particle walk.  Accepted nodes (with their accept mask) and the particles of opened leaves
+// (with their open mask) are staged in shared memory and evaluated in batches: far nodes by
+// monopole + traceless quadrupole about the centre of mass, near particles by the symmetrised
+// softened pair force plus the adaptive-softening correction, and, for gas pairs with
+// r < 2 max(h_i, h_j), the SPH terms.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,7 +30,12 @@ constexpr int WK_WARPS = WK_THREADS / 32;
 constexpr int FARCAP = 64;
 constexpr int NEARCAP = 64;
 
+constexpr float TAU = 1e-5f;      // safety margin of the group-level bounds
+
 struct WalkSmem {
+    float4 bA[WK_WARPS][32];      // popped batch: com, ropen^2
+    float4 bB[WK_WARPS][32];      // box centre, 2 hmax
+    float4 bC[WK_WARPS][32];      // box half widths, 2 epsmax
     int far_id[WK_WARPS][FARCAP];
     unsigned far_mask[WK_WARPS][FARCAP];
     float4 fA[WK_WARPS][FARCAP];
@@ -55,7 +64,6 @@ __global__ void __launch_bounds__(WK_THREADS) k_walk(evol_dev d, evol_kparams kp
     const int w = threadIdx.x >> 5;
     const int n = kp.n;
     const int ngroups = (n + 31) >> 5;
-    const int nn = *d.nnodes;
     const int pm = SPH ? kp.periodic_mask : 0;
     const float plen0 = kp.plen[0], plen1 = kp.plen[1], plen2 = kp.plen[2];
     const float inv_pi = 1.f / EVOL_PI_F;
@@ -222,63 +230,202 @@ __global__ void __launch_bounds__(WK_THREADS) k_walk(evol_dev d, evol_kparams kp
         };
 
         const unsigned rootmask = __ballot_sync(0xffffffffu, active);
-        int node = rootmask ? 0 : nn;
-        unsigned lvlmask = 0;
-        while (node < nn) {
-            const int4 I = d.nI[node];
-            const int lev = I.x & 255;
-            const unsigned M = lev == 0 ? rootmask : __shfl_sync(0xffffffffu, lvlmask, lev - 1);
-            bool far = false;
-            if ((M >> lane) & 1u) {
+        const unsigned ltmask = (1u << lane) - 1u;
+        // group bounds: particle box, extreme interaction radii
+        float gx0 = active ? pi.x : INFINITY, gy0 = active ? pi.y : INFINITY, gz0 = active ? pi.z : INFINITY;
+        float gx1 = active ? pi.x : -INFINITY, gy1 = active ? pi.y : -INFINITY, gz1 = active ? pi.z : -INFINITY;
+        float emax = (GRAV && active) ? two_eps_i : 0.f, emin = (GRAV && active) ? two_eps_i : INFINITY;
+        float hmax = gas_i ? two_h_i : -1.f, hmin = gas_i ? two_h_i : INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            gx0 = fminf(gx0, __shfl_xor_sync(0xffffffffu, gx0, o));
+            gy0 = fminf(gy0, __shfl_xor_sync(0xffffffffu, gy0, o));
+            gz0 = fminf(gz0, __shfl_xor_sync(0xffffffffu, gz0, o));
+            gx1 = fmaxf(gx1, __shfl_xor_sync(0xffffffffu, gx1, o));
+            gy1 = fmaxf(gy1, __shfl_xor_sync(0xffffffffu, gy1, o));
+            gz1 = fmaxf(gz1, __shfl_xor_sync(0xffffffffu, gz1, o));
+            emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+            emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+            hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+            hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
+        }
+        const float gcx = 0.5f * (gx0 + gx1), gcy = 0.5f * (gy0 + gy1), gcz = 0.5f * (gz0 + gz1);
+        const float gwx = 0.5f * (gx1 - gx0), gwy = 0.5f * (gy1 - gy0), gwz = 0.5f * (gz1 - gz0);
+        const bool all_gas = SPH && __all_sync(0xffffffffu, !active || gas_i);
+        if (!GRAV) emin = 0.f;
+
+        int2 *stk = d.wstack + (size_t)(blockIdx.x * WK_WARPS + w) * kp.stack_cap;
+        int top = 0;
+        if (rootmask) {
+            if (lane == 0) stk[0] = make_int2(0, (int)rootmask);
+            top = 1;
+        }
+        __syncwarp();
+        while (top > 0) {
+            const int k = min(top, 32);
+            top -= k;
+            int node = -1;
+            unsigned M = 0;
+            if (lane < k) {
+                const int2 e = stk[top + lane];
+                node = e.x;
+                M = (unsigned)e.y;
+            }
+            __syncwarp();
+            int4 I = make_int4(0, 0, 0, 0);
+            int cls = 0;                     // 0 none, 1 accept all, 2 open all, 3 mixed
+            unsigned Ak = 0, Ok = 0;
+            if (lane < k) {
+                I = d.nI[node];
                 const float4 B = d.nB[node];
                 const float4 C = d.nC[node];
-                float ex = fabsf(evol_wrap(pi.x - B.x, plen0, pm & 1)) - C.x;
-                float ey = fabsf(evol_wrap(pi.y - B.y, plen1, pm & 2)) - C.y;
-                float ez = fabsf(evol_wrap(pi.z - B.z, plen2, pm & 4)) - C.z;
-                ex = fmaxf(ex, 0.f); ey = fmaxf(ey, 0.f); ez = fmaxf(ez, 0.f);
-                const float bd2 = ex * ex + ey * ey + ez * ez;
-                float R = GRAV ? fmaxf(two_eps_i, C.w) : 0.f;
-                if (SPH && gas_i && B.w >= 0.f) R = fmaxf(R, fmaxf(two_h_i, B.w));
-                far = bd2 > R * R;
-                if (GRAV && far) {
-                    const float4 A = d.nA[node];
-                    const float dx = pi.x - A.x, dy = pi.y - A.y, dz = pi.z - A.z;
-                    far = dx * dx + dy * dy + dz * dz > A.w;
+                const float4 A = GRAV ? d.nA[node] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float dx = fabsf(evol_wrap(B.x - gcx, plen0, pm & 1));
+                const float dy = fabsf(evol_wrap(B.y - gcy, plen1, pm & 2));
+                const float dz = fabsf(evol_wrap(B.z - gcz, plen2, pm & 4));
+                // nearest and farthest distance of a group point from the node box
+                const float nx = fmaxf(dx - (C.x + gwx), 0.f), ny = fmaxf(dy - (C.y + gwy), 0.f),
+                            nz = fmaxf(dz - (C.z + gwz), 0.f);
+                const float fx = fmaxf(dx + gwx - C.x, 0.f), fy = fmaxf(dy + gwy - C.y, 0.f),
+                            fz = fmaxf(dz + gwz - C.z, 0.f);
+                const float bnear2 = nx * nx + ny * ny + nz * nz, bfar2 = fx * fx + fy * fy + fz * fz;
+                float rup = GRAV ? fmaxf(emax, C.w) : 0.f;
+                float rlo = GRAV ? fmaxf(emin, C.w) : 0.f;
+                if (SPH && B.w >= 0.f && hmax >= 0.f) {
+                    rup = fmaxf(rup, fmaxf(hmax, B.w));
+                    if (all_gas) rlo = fmaxf(rlo, fmaxf(hmin, B.w));
                 }
-            }
-            const unsigned Af = __ballot_sync(0xffffffffu, far);
-            const unsigned O = M & ~Af;
-            if (CHECK && ((Af >> lane) & 1u)) {
-                ++cfar;
-                hfar += evol_mix64((unsigned long long)node);
-            }
-            if (GRAV && Af) {
-                if (lane == 0) {
-                    sm.far_id[w][nfar] = node;
-                    sm.far_mask[w][nfar] = Af;
+                bool acc_all = bnear2 > rup * rup * (1.f + TAU);
+                bool open_all = bfar2 < rlo * rlo * (1.f - TAU);
+                if (GRAV) {
+                    const float ax = fabsf(A.x - gcx), ay = fabsf(A.y - gcy), az = fabsf(A.z - gcz);
+                    const float mx = fmaxf(ax - gwx, 0.f), my = fmaxf(ay - gwy, 0.f), mz = fmaxf(az - gwz, 0.f);
+                    const float Mx = ax + gwx, My = ay + gwy, Mz = az + gwz;
+                    acc_all = acc_all && (mx * mx + my * my + mz * mz > A.w * (1.f + TAU));
+                    open_all = open_all || (Mx * Mx + My * My + Mz * Mz < A.w * (1.f - TAU));
                 }
-                if (++nfar == FARCAP) flush_far();
-            }
-            if (O) {
-                if (I.x >> 8) {
-                    if (CHECK && ((O >> lane) & 1u)) hnear += evol_mix64((unsigned long long)node);
-                    for (int b = I.z; b < I.w; b += 32) {
-                        const int k = min(32, I.w - b);
-                        if (nnear + k > NEARCAP) flush_near();
-                        if (lane < k) {
-                            sm.near_j[w][nnear + lane] = b + lane;
-                            sm.near_mask[w][nnear + lane] = O;
-                        }
-                        nnear += k;
-                    }
-                    node = I.y;
+                if (acc_all) {
+                    cls = 1;
+                    Ak = M;
+                } else if (open_all) {
+                    cls = 2;
+                    Ok = M;
                 } else {
-                    if (lane == lev) lvlmask = O;
-                    node = node + 1;
+                    cls = 3;
                 }
-            } else {
-                node = I.y;
+                sm.bA[w][lane] = A;
+                sm.bB[w][lane] = B;
+                sm.bC[w][lane] = C;
             }
+            __syncwarp();
+            // mixed nodes: every lane in the mask applies its own test
+            unsigned mm = __ballot_sync(0xffffffffu, cls == 3);
+            while (mm) {
+                const int kk = __ffs(mm) - 1;
+                mm &= mm - 1u;
+                const unsigned Mk = __shfl_sync(0xffffffffu, M, kk);
+                bool far = false;
+                if ((Mk >> lane) & 1u) {
+                    const float4 B = sm.bB[w][kk];
+                    const float4 C = sm.bC[w][kk];
+                    float ex = fabsf(evol_wrap(pi.x - B.x, plen0, pm & 1)) - C.x;
+                    float ey = fabsf(evol_wrap(pi.y - B.y, plen1, pm & 2)) - C.y;
+                    float ez = fabsf(evol_wrap(pi.z - B.z, plen2, pm & 4)) - C.z;
+                    ex = fmaxf(ex, 0.f); ey = fmaxf(ey, 0.f); ez = fmaxf(ez, 0.f);
+                    const float bd2 = ex * ex + ey * ey + ez * ez;
+                    float R = GRAV ? fmaxf(two_eps_i, C.w) : 0.f;
+                    if (SPH && gas_i && B.w >= 0.f) R = fmaxf(R, fmaxf(two_h_i, B.w));
+                    far = bd2 > R * R;
+                    if (GRAV && far) {
+                        const float4 A = sm.bA[w][kk];
+                        const float dx = pi.x - A.x, dy = pi.y - A.y, dz = pi.z - A.z;
+                        far = dx * dx + dy * dy + dz * dz > A.w;
+                    }
+                }
+                const unsigned Af = __ballot_sync(0xffffffffu, far);
+                if (lane == kk) {
+                    Ak = Af;
+                    Ok = Mk & ~Af;
+                }
+            }
+            // accepted nodes
+            const unsigned fa = __ballot_sync(0xffffffffu, Ak != 0u);
+            if (CHECK) {
+                unsigned f2 = fa;
+                while (f2) {
+                    const int kk = __ffs(f2) - 1;
+                    f2 &= f2 - 1u;
+                    const int nk = __shfl_sync(0xffffffffu, node, kk);
+                    const unsigned ak = __shfl_sync(0xffffffffu, Ak, kk);
+                    if ((ak >> lane) & 1u) {
+                        ++cfar;
+                        hfar += evol_mix64((unsigned long long)nk);
+                    }
+                }
+            }
+            if (GRAV && fa) {
+                const int cnt = __popc(fa);
+                if (nfar + cnt > FARCAP) flush_far();
+                if (Ak) {
+                    const int pos = nfar + __popc(fa & ltmask);
+                    sm.far_id[w][pos] = node;
+                    sm.far_mask[w][pos] = Ak;
+                }
+                nfar += cnt;
+            }
+            // opened leaves: their particles go to the near list
+            const bool isleaf = (I.x >> 8) & 1;
+            unsigned lm = __ballot_sync(0xffffffffu, Ok != 0u && isleaf);
+            while (lm) {
+                const int kk = __ffs(lm) - 1;
+                lm &= lm - 1u;
+                const unsigned ok = __shfl_sync(0xffffffffu, Ok, kk);
+                const int b0 = __shfl_sync(0xffffffffu, I.z, kk);
+                const int e0 = __shfl_sync(0xffffffffu, I.w, kk);
+                if (CHECK) {
+                    const int ln = __shfl_sync(0xffffffffu, node, kk);
+                    if ((ok >> lane) & 1u) hnear += evol_mix64((unsigned long long)ln);
+                }
+                for (int b = b0; b < e0; b += 32) {
+                    const int kc = min(32, e0 - b);
+                    if (nnear + kc > NEARCAP) flush_near();
+                    if (lane < kc) {
+                        sm.near_j[w][nnear + lane] = b + lane;
+                        sm.near_mask[w][nnear + lane] = ok;
+                    }
+                    nnear += kc;
+                }
+            }
+            // opened internal nodes: push their children with the open mask
+            const bool io = Ok != 0u && !isleaf;
+            int nch = 0;
+            int ch[8];
+            if (io) {
+                const int4 K0 = d.nK0[node], K1 = d.nK1[node];
+                ch[0] = K0.x; ch[1] = K0.y; ch[2] = K0.z; ch[3] = K0.w;
+                ch[4] = K1.x; ch[5] = K1.y; ch[6] = K1.z; ch[7] = K1.w;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) nch += ch[q] >= 0 ? 1 : 0;
+            }
+            int incl = nch;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (top + total > kp.stack_cap) {
+                if (lane == 0) evol_flag(d.err, EVOL_EOVERFLOW);
+                break;
+            }
+            if (io) {
+                int pos = top + incl - nch;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (q < nch) stk[pos + q] = make_int2(ch[q], (int)Ok);
+            }
+            top += total;
+            __syncwarp();
         }
         if (GRAV && nfar) flush_far();
         if (nnear) flush_near();
@@ -367,6 +514,7 @@ int evol_launch_walk(evol_ctx *c, const evol_particles *p, const evol_params *pr
     kp.use_tc = prm->use_tc_gradient;
     kp.periodic_mask = prm->periodic_mask;
     for (int a = 0; a < 3; ++a) kp.plen[a] = prm->periodic_hi[a] - prm->periodic_lo[a];
+    kp.stack_cap = (int)c->wstack_cap;
     bool mixed = prm->precision == EVOL_FP32_MIXED;
     bool check = c->check_mode != 0;
     if (do_grav && do_sph) launch_walk_pc<true, true>(c, kp, mixed, check);
