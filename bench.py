@@ -54,6 +54,8 @@ def make_workload(name: str):
             "plummer_2^20_theta0.6_gravity_only"
     if name == "c3":
         return W.hernquist_gas(n_dm=1 << 21, n_gas=1 << 20, seed=3), "hernquist_2^21_dm+2^20_gas"
+    if name == "c3s":      # one eighth of c3, for profiler captures
+        return W.hernquist_gas(n_dm=1 << 18, n_gas=1 << 17, seed=3), "hernquist_2^18_dm+2^17_gas"
     if name == "c4":
         return W.shock_tube(seed=4), "shock_tube_1046250_periodic_yz"
     if name == "c5":
@@ -220,7 +222,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c3s", "c4", "c5"])
     ap.add_argument("--precision", default="plain", choices=["plain", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

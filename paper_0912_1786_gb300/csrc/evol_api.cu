@@ -16,7 +16,7 @@ int evol_lengths_warps_per_block();
 
 namespace {
 
-constexpr int64_t CAND_CAP = 4096;       // candidate leaves per warp in the length solve
+constexpr int64_t CAND_CAP = 192;        // neighbour-list entries per lane in the length solve
 constexpr int64_t NODE_FACTOR = 3;       // node capacity = 3 * particles + 64
 constexpr int64_t WSTACK_CAP = 4096;     // traversal stack entries per warp in the force walk
 
@@ -181,7 +181,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     c->bbox_blocks = c->num_sms * 2;
     c->diag_blocks = c->num_sms * 2;
     c->cand_cap = CAND_CAP;
-    c->cand_slots = (int64_t)c->num_sms * 8 * evol_lengths_warps_per_block();
+    c->cand_slots = (int64_t)c->num_sms * 6 * evol_lengths_warps_per_block();
     c->wstack_slots = (int64_t)c->num_sms * 64;      // at most 64 resident warps per SM
     c->wstack_cap = WSTACK_CAP;
     int64_t n = max_n, nn = c->node_cap;
@@ -204,8 +204,8 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.nBmin, nn); rc |= dalloc(&d.nBmax, nn); rc |= dalloc(&d.nI, nn);
     rc |= dalloc(&d.nK0, nn); rc |= dalloc(&d.nK1, nn);
     rc |= dalloc(&d.wstack, c->wstack_slots * c->wstack_cap);
-    rc |= dalloc(&d.cand_leaf, 2 * c->cand_slots * c->cand_cap);
-    rc |= dalloc(&d.cand_mask, c->cand_slots * c->cand_cap);
+    rc |= dalloc(&d.cand_leaf, 2 * 32 * c->cand_slots * c->cand_cap);   // float2 per lane entry
+    rc |= dalloc(&d.cand_mask, 1);
     rc |= dalloc(&d.diag_part, 16 * c->diag_blocks); rc |= dalloc(&d.diag, 16);
     rc |= dalloc(&d.counters, 8); rc |= dalloc(&d.err, 1); rc |= dalloc(&d.nnodes, 1);
     rc |= dalloc(&d.cube, 4); rc |= dalloc(&d.fcube, 4); rc |= dalloc(&d.bbox_part, 6 * c->bbox_blocks);

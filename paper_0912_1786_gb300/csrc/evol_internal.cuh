@@ -52,9 +52,9 @@ struct evol_dev {
     int4 *nI;                           // walk copy: level | leaf << 8, next, begin, end
     int4 *nK0, *nK1;                    // child ids (up to 8, -1 padded) of internal nodes
     int2 *wstack;                       // per-warp traversal stacks of the force walk
-    // length solve scratch: per resident warp candidate lists
+    // length solve scratch: per-lane (distance, mass) neighbour lists of every warp slot
     int32_t *cand_leaf;
-    uint32_t *cand_mask;
+    uint32_t *cand_mask;     // unused
     // reductions / counters
     double *diag_part;       // per-block partials of diagnostics
     double *diag;            // 16

@@ -1,13 +1,16 @@
 // Smoothing and softening lengths (Sect. 2.1 Eqs. rho0, etan, iter; Sect. 3 Eqs. hn, nsum,
 // densitySPH, drhodr; Sect. 3.1 "gather" view with an enlarged search radius).
 //
-// A warp owns a group of 32 consecutive particles in key order.  It walks the tree once with
-// per-lane search radii R_i = 2 L_i (1 + 0.1) and records every leaf that any lane must open,
-// with the mask of those lanes, in a per-warp candidate list.  Each lane then solves
+// A warp owns a group of 32 consecutive particles in key order.  Each lane needs the particles
+// within its search radius R_i = 2 L_i (1 + 0.1).  The warp walks the tree once for all lanes,
+// popping up to 32 nodes at a time and classifying each against the group's bounding box (skip
+// for every lane / open for every lane / test lane by lane, with a 1e-5 relative margin over
+// FP32 rounding).  The particles of the opened leaves are gathered: each lane keeps those within
+// its own radius, as (distance, mass) pairs, in a private list.  Each lane then solves
 //     F(L) = L^3 n(L) - eta^3 = 0,   n(L) = sum_j W(r_ij, L)  (self term included)
-// by Newton steps kept inside a bisection bracket, re-using the list while 2L stays inside
-// the cached radius and walking again otherwise.  F is non-decreasing in L, so the root is
-// unique; with w(u) = pi L^3 W the sums are kept dimensionless:
+// by Newton steps kept inside a bisection bracket on its list, gathering again when 2L leaves
+// the cached radius.  F is non-decreasing in L, so the root is unique.  With w(u) = pi L^3 W
+// the sums are dimensionless:
 //     F = Sw/pi - eta^3,  F' = -Suw/(pi L),  Sw = sum w(u),  Suw = sum u w'(u).
 // Outputs (mode 0, gas h):   rho = Smw/(pi h^3), Omega* = -Suw/(3 Sw),
 //                           zeta = (3 Smw + Smuw)/(3 Sw)          (Sect. 3, Eq. drhodr)
@@ -26,24 +29,31 @@ constexpr int MAX_ITERS = 60;
 constexpr int MAX_WALKS = 24;
 constexpr float SEARCH_MARGIN = 1.1f;
 constexpr float CONV_TOL = 1e-6f;     // relative step below which one last evaluation is taken
+constexpr float TAU = 1e-5f;          // safety margin of the group-level bounds
 
 enum { ST_DONE = 0, ST_ACTIVE = 1, ST_LAST = 2 };
 
+struct LenSmem {
+    float4 bB[LW_WARPS][32];
+    float4 bC[LW_WARPS][32];
+};
+
 template <int MODE>
-__global__ void __launch_bounds__(LW_THREADS) k_lengths(evol_dev d, evol_kparams kp, int cand_cap,
+__global__ void __launch_bounds__(LW_THREADS, 6) k_lengths(evol_dev d, evol_kparams kp, int list_cap,
                                                         unsigned long long *queue)
 {
+    __shared__ LenSmem sm;
     const int lane = threadIdx.x & 31;
-    const int wslot = blockIdx.x * LW_WARPS + (threadIdx.x >> 5);
-    int2 *cl = reinterpret_cast<int2 *>(d.cand_leaf) + (size_t)wslot * cand_cap;
-    uint32_t *cm = d.cand_mask + (size_t)wslot * cand_cap;
+    const int w = threadIdx.x >> 5;
+    const int wslot = blockIdx.x * LW_WARPS + w;
+    float2 *lst = reinterpret_cast<float2 *>(d.cand_leaf) + (size_t)wslot * list_cap * 32;
+    int2 *stk = d.wstack + (size_t)wslot * kp.stack_cap;
     const int n = kp.n;
     const int ngroups = (n + 31) >> 5;
-    const int nn = *d.nnodes;
     const float eta = MODE == 0 ? kp.eta_h : kp.eta_e;
     const float eta3 = eta * eta * eta;
     const float inv_pi = 1.f / EVOL_PI_F;
-    float plen[3] = {kp.plen[0], kp.plen[1], kp.plen[2]};
+    const float plen0 = kp.plen[0], plen1 = kp.plen[1], plen2 = kp.plen[2];
     const int pm = kp.periodic_mask;
     const float side = d.fcube[3];
 
@@ -54,7 +64,7 @@ __global__ void __launch_bounds__(LW_THREADS) k_lengths(evol_dev d, evol_kparams
         if (g >= ngroups) break;
         const int s = g * 32 + lane;
         const bool valid = s < n;
-        float4 pi4 = valid ? d.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 pi4 = valid ? d.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
         const bool gas_i = valid && d.orig[s] < kp.n_gas;
         const bool act = MODE == 0 ? gas_i : valid;
         float L = 0.f;
@@ -64,147 +74,251 @@ __global__ void __launch_bounds__(LW_THREADS) k_lengths(evol_dev d, evol_kparams
         }
         float lo = 0.f, hi = INFINITY;
         int status = act ? ST_ACTIVE : ST_DONE;
-        bool stale = act;                  // needs a (re)walk before its sums are valid
+        bool stale = act;                  // needs a (re)gather before its sums are valid
         float Rc = 0.f;
+        int cnt = 0;                        // entries in this lane's list
         int iters = 0, walks = 0;
+        // group box of the lanes' positions (fixed for the group)
+        float gx0 = act ? pi4.x : INFINITY, gy0 = act ? pi4.y : INFINITY, gz0 = act ? pi4.z : INFINITY;
+        float gx1 = act ? pi4.x : -INFINITY, gy1 = act ? pi4.y : -INFINITY, gz1 = act ? pi4.z : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            gx0 = fminf(gx0, __shfl_xor_sync(0xffffffffu, gx0, o));
+            gy0 = fminf(gy0, __shfl_xor_sync(0xffffffffu, gy0, o));
+            gz0 = fminf(gz0, __shfl_xor_sync(0xffffffffu, gz0, o));
+            gx1 = fmaxf(gx1, __shfl_xor_sync(0xffffffffu, gx1, o));
+            gy1 = fmaxf(gy1, __shfl_xor_sync(0xffffffffu, gy1, o));
+            gz1 = fmaxf(gz1, __shfl_xor_sync(0xffffffffu, gz1, o));
+        }
+        const float gcx = 0.5f * (gx0 + gx1), gcy = 0.5f * (gy0 + gy1), gcz = 0.5f * (gz0 + gz1);
+        const float gwx = 0.5f * (gx1 - gx0), gwy = 0.5f * (gy1 - gy0), gwz = 0.5f * (gz1 - gz0);
 
         while (__any_sync(0xffffffffu, status != ST_DONE)) {
-            // ---- walk: collect the leaves any stale lane must open ----
-            if (__any_sync(0xffffffffu, stale)) {
-                if (stale) Rc = 2.f * L * SEARCH_MARGIN;
-                ++walks;
-                const unsigned rootmask = __ballot_sync(0xffffffffu, status != ST_DONE);
-                const float R2 = Rc * Rc;
-                int node = 0, nc = 0;
-                unsigned lvlmask = 0;
-                bool overflow = false;
-                while (node < nn) {
-                    const int4 I = d.nI[node];
-                    const int lev = I.x & 255;
-                    const unsigned M = lev == 0 ? rootmask : __shfl_sync(0xffffffffu, lvlmask, lev - 1);
-                    bool open = false;
-                    if ((M >> lane) & 1u) {
-                        const float4 B = d.nB[node];
-                        if (MODE == 1 || B.w >= 0.f) {
-                            const float4 C = d.nC[node];
-                            float ex = fabsf(evol_wrap(pi4.x - B.x, plen[0], pm & 1)) - C.x;
-                            float ey = fabsf(evol_wrap(pi4.y - B.y, plen[1], pm & 2)) - C.y;
-                            float ez = fabsf(evol_wrap(pi4.z - B.z, plen[2], pm & 4)) - C.z;
-                            ex = fmaxf(ex, 0.f); ey = fmaxf(ey, 0.f); ez = fmaxf(ez, 0.f);
-                            open = ex * ex + ey * ey + ez * ez < R2;
-                        }
-                    }
-                    const unsigned O = __ballot_sync(0xffffffffu, open);
-                    if (O == 0u) {
-                        node = I.y;
-                    } else if (I.x >> 8) {
-                        if (nc < cand_cap) {
-                            if (lane == 0) {
-                                cl[nc] = make_int2(I.z, I.w);
-                                cm[nc] = O;
-                            }
-                            ++nc;
-                        } else {
-                            overflow = true;
-                        }
-                        node = I.y;
-                    } else {
-                        if (lane == lev) lvlmask = O;
-                        node = node + 1;
-                    }
-                }
-                __syncwarp();
-                if (overflow) {
-                    if (lane == 0) evol_flag(d.err, EVOL_EOVERFLOW);
-                    break;
-                }
-                stale = false;
-                // ---- Newton / bisection on the cached list ----
-                for (;;) {
-                    const bool need = (status == ST_ACTIVE || status == ST_LAST) && !stale;
-                    if (!__any_sync(0xffffffffu, need)) break;
-                    float Sw = 0.f, Suw = 0.f, Smw = 0.f, Smuw = 0.f;
-                    const float Linv = need ? 1.f / L : 0.f;
-                    const float L2x4 = 4.f * L * L;
-                    for (int e = 0; e < nc; ++e) {
-                        const int2 rg = cl[e];
-                        const unsigned msk = cm[e];
-                        const bool mine = need && ((msk >> lane) & 1u);
-                        if (!__any_sync(0xffffffffu, mine)) continue;
-                        for (int j = rg.x; j < rg.y; ++j) {
-                            const float4 pj = d.pos[j];
-                            if (MODE == 0 && d.orig[j] >= kp.n_gas) continue;
-                            if (!mine) continue;
-                            float dx = evol_wrap(pi4.x - pj.x, plen[0], pm & 1);
-                            float dy = evol_wrap(pi4.y - pj.y, plen[1], pm & 2);
-                            float dz = evol_wrap(pi4.z - pj.z, plen[2], pm & 4);
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < L2x4) {
-                                const float u = sqrtf(r2) * Linv;
-                                float w, dw;
-                                evol_w_dw(u, w, dw);
-                                Sw += w;
-                                Suw += u * dw;
-                                if (MODE == 0) {
-                                    Smw += pj.w * w;
-                                    Smuw += pj.w * u * dw;
-                                } else {
-                                    Smw += pj.w * evol_dphideps(u);
-                                }
-                            }
-                        }
-                    }
-                    if (status == ST_LAST && !stale) {
-                        const float nsum = Sw * inv_pi * Linv * Linv * Linv;
-                        if (MODE == 0) {
-                            d.len_h[s] = L;
-                            d.nh[s] = nsum;
-                            d.rho[s] = Smw * inv_pi * Linv * Linv * Linv;
-                            d.omega[s] = -Suw / (3.f * Sw);
-                            d.zeta[s] = (3.f * Smw + Smuw) / (3.f * Sw);
-                        } else {
-                            d.len_eps[s] = L;
-                            d.neps[s] = nsum;
-                            d.ups[s] = -Suw / (3.f * Sw);
-                            d.X[s] = -EVOL_PI_F * L * L * Smw / (3.f * Sw);
-                        }
-                        status = ST_DONE;
-                    } else if (status == ST_ACTIVE && !stale) {
-                        ++iters;
-                        const float F = Sw * inv_pi - eta3;
-                        const float Fp = -Suw * inv_pi * Linv;
-                        if (F < 0.f) lo = L;
-                        if (F > 0.f) hi = L;
-                        float Ln;
-                        if (F == 0.f) {
-                            Ln = L;
-                        } else {
-                            Ln = Fp > 0.f ? L - F / Fp : (hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L);
-                            if (!(Ln > lo && Ln < hi)) Ln = hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L;
-                        }
-                        const bool conv = fabsf(Ln - L) <= CONV_TOL * L || (hi < INFINITY && hi - lo <= 1e-7f * hi);
-                        L = Ln;
-                        if (conv) status = ST_LAST;
-                        if (iters >= MAX_ITERS) {
-                            evol_flag(d.err, EVOL_ENOCONV);
-                            status = ST_LAST;
-                        }
-                        if (2.f * L >= Rc) stale = true;
-                        if (L > 4.f * side) {             // no root: fewer neighbours than required
-                            evol_flag(d.err, EVOL_ENOCONV);
-                            status = ST_DONE;
-                            stale = false;
-                            if (MODE == 0) d.len_h[s] = L; else d.len_eps[s] = L;
-                        }
-                    }
-                }
-            }
-            if (walks >= MAX_WALKS && __any_sync(0xffffffffu, status != ST_DONE)) {
+            if (walks >= MAX_WALKS) {
                 if (status != ST_DONE) evol_flag(d.err, EVOL_ENOCONV);
                 break;
             }
+            // ---- gather: the stale lanes collect the particles within their radius ----
+            if (__any_sync(0xffffffffu, stale)) {
+                ++walks;
+                if (stale) {
+                    Rc = 2.f * L * SEARCH_MARGIN;
+                    cnt = 0;
+                }
+                const bool coll = stale;
+                const float R2 = coll ? Rc * Rc : 0.f;
+                float rmax = coll ? Rc : 0.f, rmin = coll ? Rc : INFINITY;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+                    rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+                }
+                const unsigned rootmask = __ballot_sync(0xffffffffu, coll);
+                bool over = false;
+                bool broken = false;
+                int top = 1;
+                if (lane == 0) stk[0] = make_int2(0, (int)rootmask);
+                __syncwarp();
+                while (top > 0) {
+                    const int k = min(top, 32);
+                    top -= k;
+                    int node = -1;
+                    unsigned M = 0;
+                    if (lane < k) {
+                        const int2 e = stk[top + lane];
+                        node = e.x;
+                        M = (unsigned)e.y;
+                    }
+                    __syncwarp();
+                    int4 I = make_int4(0, 0, 0, 0);
+                    int cls = 0;              // 0 none/skip, 2 open all, 3 mixed
+                    unsigned Ok = 0;
+                    if (lane < k) {
+                        I = d.nI[node];
+                        const float4 B = d.nB[node];
+                        const float4 C = d.nC[node];
+                        if (MODE == 1 || B.w >= 0.f) {
+                            const float dx = fabsf(evol_wrap(B.x - gcx, plen0, pm & 1));
+                            const float dy = fabsf(evol_wrap(B.y - gcy, plen1, pm & 2));
+                            const float dz = fabsf(evol_wrap(B.z - gcz, plen2, pm & 4));
+                            const float nx = fmaxf(dx - (C.x + gwx), 0.f), ny = fmaxf(dy - (C.y + gwy), 0.f),
+                                        nz = fmaxf(dz - (C.z + gwz), 0.f);
+                            const float fx = fmaxf(dx + gwx - C.x, 0.f), fy = fmaxf(dy + gwy - C.y, 0.f),
+                                        fz = fmaxf(dz + gwz - C.z, 0.f);
+                            const float bnear2 = nx * nx + ny * ny + nz * nz, bfar2 = fx * fx + fy * fy + fz * fz;
+                            if (bnear2 >= rmax * rmax * (1.f + TAU)) {
+                                cls = 0;
+                            } else if (bfar2 < rmin * rmin * (1.f - TAU)) {
+                                cls = 2;
+                                Ok = M;
+                            } else {
+                                cls = 3;
+                            }
+                        }
+                        sm.bB[w][lane] = B;
+                        sm.bC[w][lane] = C;
+                    }
+                    __syncwarp();
+                    unsigned mm = __ballot_sync(0xffffffffu, cls == 3);
+                    while (mm) {
+                        const int kk = __ffs(mm) - 1;
+                        mm &= mm - 1u;
+                        const unsigned Mk = __shfl_sync(0xffffffffu, M, kk);
+                        bool open = false;
+                        if ((Mk >> lane) & 1u) {
+                            const float4 B = sm.bB[w][kk];
+                            const float4 C = sm.bC[w][kk];
+                            float ex = fabsf(evol_wrap(pi4.x - B.x, plen0, pm & 1)) - C.x;
+                            float ey = fabsf(evol_wrap(pi4.y - B.y, plen1, pm & 2)) - C.y;
+                            float ez = fabsf(evol_wrap(pi4.z - B.z, plen2, pm & 4)) - C.z;
+                            ex = fmaxf(ex, 0.f); ey = fmaxf(ey, 0.f); ez = fmaxf(ez, 0.f);
+                            open = ex * ex + ey * ey + ez * ez < R2;
+                        }
+                        const unsigned Of = __ballot_sync(0xffffffffu, open);
+                        if (lane == kk) Ok = Of;
+                    }
+                    // opened leaves: gather their particles into the lanes' lists
+                    const bool isleaf = (I.x >> 8) & 1;
+                    unsigned lm = __ballot_sync(0xffffffffu, Ok != 0u && isleaf);
+                    while (lm) {
+                        const int kk = __ffs(lm) - 1;
+                        lm &= lm - 1u;
+                        const unsigned ok = __shfl_sync(0xffffffffu, Ok, kk);
+                        const int b0 = __shfl_sync(0xffffffffu, I.z, kk);
+                        const int e0 = __shfl_sync(0xffffffffu, I.w, kk);
+                        const bool mine = (ok >> lane) & 1u;
+                        for (int j = b0; j < e0; ++j) {
+                            const float4 pj = d.pos[j];
+                            if (MODE == 0 && d.orig[j] >= kp.n_gas) continue;
+                            if (!mine) continue;
+                            const float dx = evol_wrap(pi4.x - pj.x, plen0, pm & 1);
+                            const float dy = evol_wrap(pi4.y - pj.y, plen1, pm & 2);
+                            const float dz = evol_wrap(pi4.z - pj.z, plen2, pm & 4);
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < R2) {
+                                if (cnt < list_cap) lst[(size_t)cnt * 32 + lane] = make_float2(sqrtf(r2), pj.w);
+                                else over = true;
+                                ++cnt;
+                            }
+                        }
+                    }
+                    // opened internal nodes: push children
+                    const bool io = Ok != 0u && !isleaf;
+                    int nch = 0;
+                    int ch[8];
+                    if (io) {
+                        const int4 K0 = d.nK0[node], K1 = d.nK1[node];
+                        ch[0] = K0.x; ch[1] = K0.y; ch[2] = K0.z; ch[3] = K0.w;
+                        ch[4] = K1.x; ch[5] = K1.y; ch[6] = K1.z; ch[7] = K1.w;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) nch += ch[q] >= 0 ? 1 : 0;
+                    }
+                    int incl = nch;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += t;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, incl, 31);
+                    if (top + total > kp.stack_cap) {
+                        if (lane == 0) evol_flag(d.err, EVOL_EOVERFLOW);
+                        broken = true;
+                        break;
+                    }
+                    if (io) {
+                        const int pos = top + incl - nch;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            if (q < nch) stk[pos + q] = make_int2(ch[q], (int)Ok);
+                    }
+                    top += total;
+                    __syncwarp();
+                }
+                if (broken) break;
+                stale = false;
+                if (over) {
+                    // more neighbours than the list holds: the radius is too large; shrink, gather again
+                    float Ln = 0.75f * L;
+                    if (Ln <= lo) Ln = 0.5f * (lo + L);
+                    L = Ln;
+                    stale = true;
+                    cnt = 0;
+                }
+            }
+            // ---- Newton / bisection on the private lists ----
+            for (;;) {
+                const bool need = (status == ST_ACTIVE || status == ST_LAST) && !stale;
+                if (!__any_sync(0xffffffffu, need)) break;
+                float Sw = 0.f, Suw = 0.f, Smw = 0.f, Smuw = 0.f;
+                const float Linv = need ? 1.f / L : 0.f;
+                const float twoL = 2.f * L;
+                const int my = need ? cnt : 0;
+                int mx = my;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                for (int e = 0; e < mx; ++e) {
+                    if (e < my) {
+                        const float2 rm = lst[(size_t)e * 32 + lane];
+                        if (rm.x < twoL) {
+                            const float u = rm.x * Linv;
+                            float wv, dw;
+                            evol_w_dw(u, wv, dw);
+                            Sw += wv;
+                            Suw += u * dw;
+                            if (MODE == 0) {
+                                Smw += rm.y * wv;
+                                Smuw += rm.y * u * dw;
+                            } else {
+                                Smw += rm.y * evol_dphideps(u);
+                            }
+                        }
+                    }
+                }
+                if (status == ST_LAST && !stale) {
+                    const float nsum = Sw * inv_pi * Linv * Linv * Linv;
+                    if (MODE == 0) {
+                        d.len_h[s] = L;
+                        d.nh[s] = nsum;
+                        d.rho[s] = Smw * inv_pi * Linv * Linv * Linv;
+                        d.omega[s] = -Suw / (3.f * Sw);
+                        d.zeta[s] = (3.f * Smw + Smuw) / (3.f * Sw);
+                    } else {
+                        d.len_eps[s] = L;
+                        d.neps[s] = nsum;
+                        d.ups[s] = -Suw / (3.f * Sw);
+                        d.X[s] = -EVOL_PI_F * L * L * Smw / (3.f * Sw);
+                    }
+                    status = ST_DONE;
+                } else if (status == ST_ACTIVE && !stale) {
+                    ++iters;
+                    const float F = Sw * inv_pi - eta3;
+                    const float Fp = -Suw * inv_pi * Linv;
+                    if (F < 0.f) lo = L;
+                    if (F > 0.f) hi = L;
+                    float Ln;
+                    if (F == 0.f) {
+                        Ln = L;
+                    } else {
+                        Ln = Fp > 0.f ? L - F / Fp : (hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L);
+                        if (!(Ln > lo && Ln < hi)) Ln = hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L;
+                    }
+                    const bool conv = fabsf(Ln - L) <= CONV_TOL * L || (hi < INFINITY && hi - lo <= 1e-7f * hi);
+                    L = Ln;
+                    if (conv) status = ST_LAST;
+                    if (iters >= MAX_ITERS) {
+                        evol_flag(d.err, EVOL_ENOCONV);
+                        status = ST_LAST;
+                    }
+                    if (2.f * L >= Rc) stale = true;
+                    if (L > 4.f * side) {             // no root: fewer neighbours than required
+                        evol_flag(d.err, EVOL_ENOCONV);
+                        status = ST_DONE;
+                        stale = false;
+                        if (MODE == 0) d.len_h[s] = L; else d.len_eps[s] = L;
+                    }
+                }
+            }
         }
-        // iteration count for the diagnostics
         int it = iters;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) it += __shfl_xor_sync(0xffffffffu, it, o);
@@ -223,6 +337,7 @@ int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params 
     kp.eta_e = 0.5f * cbrtf(3.f * prm->n_nei_grav / (4.f * EVOL_PI_F));
     kp.periodic_mask = prm->periodic_mask;
     for (int a = 0; a < 3; ++a) kp.plen[a] = prm->periodic_hi[a] - prm->periodic_lo[a];
+    kp.stack_cap = (int)c->wstack_cap;
     unsigned long long *q = c->d.counters + (mode == 0 ? 5 : 6);
     cudaMemsetAsync(q, 0, sizeof(unsigned long long), c->stream);
     int blocks = (int)(c->cand_slots / LW_WARPS);
