@@ -59,7 +59,7 @@ def make_workload(name: str):
     if name == "c4":
         return W.shock_tube(seed=4), "shock_tube_1046250_periodic_yz"
     if name == "c5":
-        return W.ensemble(64, seed=5), "ensemble_64_spheres"
+        return W.ensemble(64, seed=5), "ensemble_64_spheres_N_2^10..2^17"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -216,6 +216,69 @@ def run_reference(args):
     return 0
 
 
+def time_steps(torch, dev, stream, fn, steps):
+    """CUDA-event time of `steps` calls of fn on `stream` (ms)."""
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        fn()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    return t0.elapsed_time(t1)
+
+
+def other_forms(torch, dev, stream, E, DeviceSet, w, steps, precision_used, leaf):
+    """Throughput of the other precision form (same workload) and, for an ensemble, of one
+    launch per system; particles/s each."""
+    forms = {}
+    other = E.EVOL_FP32_MIXED if precision_used == E.EVOL_FP32_PLAIN else E.EVOL_FP32_PLAIN
+    ds = DeviceSet(w, device=str(dev), precision=other)
+    ds.params.leaf_size = leaf
+    ctx = E.evol_create(w.n, stream.cuda_stream)
+    try:
+        if w.sys_offsets is not None:
+            offs = [int(v) for v in w.sys_offsets]
+            run = lambda: (ds.reset_lengths(), E.evol_step_batched(ctx, offs, ds.particles, ds.params, ds.outputs))
+        else:
+            run = lambda: (ds.reset_lengths(), E.evol_step(ctx, ds.particles, ds.params, ds.outputs))
+        for _ in range(2):
+            run()
+        E.evol_sync(ctx)
+        ms = time_steps(torch, dev, stream, run, steps)
+        E.evol_sync(ctx)
+        forms["mixed" if other == E.EVOL_FP32_MIXED else "plain"] = w.n * steps / (ms / 1e3)
+    finally:
+        E.evol_destroy(ctx)
+    if w.sys_offsets is not None:
+        # the same ensemble as one evol_step per system, each on its own slice of the arrays
+        from paper_0912_1786_gb300 import evol as E2
+        ds = DeviceSet(w, device=str(dev), precision=precision_used)
+        ds.params.leaf_size = leaf
+        offs = [int(v) for v in w.sys_offsets]
+        ctxs, parts = [], []
+        try:
+            for k in range(len(offs) - 1):
+                b, e = offs[k], offs[k + 1]
+                arr = {key: (t[b:e] if key not in ("u", "h") or e <= w.n_gas else t[b:min(e, w.n_gas)])
+                       for key, t in ds.inp.items()}
+                outs = {key: t[b:e] for key, t in ds.out.items()}
+                ctxs.append(E2.evol_create(max(e - b, 1), stream.cuda_stream))
+                parts.append((E2.make_particles(e - b, e - b, arr), E2.make_outputs(outs)))
+            run = lambda: [E2.evol_step(c, pp, ds.params, oo) for c, (pp, oo) in zip(ctxs, parts)]
+            for _ in range(2):
+                ds.reset_lengths()
+                run()
+            torch.cuda.synchronize(dev)
+            ms = time_steps(torch, dev, stream, lambda: (ds.reset_lengths(), run()), steps)
+            forms["per_system_launches"] = w.n * steps / (ms / 1e3)
+        finally:
+            for c in ctxs:
+                E2.evol_destroy(c)
+    return forms
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,6 +289,8 @@ def main():
     ap.add_argument("--precision", default="plain", choices=["plain", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -257,10 +322,20 @@ def main():
     ds = DeviceSet(w, device=str(dev), precision=prec)
     stream = torch.cuda.current_stream(dev)
     ctx = E.evol_create(w.n, stream.cuda_stream)
+    autotune = None
+    if not args.no_autotune and w.sys_offsets is None:
+        best, ms = E.evol_autotune(ctx, ds.particles, ds.params, ds.outputs, candidates=[8, 12, 16, 24, 32], reps=2)
+        ds.params.leaf_size = best
+        autotune = {"leaf_size": best, "median_ms_by_leaf": ms}
+
+    offsets = [int(v) for v in w.sys_offsets] if w.sys_offsets is not None else None
 
     def one_step():
         ds.reset_lengths()
-        E.evol_step(ctx, ds.particles, ds.params, ds.outputs)
+        if offsets is not None:
+            E.evol_step_batched(ctx, offsets, ds.particles, ds.params, ds.outputs)
+        else:
+            E.evol_step(ctx, ds.particles, ds.params, ds.outputs)
 
     for _ in range(args.warmup):
         one_step()
@@ -330,6 +405,11 @@ def main():
         e2e = {"value": n_total * ke / te, "unit": "particles/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ke}
 
+    forms = {args.precision if offsets is None else f"batched_{args.precision}": value}
+    if not args.no_forms:
+        forms.update(other_forms(torch, dev, stream, E, DeviceSet, w, max(2, min(args.steps, 5)), prec,
+                                 int(ds.params.leaf_size)))
+
     # ---- roofline of the dominant kernel (the force walk) ----
     far, pp, sph = diag[12], diag[13], diag[14]
     flops = far * FLOPS_FAR + pp * FLOPS_PP + sph * FLOPS_SPH
@@ -363,13 +443,15 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "precision": args.precision, "data": "synthetic",
                 "config": {"workload": wname, "n": w.n, "n_gas": w.n_gas, "theta": w.params.theta,
-                           "n_nei": w.params.n_nei_sph, "leaf_size": w.params.leaf_size,
+                           "n_nei": w.params.n_nei_sph, "leaf_size": int(ds.params.leaf_size),
+                "autotune": autotune,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "working set > L2 (inputs 40 B/particle x 3.1M + tree), no flush"},
                 "phase_ms": {"build": ph[0], "eps_solve": ph[1], "h_solve": ph[2], "walk": ph[3], "total": ph[4]},
                 "interactions_per_s": {"far": far / walk_s, "pp": pp / walk_s, "sph": sph / walk_s},
                 "length_iterations_per_particle": diag[15] / max(1, w.n + w.n_gas),
                 "status_last_step": rc,
+                "forms_particles_per_s": forms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": None}
         line["gpu_launches"] = launches_per_step(w) * args.steps

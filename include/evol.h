@@ -132,11 +132,40 @@ int evol_sph_forces(evol_ctx *ctx, const evol_particles *p, const evol_params *p
  * and replayed afterwards; no host synchronisation inside. */
 int evol_step(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outputs *out);
 
+/* Batched step over nsys independent systems (no forces between systems): the particles of
+ * system k are positions [sys_offsets[k], sys_offsets[k+1]) of every per-particle array
+ * (sys_offsets: HOST array of nsys + 1 values, 0 = sys_offsets[0] <= ... <= sys_offsets[nsys] = n;
+ * gas still means the first n_gas particles overall).  Each system gets its own root cube and
+ * tree, exactly as evol_step would build for it alone; all systems go through the same kernel
+ * launches (one per phase, CUDA-graph captured per nsys).  1 <= nsys <= 65536, else EVOL_EINVAL.
+ * Synchronises the context stream on entry (the offsets are staged in pinned host memory). */
+int evol_step_batched(evol_ctx *ctx, const int64_t *sys_offsets, int nsys, evol_particles *p,
+                      const evol_params *prm, evol_outputs *out);
+
+/* Kick-drift-kick leapfrog with a fixed step dt (Sect. 4.1): one force step at the start, then
+ * nsteps times: v += a dt/2 (and u += du/dt dt/2 for gas); x += v dt (periodic axes wrapped
+ * into [periodic_lo, periodic_hi)); force step; v += a dt/2, u += du/dt dt/2.  The particle
+ * arrays x, y, z, vx, vy, vz and u are updated IN PLACE, so they must be writable device
+ * memory despite their const qualifiers; h and eps carry over as the next step's starting
+ * guesses.  out receives the outputs of the last force step (any field may be NULL).  One KDK
+ * step (kicks, drift and the force phases) is recorded into CUDA graphs once and replayed
+ * nsteps times.  Returns EVOL_EINVAL for nsteps < 0 or dt not finite. */
+int evol_kdk(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outputs *out, float dt, int nsteps);
+
 /* evol_step on HOST buffers: copies the inputs host -> device into context-owned buffers,
  * runs the step and copies every non-NULL output (and h, eps) back, then synchronises.
  * The particle and output pointers of this call are host pointers (pinned memory is
  * fastest).  Returns the step status (as evol_sync). */
 int evol_step_host(evol_ctx *ctx, evol_particles *p_host, const evol_params *prm, evol_outputs *out_host);
+
+/* Autotuner for the cost parameters of the step (never theta or the neighbour numbers): times
+ * evol_step on these particles for each candidate leaf size and returns the fastest in
+ * *best_leaf.  candidates: host array of ncand leaf sizes in 1..64 (NULL: {4, 8, 12, 16, 24, 32});
+ * reps >= 1 timed steps per candidate after one untimed step; ms_out (host, ncand floats, may be
+ * NULL) receives each candidate's median step time.  The particles' h and eps are overwritten
+ * by the solved lengths as in evol_step; out receives the last run's results.  Synchronous. */
+int evol_autotune(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outputs *out,
+                  const int *candidates, int ncand, int reps, int *best_leaf, float *ms_out);
 
 /* Wait for the context stream and return the first device-side error recorded since the
  * previous evol_sync (then clear it), or EVOL_OK. */

@@ -242,3 +242,43 @@ def force_step(w, params=None, idx=None, use_tc=None, tree=None, fixed_lengths=N
     res["tree"] = t
     res["state"] = st
     return res
+
+
+def kdk(w, dt: float, nsteps: int, params=None):
+    """Kick-drift-kick leapfrog with a fixed step (Sect. 4.1) in FP64 on top of force_step.
+
+    The state (x, v, u) is kept in double precision; each force evaluation receives it rounded to
+    float32, the oracle's input type.  Periodic axes are wrapped into [lo, hi).  Returns a dict
+    with x, y, z, vx, vy, vz, u (float64) and the last force-step result."""
+    import copy
+
+    p = params or w.params
+    n, ng = w.n, w.n_gas
+    X = np.stack([w.x, w.y, w.z], 1).astype(np.float64)
+    V = np.stack([w.vx, w.vy, w.vz], 1).astype(np.float64)
+    U = w.u.astype(np.float64).copy()
+    cur = copy.copy(w)
+
+    def forces():
+        cur.x, cur.y, cur.z = (np.ascontiguousarray(X[:, a], np.float32) for a in range(3))
+        cur.vx, cur.vy, cur.vz = (np.ascontiguousarray(V[:, a], np.float32) for a in range(3))
+        cur.u = np.ascontiguousarray(U, np.float32)
+        r = force_step(cur, params=p)
+        A = np.stack([r["ax"], r["ay"], r["az"]], 1)
+        return A, r["dudt"], r
+
+    A, DU, r = forces()
+    lo = np.asarray(getattr(p, "periodic_lo", (0, 0, 0)), np.float64)
+    hi = np.asarray(getattr(p, "periodic_hi", (1, 1, 1)), np.float64)
+    for _ in range(nsteps):
+        V += 0.5 * dt * A
+        U[:ng] += 0.5 * dt * DU[:ng]
+        X += dt * V
+        for a in range(3):
+            if (getattr(p, "periodic_mask", 0) >> a) & 1:
+                X[:, a] = lo[a] + np.mod(X[:, a] - lo[a], hi[a] - lo[a])
+        A, DU, r = forces()
+        V += 0.5 * dt * A
+        U[:ng] += 0.5 * dt * DU[:ng]
+    return {"x": X[:, 0], "y": X[:, 1], "z": X[:, 2], "vx": V[:, 0], "vy": V[:, 1], "vz": V[:, 2], "u": U,
+            "last": r}

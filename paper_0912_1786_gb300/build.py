@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import os
+import re
 import subprocess
 from concurrent.futures import ThreadPoolExecutor
 
@@ -14,6 +15,23 @@ SOURCES = ["evol_api.cu", "tree.cu", "lengths.cu", "walk.cu", "post.cu", "noallo
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# sources whose kernels must compile without a local-memory stack frame (register spills): the
+# force walk's single-physics variants that spilled faulted on GB300, so a spilling build is refused
+NO_SPILL = {"walk.cu": "k_walk"}
+
+
+def _spilling_kernels(ptxas_log: str, prefix: str):
+    """Kernels named like `prefix` with a non-zero stack frame in a `-Xptxas -v` log."""
+    bad, name = [], None
+    for line in ptxas_log.splitlines():
+        m = re.search(r"Compiling entry function '([^']+)'", line)
+        if m:
+            name = m.group(1)
+            continue
+        m = re.search(r"(\d+) bytes stack frame", line)
+        if m and name and prefix in name and int(m.group(1)) > 0:
+            bad.append((name, int(m.group(1))))
+    return bad
 
 
 def _deps():
@@ -39,10 +57,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(OBJDIR, src.replace(".cu", ".o"))
-        cmd = [NVCC, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        check = ["-Xptxas", "-v"] if src in NO_SPILL else []
+        cmd = [NVCC, *ARCH, *FLAGS, *check, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        if src in NO_SPILL:
+            bad = _spilling_kernels(r.stdout + r.stderr, NO_SPILL[src])
+            if bad:
+                raise RuntimeError(f"{src}: kernels compiled with a local-memory stack frame: {bad}")
         if verbose and (r.stdout or r.stderr):
             print(r.stdout, r.stderr)
         return obj

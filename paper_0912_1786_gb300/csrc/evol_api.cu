@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "evol_internal.cuh"
@@ -13,12 +14,16 @@
 int evol_launch_pack(evol_ctx *c, const evol_particles *p, const evol_params *prm, int do_grav, int do_sph);
 int evol_launch_unpermute_ex(evol_ctx *c, const evol_particles *p, const evol_outputs *o, int what, int add_acc);
 int evol_lengths_warps_per_block();
+int evol_launch_kick(evol_ctx *c, const evol_particles *p, float half_dt, const float *ax, const float *ay,
+                     const float *az, const float *dudt);
+int evol_launch_drift(evol_ctx *c, const evol_particles *p, const evol_params *prm, float dt);
 
 namespace {
 
 constexpr int64_t CAND_CAP = 192;        // neighbour-list entries per lane in the length solve
 constexpr int64_t NODE_FACTOR = 3;       // node capacity = 3 * particles + 64
 constexpr int64_t WSTACK_CAP = 4096;     // traversal stack entries per warp in the force walk
+constexpr int NSYS_CAP = 65536;          // independent systems per batched call
 
 template <typename T>
 int dalloc(T **p, size_t count)
@@ -36,13 +41,15 @@ void free_all(evol_ctx *c)
                     d.hist, d.lcp, d.cnt, d.base, d.scan_part, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
                     d.nnch, d.narrive, d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nM64, d.nC64, d.nQ64, d.nBmin,
                     d.nBmax, d.nI, d.nK0, d.nK1, d.wstack, d.cand_leaf, d.cand_mask, d.diag_part, d.diag, d.counters, d.err, d.nnodes,
-                    d.cube, d.fcube, d.bbox_part, d.hash3, d.cnt3, c->stage};
+                    d.cube, d.fcube, d.bbox_part, d.hash3, d.cnt3, c->stage, c->kdk_acc, d.sys_off, d.sys_root, d.sys_sorted};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 6; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->h_sys_off) cudaFreeHost(c->h_sys_off);
     for (int k = 0; k < 8; ++k)
         if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
+    if (c->kdk_exec) cudaGraphExecDestroy(c->kdk_exec);
 }
 
 int check_args(evol_ctx *c, const evol_particles *p, const evol_params *prm)
@@ -89,7 +96,9 @@ void reset_counters(evol_ctx *c)
 
 int ensure_tree(evol_ctx *c, const evol_particles *p, const evol_params *prm)
 {
-    if (c->built_n == p->n && c->built_ngas == p->n_gas && c->built_x == (const void *)p->x) return EVOL_OK;
+    if (c->built_n == p->n && c->built_ngas == p->n_gas && c->built_x == (const void *)p->x && c->nsys == 1)
+        return EVOL_OK;
+    c->nsys = 1;
     int rc = evol_launch_build(c, p, prm);
     if (rc) return rc;
     c->built_n = p->n;
@@ -182,7 +191,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     c->diag_blocks = c->num_sms * 2;
     c->cand_cap = CAND_CAP;
     c->cand_slots = (int64_t)c->num_sms * 6 * evol_lengths_warps_per_block();
-    c->wstack_slots = (int64_t)c->num_sms * 64;      // at most 64 resident warps per SM
+    c->wstack_slots = (int64_t)c->num_sms * 32;      // the walk and length grids use at most 32 warps per SM
     c->wstack_cap = WSTACK_CAP;
     int64_t n = max_n, nn = c->node_cap;
     int64_t scan_parts = (256 * c->sort_blocks > n + 1 ? 256 * c->sort_blocks : n + 1) / 4096 + 2;
@@ -208,9 +217,14 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.cand_mask, 1);
     rc |= dalloc(&d.diag_part, 16 * c->diag_blocks); rc |= dalloc(&d.diag, 16);
     rc |= dalloc(&d.counters, 8); rc |= dalloc(&d.err, 1); rc |= dalloc(&d.nnodes, 1);
-    rc |= dalloc(&d.cube, 4); rc |= dalloc(&d.fcube, 4); rc |= dalloc(&d.bbox_part, 6 * c->bbox_blocks);
+    c->nsys_cap = NSYS_CAP;
+    rc |= dalloc(&d.cube, 4 * (int64_t)NSYS_CAP); rc |= dalloc(&d.fcube, 4 * (int64_t)NSYS_CAP);
+    rc |= dalloc(&d.bbox_part, 6 * c->bbox_blocks);
+    rc |= dalloc(&d.sys_off, NSYS_CAP + 1); rc |= dalloc(&d.sys_root, NSYS_CAP); rc |= dalloc(&d.sys_sorted, n);
+    if (!rc && cudaMallocHost((void **)&c->h_sys_off, (NSYS_CAP + 1) * sizeof(int32_t)) != cudaSuccess) rc = EVOL_ENOMEM;
     rc |= dalloc(&d.hash3, 3 * n); rc |= dalloc(&d.cnt3, 3 * n);
     rc |= dalloc(&c->stage, 24 * n);
+    rc |= dalloc(&c->kdk_acc, 4 * n);
     for (int k = 0; k < 6 && !rc; ++k)
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) rc = EVOL_ECUDA;
     if (!rc) {
@@ -299,13 +313,12 @@ int evol_sph_forces(evol_ctx *c, const evol_particles *p, const evol_params *prm
     return EVOL_OK;
 }
 
-int evol_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out)
+static int run_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out)
 {
-    int rc = check_args(c, p, prm);
-    if (rc || p->n == 0) return rc;
     evol_outputs zero{};
     if (!out) out = &zero;
     uint64_t sig = 1469598103934665603ull;
+    sig = fnv(sig, &c->nsys, sizeof c->nsys);
     sig = fnv(sig, p, sizeof *p);
     sig = fnv(sig, prm, sizeof *prm);
     sig = fnv(sig, out, sizeof *out);
@@ -369,6 +382,110 @@ int evol_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outpu
     return EVOL_OK;
 }
 
+int evol_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out)
+{
+    int rc = check_args(c, p, prm);
+    if (rc || p->n == 0) return rc;
+    c->nsys = 1;
+    return run_step(c, p, prm, out);
+}
+
+int evol_step_batched(evol_ctx *c, const int64_t *sys_offsets, int nsys, evol_particles *p, const evol_params *prm,
+                      evol_outputs *out)
+{
+    int rc = check_args(c, p, prm);
+    if (rc) return rc;
+    if (!sys_offsets || nsys < 1 || nsys > c->nsys_cap) return EVOL_EINVAL;
+    if (sys_offsets[0] != 0 || sys_offsets[nsys] != p->n) return EVOL_EINVAL;
+    for (int k = 0; k < nsys; ++k)
+        if (sys_offsets[k + 1] < sys_offsets[k]) return EVOL_EINVAL;
+    if (p->n == 0) return EVOL_OK;
+    // the previous call's copy may still be in flight from the pinned staging buffer
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return set_err(c, EVOL_ECUDA);
+    for (int k = 0; k <= nsys; ++k) c->h_sys_off[k] = (int32_t)sys_offsets[k];
+    if (cudaMemcpyAsync(c->d.sys_off, c->h_sys_off, (nsys + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess)
+        return set_err(c, EVOL_ECUDA);
+    c->nsys = nsys;
+    return run_step(c, p, prm, out);
+}
+
+int evol_kdk(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out, float dt, int nsteps)
+{
+    int rc = check_args(c, p, prm);
+    if (rc || (p && p->n == 0)) return rc;
+    if (nsteps < 0 || !(dt == dt) || dt > 3.0e38f || dt < -3.0e38f) return EVOL_EINVAL;
+    if (!p->vx || !p->vy || !p->vz) return EVOL_EINVAL;
+    const int64_t cap = c->cap;
+    evol_outputs o = out ? *out : evol_outputs{};
+    o.ax = c->kdk_acc;
+    o.ay = c->kdk_acc + cap;
+    o.az = c->kdk_acc + 2 * cap;
+    o.dudt = c->kdk_acc + 3 * cap;
+    // forces at the starting positions
+    if ((rc = evol_step(c, p, prm, &o))) return rc;
+    if (nsteps > 0) {
+        uint64_t sig = 88172645463325252ull;
+        sig = fnv(sig, p, sizeof *p);
+        sig = fnv(sig, prm, sizeof *prm);
+        sig = fnv(sig, &o, sizeof o);
+        sig = fnv(sig, &dt, sizeof dt);
+        sig = fnv(sig, &c->check_mode, sizeof c->check_mode);
+        sig = fnv(sig, &c->stream, sizeof c->stream);
+        if (!c->kdk_exec || sig != c->kdk_sig) {
+            if (c->kdk_exec) {
+                cudaGraphExecDestroy(c->kdk_exec);
+                c->kdk_exec = nullptr;
+            }
+            cudaStream_t cap_stream = c->stream;
+            bool own = false;
+            if (!cap_stream) {
+                if (cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+                    return set_err(c, EVOL_ECUDA);
+                own = true;
+            }
+            cudaStream_t saved = c->stream;
+            c->stream = cap_stream;
+            cudaGraph_t graph = nullptr;
+            int prc = EVOL_OK;
+            if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                prc = EVOL_ECUDA;
+            } else {
+                prc = evol_launch_kick(c, p, 0.5f * dt, o.ax, o.ay, o.az, o.dudt);
+                if (!prc) prc = evol_launch_drift(c, p, prm, dt);
+                for (int k = 0; k < NPHASE && !prc; ++k) prc = record_phase(c, k, p, prm, &o);
+                if (!prc) prc = evol_launch_kick(c, p, 0.5f * dt, o.ax, o.ay, o.az, o.dudt);
+                cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
+                if (!prc && (e != cudaSuccess || !graph)) prc = EVOL_ECUDA;
+                if (!prc && cudaGraphInstantiate(&c->kdk_exec, graph, 0) != cudaSuccess) {
+                    c->kdk_exec = nullptr;
+                    prc = EVOL_ECUDA;
+                }
+            }
+            if (graph) cudaGraphDestroy(graph);
+            c->stream = saved;
+            if (own) cudaStreamDestroy(cap_stream);
+            if (prc) {
+                cudaGetLastError();
+                return set_err(c, prc);
+            }
+            c->kdk_sig = sig;
+        }
+        for (int k = 0; k < nsteps; ++k)
+            if (cudaGraphLaunch(c->kdk_exec, c->stream) != cudaSuccess) return set_err(c, EVOL_ECUDA);
+    }
+    // hand the last accelerations and du/dt to the caller
+    const int64_t n = p->n, ng = p->n_gas;
+    float *dst[4] = {out ? out->ax : nullptr, out ? out->ay : nullptr, out ? out->az : nullptr,
+                     out ? out->dudt : nullptr};
+    const float *src[4] = {o.ax, o.ay, o.az, o.dudt};
+    const int64_t len[4] = {n, n, n, ng};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k] && len[k] > 0)
+            cudaMemcpyAsync(dst[k], src[k], len[k] * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    return EVOL_OK;
+}
+
 int evol_step_host(evol_ctx *c, evol_particles *ph, const evol_params *prm, evol_outputs *oh)
 {
     int rc = check_args(c, ph, prm);
@@ -409,6 +526,60 @@ int evol_step_host(evol_ctx *c, evol_particles *ph, const evol_params *prm, evol
     if (ph->h && ng > 0) cudaMemcpyAsync(ph->h, in[8], ng * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
     if (ph->eps) cudaMemcpyAsync(ph->eps, in[9], n * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
     return evol_sync(c);
+}
+
+int evol_autotune(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out,
+                  const int *candidates, int ncand, int reps, int *best_leaf, float *ms_out)
+{
+    static const int defaults[6] = {4, 8, 12, 16, 24, 32};
+    int rc = check_args(c, p, prm);
+    if (rc) return rc;
+    if (!best_leaf || reps < 1 || (candidates && ncand < 1)) return EVOL_EINVAL;
+    if (!candidates) {
+        candidates = defaults;
+        ncand = 6;
+    }
+    for (int k = 0; k < ncand; ++k)
+        if (candidates[k] < 1 || candidates[k] > 64) return EVOL_EINVAL;
+    if (p->n == 0) {
+        *best_leaf = candidates[0];
+        return EVOL_OK;
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return EVOL_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return EVOL_ECUDA;
+    }
+    float best = 3.0e38f;
+    int best_k = 0;
+    std::vector<float> t(reps);
+    for (int k = 0; k < ncand && !rc; ++k) {
+        evol_params q = *prm;
+        q.leaf_size = candidates[k];
+        if ((rc = evol_step(c, p, &q, out))) break;           // records the graphs for this leaf size
+        if ((rc = evol_sync(c))) break;
+        for (int r = 0; r < reps && !rc; ++r) {
+            cudaEventRecord(e0, c->stream);
+            rc = evol_step(c, p, &q, out);
+            cudaEventRecord(e1, c->stream);
+            if (!rc) rc = evol_sync(c);
+            if (!rc && cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess) rc = EVOL_ECUDA;
+        }
+        if (rc) break;
+        std::vector<float> srt(t);
+        std::sort(srt.begin(), srt.end());
+        const float med = srt[reps / 2];
+        if (ms_out) ms_out[k] = med;
+        if (med < best) {
+            best = med;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) *best_leaf = candidates[best_k];
+    return rc;
 }
 
 int evol_sync(evol_ctx *c)

@@ -37,7 +37,7 @@ struct evol_dev {
     int32_t *vals_a, *vals_b;
     uint32_t *hist;          // 256 * nblocks
     // tree construction
-    uint8_t *lcp;            // d_i: common octal digits of keys i-1, i
+    int8_t *lcp;             // d_i: common octal digits of keys i-1, i (-1: i starts a system)
     int32_t *cnt, *base;     // nodes beginning at each sorted position, and its exclusive scan
     int32_t *scan_part;      // scan block partials
     // nodes (pre-order)
@@ -61,8 +61,11 @@ struct evol_dev {
     unsigned long long *counters;   // [0] far [1] pp [2] sph [3] iters [4] work queue [5] q2 [6] q3
     int *err;
     int32_t *nnodes;         // device node count
-    double *cube;            // corner x, y, z, side
-    float *fcube;            // corner x, y, z (float), side (float)
+    double *cube;            // corner x, y, z, side of every system (4 per system)
+    float *fcube;            // the same in float
+    int32_t *sys_off;        // system offsets (nsys + 1), sorted order keeps systems contiguous
+    int32_t *sys_sorted;     // system of each sorted position
+    int32_t *sys_root;       // root node of each system
     float *bbox_part;        // per-block min/max partials
     // check mode
     unsigned long long *hash3;   // 3 per particle (sorted)
@@ -84,6 +87,9 @@ struct evol_ctx {
     int check_mode;
     // state of the last build / density
     int64_t built_n, built_ngas;
+    int nsys;                // systems of the current particle set (1 unless batched)
+    int nsys_cap;
+    int32_t *h_sys_off;      // pinned host staging of the system offsets
     const void *built_x;
     int density_done, eps_done;
     // graph cache for evol_step
@@ -93,10 +99,14 @@ struct evol_ctx {
     cudaEvent_t ev[6];
     // host staging for evol_step_host (device buffers)
     float *stage;            // 10 * cap floats (inputs) + 14 * cap floats (outputs)
+    // leapfrog: accelerations and du/dt in caller order, and the recorded KDK step
+    float *kdk_acc;
+    cudaGraphExec_t kdk_exec;
+    uint64_t kdk_sig;
 };
 
 // ---- host-side launch helpers (defined in evol_api.cu / tree.cu / walks) ------------------
-int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *prm);
+int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *prm);   // uses c->nsys
 int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params *prm, int mode);
 int evol_launch_walk(evol_ctx *c, const evol_particles *p, const evol_params *prm, int do_grav, int do_sph);
 int evol_launch_node_lengths(evol_ctx *c, const evol_params *prm, int n_gas);
@@ -186,4 +196,5 @@ struct evol_kparams {
     float plen[3];
     int n, n_gas, leaf;
     int stack_cap;
+    int nsys;
 };

@@ -33,9 +33,14 @@ constexpr float TAU = 1e-5f;          // safety margin of the group-level bounds
 
 enum { ST_DONE = 0, ST_ACTIVE = 1, ST_LAST = 2 };
 
+constexpr int GCAP = 64;              // staged leaf particles per warp
+
 struct LenSmem {
     float4 bB[LW_WARPS][32];
     float4 bC[LW_WARPS][32];
+    int gj[LW_WARPS][GCAP];           // staged particle index
+    unsigned gmask[LW_WARPS][GCAP];   // lanes that opened its leaf
+    float4 gp[LW_WARPS][GCAP];        // position, mass (mass < 0: excluded species)
 };
 
 template <int MODE>
@@ -55,7 +60,6 @@ __global__ void __launch_bounds__(LW_THREADS, 6) k_lengths(evol_dev d, evol_kpar
     const float inv_pi = 1.f / EVOL_PI_F;
     const float plen0 = kp.plen[0], plen1 = kp.plen[1], plen2 = kp.plen[2];
     const int pm = kp.periodic_mask;
-    const float side = d.fcube[3];
 
     for (;;) {
         int g = 0;
@@ -67,6 +71,7 @@ __global__ void __launch_bounds__(LW_THREADS, 6) k_lengths(evol_dev d, evol_kpar
         const float4 pi4 = valid ? d.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
         const bool gas_i = valid && d.orig[s] < kp.n_gas;
         const bool act = MODE == 0 ? gas_i : valid;
+        const float side = valid ? d.fcube[4 * d.sys_sorted[s] + 3] : 1.f;     // the system's root cube
         float L = 0.f;
         if (act) {
             L = MODE == 0 ? d.len_h[s] : d.len_eps[s];
@@ -113,13 +118,57 @@ __global__ void __launch_bounds__(LW_THREADS, 6) k_lengths(evol_dev d, evol_kpar
                     rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
                     rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
                 }
-                const unsigned rootmask = __ballot_sync(0xffffffffu, coll);
                 bool over = false;
                 bool broken = false;
-                int top = 1;
-                if (lane == 0) stk[0] = make_int2(0, (int)rootmask);
+                int ng = 0;
+                auto gather_flush = [&]() {
+                    __syncwarp();
+                    for (int l = lane; l < ng; l += 32) {
+                        const int j = sm.gj[w][l];
+                        float4 p = d.pos[j];
+                        if (MODE == 0 && d.orig[j] >= kp.n_gas) p.w = -1.f;
+                        sm.gp[w][l] = p;
+                    }
+                    __syncwarp();
+                    for (int t = 0; t < ng; ++t) {
+                        const float4 pj = sm.gp[w][t];
+                        if (((sm.gmask[w][t] >> lane) & 1u) && pj.w >= 0.f) {
+                            const float dx = evol_wrap(pi4.x - pj.x, plen0, pm & 1);
+                            const float dy = evol_wrap(pi4.y - pj.y, plen1, pm & 2);
+                            const float dz = evol_wrap(pi4.z - pj.z, plen2, pm & 4);
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < R2) {
+                                if (cnt < list_cap) lst[(size_t)cnt * 32 + lane] = make_float2(sqrtf(r2), pj.w);
+                                else over = true;
+                                ++cnt;
+                            }
+                        }
+                    }
+                    ng = 0;
+                    __syncwarp();
+                };
+                // one stack entry per system present among the collecting lanes
+                int top = 0;
+                {
+                    const int myroot = coll ? d.sys_root[d.sys_sorted[s]] : -1;
+                    const unsigned peers = __match_any_sync(0xffffffffu, myroot);
+                    const bool leader = coll && (__ffs(peers) - 1) == lane;
+                    const unsigned leaders = __ballot_sync(0xffffffffu, leader);
+                    if (leader) stk[__popc(leaders & ((1u << lane) - 1u))] = make_int2(myroot, (int)peers);
+                    top = __popc(leaders);
+                }
                 __syncwarp();
+                long long pops = 0;
+                const long long pop_cap = 2ll * (long long)(*d.nnodes) + 64;
                 while (top > 0) {
+                    if (++pops > pop_cap) {        // corrupt tree: stop, flag and report where
+                        if (lane == 0) {
+                            evol_flag(d.err, EVOL_ETIMEOUT);
+                            atomicMax(&d.counters[7], 2ull);
+                        }
+                        broken = true;
+                        break;
+                    }
                     const int k = min(top, 32);
                     top -= k;
                     int node = -1;
@@ -177,7 +226,7 @@ __global__ void __launch_bounds__(LW_THREADS, 6) k_lengths(evol_dev d, evol_kpar
                         const unsigned Of = __ballot_sync(0xffffffffu, open);
                         if (lane == kk) Ok = Of;
                     }
-                    // opened leaves: gather their particles into the lanes' lists
+                    // opened leaves: stage their particles, then each lane keeps those within its radius
                     const bool isleaf = (I.x >> 8) & 1;
                     unsigned lm = __ballot_sync(0xffffffffu, Ok != 0u && isleaf);
                     while (lm) {
@@ -186,20 +235,14 @@ __global__ void __launch_bounds__(LW_THREADS, 6) k_lengths(evol_dev d, evol_kpar
                         const unsigned ok = __shfl_sync(0xffffffffu, Ok, kk);
                         const int b0 = __shfl_sync(0xffffffffu, I.z, kk);
                         const int e0 = __shfl_sync(0xffffffffu, I.w, kk);
-                        const bool mine = (ok >> lane) & 1u;
-                        for (int j = b0; j < e0; ++j) {
-                            const float4 pj = d.pos[j];
-                            if (MODE == 0 && d.orig[j] >= kp.n_gas) continue;
-                            if (!mine) continue;
-                            const float dx = evol_wrap(pi4.x - pj.x, plen0, pm & 1);
-                            const float dy = evol_wrap(pi4.y - pj.y, plen1, pm & 2);
-                            const float dz = evol_wrap(pi4.z - pj.z, plen2, pm & 4);
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < R2) {
-                                if (cnt < list_cap) lst[(size_t)cnt * 32 + lane] = make_float2(sqrtf(r2), pj.w);
-                                else over = true;
-                                ++cnt;
+                        for (int b = b0; b < e0; b += 32) {
+                            const int kc = min(32, e0 - b);
+                            if (ng + kc > GCAP) gather_flush();
+                            if (lane < kc) {
+                                sm.gj[w][ng + lane] = b + lane;
+                                sm.gmask[w][ng + lane] = ok;
                             }
+                            ng += kc;
                         }
                     }
                     // opened internal nodes: push children
@@ -235,6 +278,7 @@ __global__ void __launch_bounds__(LW_THREADS, 6) k_lengths(evol_dev d, evol_kpar
                     __syncwarp();
                 }
                 if (broken) break;
+                if (ng) gather_flush();
                 stale = false;
                 if (over) {
                     // more neighbours than the list holds: the radius is too large; shrink, gather again
@@ -246,9 +290,18 @@ __global__ void __launch_bounds__(LW_THREADS, 6) k_lengths(evol_dev d, evol_kpar
                 }
             }
             // ---- Newton / bisection on the private lists ----
-            for (;;) {
+            for (int sweep = 0;; ++sweep) {
                 const bool need = (status == ST_ACTIVE || status == ST_LAST) && !stale;
                 if (!__any_sync(0xffffffffu, need)) break;
+                if (sweep > 2 * MAX_ITERS + 8) {   // cannot happen: every active lane converges or stops
+                    if (lane == 0) {
+                        evol_flag(d.err, EVOL_ETIMEOUT);
+                        atomicMax(&d.counters[7], 3ull);
+                    }
+                    status = ST_DONE;
+                    stale = false;
+                    break;
+                }
                 float Sw = 0.f, Suw = 0.f, Smw = 0.f, Smuw = 0.f;
                 const float Linv = need ? 1.f / L : 0.f;
                 const float twoL = 2.f * L;

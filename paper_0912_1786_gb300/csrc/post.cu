@@ -134,7 +134,60 @@ __global__ void k_diag_final(int nparts, const double *part, const int32_t *nnod
     }
 }
 
+// Leapfrog pieces (Sect. 4.1, KDK): half kick of v (and u for gas), drift of x with periodic
+// wrapping, in the caller's order.
+__global__ void k_kick(int n, int n_gas, float half_dt, float *vx, float *vy, float *vz, float *u, const float *ax,
+                       const float *ay, const float *az, const float *dudt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    vx[i] += half_dt * ax[i];
+    vy[i] += half_dt * ay[i];
+    vz[i] += half_dt * az[i];
+    if (u && dudt && i < n_gas) u[i] += half_dt * dudt[i];
+}
+
+__global__ void k_drift(int n, float dt, float *x, float *y, float *z, const float *vx, const float *vy,
+                        const float *vz, int pmask, float lo0, float lo1, float lo2, float len0, float len1, float len2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float p[3] = {x[i] + dt * vx[i], y[i] + dt * vy[i], z[i] + dt * vz[i]};
+    const float lo[3] = {lo0, lo1, lo2}, len[3] = {len0, len1, len2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if ((pmask >> a) & 1) {
+            float t = p[a] - lo[a];
+            t -= len[a] * floorf(t / len[a]);
+            if (t >= len[a]) t -= len[a];       // rounding can land exactly on the upper edge
+            if (t < 0.f) t = 0.f;
+            p[a] = lo[a] + t;
+        }
+    x[i] = p[0];
+    y[i] = p[1];
+    z[i] = p[2];
+}
+
 }  // namespace
+
+int evol_launch_kick(evol_ctx *c, const evol_particles *p, float half_dt, const float *ax, const float *ay,
+                     const float *az, const float *dudt)
+{
+    int n = (int)p->n;
+    k_kick<<<(n + 255) / 256, 256, 0, c->stream>>>(n, (int)p->n_gas, half_dt, (float *)p->vx, (float *)p->vy,
+                                                   (float *)p->vz, (float *)p->u, ax, ay, az, dudt);
+    return evol_cuda_ok(cudaGetLastError());
+}
+
+int evol_launch_drift(evol_ctx *c, const evol_particles *p, const evol_params *prm, float dt)
+{
+    int n = (int)p->n;
+    k_drift<<<(n + 255) / 256, 256, 0, c->stream>>>(
+        n, dt, (float *)p->x, (float *)p->y, (float *)p->z, p->vx, p->vy, p->vz, prm->periodic_mask,
+        prm->periodic_lo[0], prm->periodic_lo[1], prm->periodic_lo[2], prm->periodic_hi[0] - prm->periodic_lo[0],
+        prm->periodic_hi[1] - prm->periodic_lo[1], prm->periodic_hi[2] - prm->periodic_lo[2]);
+    return evol_cuda_ok(cudaGetLastError());
+}
 
 int evol_launch_pack(evol_ctx *c, const evol_particles *p, const evol_params *prm, int do_grav, int do_sph)
 {

@@ -297,20 +297,36 @@ __global__ void k_permute(int n, int n_gas, const int32_t *__restrict__ perm, co
 // ---------------------------------------------------------------------------------------
 // Node construction.
 // ---------------------------------------------------------------------------------------
-__global__ void k_lcp(int n, const uint64_t *__restrict__ keys, uint8_t *__restrict__ lcp)
+__device__ __forceinline__ int sys_of_pos(const int32_t *__restrict__ sys_off, int nsys, int s)
+{
+    // largest k with sys_off[k] <= s
+    int lo = 0, hi = nsys;           // sys_off[0] = 0 <= s < sys_off[nsys]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (sys_off[mid] <= s) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// d_i = common leading octal digits of keys i-1 and i; -1 where i starts a system (a forest of
+// independent trees, one per system, in one pre-order list).
+__global__ void k_lcp(int n, const uint64_t *__restrict__ keys, const int32_t *__restrict__ sys_off, int nsys,
+                      int8_t *__restrict__ lcp, int32_t *__restrict__ sys_sorted)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (i == 0) {
-        lcp[0] = 0;
+    const int sy = sys_of_pos(sys_off, nsys, i);
+    sys_sorted[i] = sy;
+    if (i == sys_off[sy]) {
+        lcp[i] = -1;
         return;
     }
     uint64_t x = keys[i - 1] ^ keys[i];
-    lcp[i] = x == 0 ? (uint8_t)EVOL_MAXLEVEL : (uint8_t)((__clzll((long long)x) - 1) / 3);
+    lcp[i] = x == 0 ? (int8_t)EVOL_MAXLEVEL : (int8_t)((__clzll((long long)x) - 1) / 3);
 }
 
 // Does the level-lam run containing position i hold more than `leaf` particles?
-__device__ __forceinline__ bool run_exceeds(int n, const uint8_t *__restrict__ lcp, int i, int lam, int leaf)
+__device__ __forceinline__ bool run_exceeds(int n, const int8_t *__restrict__ lcp, int i, int lam, int leaf)
 {
     int c = 1;
     for (int t = i; c <= leaf && t > 0 && lcp[t] >= lam; --t) ++c;
@@ -318,9 +334,9 @@ __device__ __forceinline__ bool run_exceeds(int n, const uint8_t *__restrict__ l
     return c > leaf;
 }
 
-__device__ __forceinline__ int nodes_at(int n, const uint8_t *__restrict__ lcp, int i, int leaf, int &lo)
+__device__ __forceinline__ int nodes_at(int n, const int8_t *__restrict__ lcp, int i, int leaf, int &lo)
 {
-    lo = (i == 0) ? 0 : lcp[i] + 1;
+    lo = lcp[i] + 1;                  // 0 where a system starts (lcp = -1)
     int c = 0;
     for (int l = lo; l <= EVOL_MAXLEVEL; ++l) {
         if (l > 0 && !run_exceeds(n, lcp, i, l - 1, leaf)) break;
@@ -329,7 +345,7 @@ __device__ __forceinline__ int nodes_at(int n, const uint8_t *__restrict__ lcp, 
     return c;
 }
 
-__global__ void k_count(int n, const uint8_t *__restrict__ lcp, int leaf, int32_t *__restrict__ cnt)
+__global__ void k_count(int n, const int8_t *__restrict__ lcp, int leaf, int32_t *__restrict__ cnt)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -337,25 +353,25 @@ __global__ void k_count(int n, const uint8_t *__restrict__ lcp, int leaf, int32_
     cnt[i] = nodes_at(n, lcp, i, leaf, lo);
 }
 
-// end of the level-l run beginning at position i
-__device__ __forceinline__ int run_end(int n, const uint64_t *__restrict__ keys, const uint8_t *__restrict__ lcp,
+// end of the level-l run beginning at position i; nend = end of i's system
+__device__ __forceinline__ int run_end(int nend, const uint64_t *__restrict__ keys, const int8_t *__restrict__ lcp,
                                        int i, int l, int leaf)
 {
     int t = i + 1;
-    for (int k = 0; k <= leaf && t < n; ++k, ++t)
+    for (int k = 0; k <= leaf && t < nend; ++k, ++t)
         if (lcp[t] < l) return t;
-    if (t >= n) return n;
-    if (l == 0) return n;
+    if (t >= nend) return nend;
+    if (l == 0) return nend;
     int sh = 3 * (EVOL_MAXLEVEL - l);
     uint64_t upper = keys[i] | ((1ull << sh) - 1ull);
     // gallop then bisect for the first index with key > upper
     int lo = t - 1, step = 1, hi = t;
-    while (hi < n && keys[hi] <= upper) {
+    while (hi < nend && keys[hi] <= upper) {
         lo = hi;
         step <<= 1;
         hi = t - 1 + step;
     }
-    if (hi > n) hi = n;
+    if (hi > nend) hi = nend;
     while (hi - lo > 1) {
         int mid = lo + ((hi - lo) >> 1);
         if (keys[mid] <= upper) lo = mid; else hi = mid;
@@ -363,7 +379,8 @@ __device__ __forceinline__ int run_end(int n, const uint64_t *__restrict__ keys,
     return hi;
 }
 
-__global__ void k_fill(int n, const uint64_t *__restrict__ keys, const uint8_t *__restrict__ lcp,
+__global__ void k_fill(int n, const uint64_t *__restrict__ keys, const int8_t *__restrict__ lcp,
+                       const int32_t *__restrict__ sys_off, const int32_t *__restrict__ sys_sorted,
                        const int32_t *__restrict__ base, int leaf, int64_t node_cap, int32_t *__restrict__ nbeg,
                        int32_t *__restrict__ nend, int32_t *__restrict__ nlev, int32_t *__restrict__ nnext,
                        int32_t *__restrict__ nnodes, int *err)
@@ -378,11 +395,12 @@ __global__ void k_fill(int n, const uint64_t *__restrict__ keys, const uint8_t *
     int lo;
     int c = nodes_at(n, lcp, i, leaf, lo);
     int b = base[i];
+    const int send = sys_off[sys_sorted[i] + 1];
     for (int k = 0; k < c; ++k) {
         int id = b + k;
         if (id >= node_cap) return;
         int l = lo + k;
-        int e = run_end(n, keys, lcp, i, l, leaf);
+        int e = run_end(send, keys, lcp, i, l, leaf);
         nbeg[id] = i;
         nend[id] = e;
         nlev[id] = l;
@@ -400,7 +418,7 @@ __global__ void k_link(const int32_t *__restrict__ nnodes, int leaf, const int32
     int nn = *nnodes;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += gridDim.x * blockDim.x) {
         narrive[id] = 0;
-        if (id == 0) nparent[0] = -1;
+        if (nlev[id] == 0) nparent[id] = -1;     // the root of a system
         int e = nend[id];
         bool internal = (e - nbeg[id] > leaf) && nlev[id] < EVOL_MAXLEVEL;
         int k = 0;
@@ -574,8 +592,8 @@ __global__ void k_moments(const int32_t *__restrict__ nnodes, int n_gas, const i
                           const int32_t *__restrict__ nnext, const int32_t *__restrict__ nparent,
                           const int32_t *__restrict__ nnch, int32_t *__restrict__ narrive,
                           const float4 *__restrict__ pos, const int32_t *__restrict__ orig,
-                          const uint64_t *__restrict__ keys, const double *__restrict__ cube, float theta,
-                          NodeOut o, int mixed)
+                          const uint64_t *__restrict__ keys, const double *__restrict__ cube,
+                          const int32_t *__restrict__ sys_sorted, float theta, NodeOut o, int mixed, int *err)
 {
     int nn = *nnodes;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += gridDim.x * blockDim.x) {
@@ -584,15 +602,21 @@ __global__ void k_moments(const int32_t *__restrict__ nnodes, int n_gas, const i
         float3 lo, hi;
         int hg;
         leaf_moments<T>(nbeg[id], nend[id], n_gas, pos, orig, mm, lo, hi, hg);
-        write_node<T>(o, id, mm, lo, hi, hg, nlev[id], cube, keys[nbeg[id]], theta, mixed != 0);
+        write_node<T>(o, id, mm, lo, hi, hg, nlev[id], cube + 4 * sys_sorted[nbeg[id]], keys[nbeg[id]], theta,
+                      mixed != 0);
         __threadfence();
         int p = nparent[id];
-        while (p >= 0 && p < nn) {
+        for (int climb = 0; p >= 0 && p < nn; ++climb) {
+            if (climb > EVOL_MAXLEVEL + 1) {     // deeper than the tree can be: corrupt parents
+                evol_flag(err, EVOL_ETIMEOUT);
+                break;
+            }
             int old = atomicAdd(&narrive[p], 1);
             if (old != nnch[p] - 1) break;
             __threadfence();
             combine<T>(o, p, nnch[p], nnext, mm, lo, hi, hg, mixed != 0);
-            write_node<T>(o, p, mm, lo, hi, hg, nlev[p], cube, keys[nbeg[p]], theta, mixed != 0);
+            write_node<T>(o, p, mm, lo, hi, hg, nlev[p], cube + 4 * sys_sorted[nbeg[p]], keys[nbeg[p]], theta,
+                          mixed != 0);
             __threadfence();
             p = nparent[p];
         }
@@ -616,7 +640,8 @@ __global__ void k_node_lengths(const int32_t *__restrict__ nnodes, int n_gas, co
                                const int32_t *__restrict__ nend, const int32_t *__restrict__ nnext,
                                const int32_t *__restrict__ nparent, const int32_t *__restrict__ nnch,
                                int32_t *__restrict__ narrive, const int32_t *__restrict__ orig,
-                               const float *__restrict__ le, const float *__restrict__ lh, float4 *nB, float4 *nC)
+                               const float *__restrict__ le, const float *__restrict__ lh, float4 *nB, float4 *nC,
+                               int *err)
 {
     int nn = *nnodes;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += gridDim.x * blockDim.x) {
@@ -627,7 +652,11 @@ __global__ void k_node_lengths(const int32_t *__restrict__ nnodes, int n_gas, co
         nB[id].w = hm >= 0.f ? 2.f * hm : -1.f;
         __threadfence();
         int p = nparent[id];
-        while (p >= 0 && p < nn) {
+        for (int climb = 0; p >= 0 && p < nn; ++climb) {
+            if (climb > EVOL_MAXLEVEL + 1) {     // deeper than the tree can be: corrupt parents
+                evol_flag(err, EVOL_ETIMEOUT);
+                break;
+            }
             int old = atomicAdd(&narrive[p], 1);
             if (old != nnch[p] - 1) break;
             __threadfence();
@@ -642,6 +671,126 @@ __global__ void k_node_lengths(const int32_t *__restrict__ nnodes, int n_gas, co
             p = nparent[p];
         }
     }
+}
+
+// ---- several independent systems (batched): per-system cube and keys ----------------------
+__global__ void k_set_single(int n, int32_t *sys_off)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        sys_off[0] = 0;
+        sys_off[1] = n;
+    }
+}
+
+// one block per system: its cube from its own particles
+__global__ void k_bbox_sys(const int32_t *__restrict__ sys_off, const float *__restrict__ x,
+                           const float *__restrict__ y, const float *__restrict__ z, double *cube, float *fcube)
+{
+    const int k = blockIdx.x;
+    const int b = sys_off[k], e = sys_off[k + 1];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+        float v[3] = {x[i], y[i], z[i]};
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], v[a]);
+            hi[a] = fmaxf(hi[a], v[a]);
+        }
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    __shared__ float sred[BB_THREADS / 32][6];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int a = 0; a < 3; ++a) {
+            sred[w][a] = lo[a];
+            sred[w][3 + a] = hi[a];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ext = 0.0;
+        float L[3], H[3];
+        for (int a = 0; a < 3; ++a) {
+            L[a] = sred[0][a];
+            H[a] = sred[0][3 + a];
+            for (int q = 1; q < BB_THREADS / 32; ++q) {
+                L[a] = fminf(L[a], sred[q][a]);
+                H[a] = fmaxf(H[a], sred[q][3 + a]);
+            }
+            double ee = (double)H[a] - (double)L[a];
+            ext = ee > ext ? ee : ext;
+        }
+        double target = ext * (1.0 + ldexp(1.0, -20)), side = 1.0;
+        if (target > 0.0) {
+            int ex;
+            double fr = frexp(target, &ex);
+            side = (fr == 0.5) ? ldexp(1.0, ex - 1) : ldexp(1.0, ex);
+        }
+        for (int a = 0; a < 3; ++a) {
+            cube[4 * k + a] = (double)L[a];
+            fcube[4 * k + a] = L[a];
+        }
+        cube[4 * k + 3] = side;
+        fcube[4 * k + 3] = (float)side;
+    }
+}
+
+__device__ __forceinline__ uint64_t key_of(float x, float y, float z, const double *__restrict__ cb)
+{
+    const double scale = ldexp(1.0, EVOL_MAXLEVEL) / cb[3];
+    const float v[3] = {x, y, z};
+    uint64_t q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double t = floor(__dmul_rn(__dsub_rn((double)v[a], cb[a]), scale));
+        t = t < 0.0 ? 0.0 : (t > 2097151.0 ? 2097151.0 : t);
+        q[a] = (uint64_t)t;
+    }
+    return (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+}
+
+// keys in the caller's order, each relative to its own system's cube
+__global__ void k_keys_sys(int n, const float *__restrict__ x, const float *__restrict__ y,
+                           const float *__restrict__ z, const int32_t *__restrict__ sys_off, int nsys,
+                           const double *__restrict__ cube, uint64_t *__restrict__ keys, int32_t *__restrict__ vals)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int sy = sys_of_pos(sys_off, nsys, i);
+    keys[i] = key_of(x[i], y[i], z[i], cube + 4 * sy);
+    vals[i] = i;
+}
+
+// system id of the particle at each position of the current order (digit source of the last passes)
+__global__ void k_gather_sys(int n, const int32_t *__restrict__ vals, const int32_t *__restrict__ sys_off, int nsys,
+                             uint64_t *__restrict__ skey)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    skey[i] = (uint64_t)sys_of_pos(sys_off, nsys, vals[i]);
+}
+
+// Morton keys again, in the final order (the system passes carried only the system digit)
+__global__ void k_keys_sorted(int n, const float *__restrict__ x, const float *__restrict__ y,
+                              const float *__restrict__ z, const int32_t *__restrict__ vals,
+                              const int32_t *__restrict__ sys_off, int nsys, const double *__restrict__ cube,
+                              uint64_t *__restrict__ keys, int32_t *__restrict__ vals_out)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int j = vals[s];
+    const int sy = sys_of_pos(sys_off, nsys, j);
+    keys[s] = key_of(x[j], y[j], z[j], cube + 4 * sy);
+    if (vals_out) vals_out[s] = j;
+}
+
+__global__ void k_sys_root(int nsys, const int32_t *__restrict__ sys_off, const int32_t *__restrict__ base,
+                           int32_t *__restrict__ sys_root)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nsys) sys_root[k] = base[sys_off[k]];
 }
 
 __global__ void k_zero_i32(const int32_t *__restrict__ nnodes, int32_t *a)
@@ -669,13 +818,21 @@ int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *p
 {
     evol_dev &d = c->d;
     int n = (int)p->n;
+    const int nsys = c->nsys > 0 ? c->nsys : 1;
     int leaf = prm->leaf_size > 0 ? prm->leaf_size : 8;
     cudaStream_t st = c->stream;
-    int nb = (int)c->bbox_blocks;
-    k_bbox_partial<<<nb, BB_THREADS, 0, st>>>(n, p->x, p->y, p->z, d.bbox_part);
-    k_bbox_final<<<1, 32, 0, st>>>(nb, d.bbox_part, d.cube, d.fcube);
     int tb = 256, gb = (n + tb - 1) / tb;
-    k_keys<<<gb, tb, 0, st>>>(n, p->x, p->y, p->z, d.cube, d.keys_a, d.vals_a);
+    if (nsys == 1) {
+        int nb = (int)c->bbox_blocks;
+        k_set_single<<<1, 32, 0, st>>>(n, d.sys_off);
+        k_bbox_partial<<<nb, BB_THREADS, 0, st>>>(n, p->x, p->y, p->z, d.bbox_part);
+        k_bbox_final<<<1, 32, 0, st>>>(nb, d.bbox_part, d.cube, d.fcube);
+        k_keys<<<gb, tb, 0, st>>>(n, p->x, p->y, p->z, d.cube, d.keys_a, d.vals_a);
+    } else {
+        // the offsets were copied into d.sys_off by the caller of this launcher
+        k_bbox_sys<<<nsys, BB_THREADS, 0, st>>>(d.sys_off, p->x, p->y, p->z, d.cube, d.fcube);
+        k_keys_sys<<<gb, tb, 0, st>>>(n, p->x, p->y, p->z, d.sys_off, nsys, d.cube, d.keys_a, d.vals_a);
+    }
     int rsb = (n + RS_TILE - 1) / RS_TILE;
     uint64_t *ka = d.keys_a, *kb = d.keys_b;
     int32_t *va = d.vals_a, *vb = d.vals_b;
@@ -688,14 +845,31 @@ int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *p
         int32_t *tv = va; va = vb; vb = tv;
     }
     // 8 passes: sorted keys and permutation are back in keys_a / vals_a
+    if (nsys > 1) {
+        // stable passes on the system id make the order (system, key); then the keys are recomputed
+        k_gather_sys<<<gb, tb, 0, st>>>(n, d.vals_a, d.sys_off, nsys, d.keys_b);
+        ka = d.keys_b; kb = d.keys_a; va = d.vals_a; vb = d.vals_b;
+        for (int shift = 0; (1ll << shift) < (long long)nsys; shift += 8) {
+            k_rs_hist<<<rsb, RS_THREADS, 0, st>>>(n, ka, shift, (int32_t *)d.hist, rsb);
+            int rc = scan_i32(c, 256 * rsb, (int32_t *)d.hist, (int32_t *)d.hist, 0);
+            if (rc) return rc;
+            k_rs_scatter<<<rsb, RS_THREADS, 0, st>>>(n, ka, va, kb, vb, shift, (int32_t *)d.hist, rsb);
+            uint64_t *tk = ka; ka = kb; kb = tk;
+            int32_t *tv = va; va = vb; vb = tv;
+        }
+        // va holds the final permutation; rebuild keys_a / vals_a from it
+        k_keys_sorted<<<gb, tb, 0, st>>>(n, p->x, p->y, p->z, va, d.sys_off, nsys, d.cube, d.keys_a,
+                                         va == d.vals_a ? nullptr : d.vals_a);
+    }
     k_permute<<<gb, tb, 0, st>>>(n, (int)p->n_gas, d.vals_a, p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->u,
                                  p->h, p->eps, d.pos, d.vel, d.len_h, d.len_eps, d.orig);
-    k_lcp<<<gb, tb, 0, st>>>(n, d.keys_a, d.lcp);
+    k_lcp<<<gb, tb, 0, st>>>(n, d.keys_a, d.sys_off, nsys, d.lcp, d.sys_sorted);
     k_count<<<gb, tb, 0, st>>>(n, d.lcp, leaf, d.cnt);
     int rc = scan_i32(c, n, d.cnt, d.base, 1);
     if (rc) return rc;
-    k_fill<<<gb, tb, 0, st>>>(n, d.keys_a, d.lcp, d.base, leaf, c->node_cap, d.nbeg, d.nend, d.nlev, d.nnext,
-                              d.nnodes, d.err);
+    k_fill<<<gb, tb, 0, st>>>(n, d.keys_a, d.lcp, d.sys_off, d.sys_sorted, d.base, leaf, c->node_cap, d.nbeg, d.nend,
+                              d.nlev, d.nnext, d.nnodes, d.err);
+    k_sys_root<<<(nsys + 255) / 256, 256, 0, st>>>(nsys, d.sys_off, d.base, d.sys_root);
     int ng = c->num_sms * 8;
     k_link<<<ng, 256, 0, st>>>(d.nnodes, leaf, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent, d.nnch, d.narrive, d.nI,
                                d.nK0, d.nK1);
@@ -703,10 +877,12 @@ int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *p
     float theta = prm->theta;
     if (prm->precision == EVOL_FP32_MIXED)
         k_moments<double><<<ng, 128, 0, st>>>(d.nnodes, (int)p->n_gas, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
-                                              d.nnch, d.narrive, d.pos, d.orig, d.keys_a, d.cube, theta, o, 1);
+                                              d.nnch, d.narrive, d.pos, d.orig, d.keys_a, d.cube, d.sys_sorted, theta,
+                                              o, 1, d.err);
     else
         k_moments<float><<<ng, 128, 0, st>>>(d.nnodes, (int)p->n_gas, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
-                                             d.nnch, d.narrive, d.pos, d.orig, d.keys_a, d.cube, theta, o, 0);
+                                             d.nnch, d.narrive, d.pos, d.orig, d.keys_a, d.cube, d.sys_sorted, theta,
+                                             o, 0, d.err);
     return evol_cuda_ok(cudaGetLastError());
 }
 
@@ -717,6 +893,6 @@ int evol_launch_node_lengths(evol_ctx *c, const evol_params *prm, int n_gas)
     (void)prm;
     k_zero_i32<<<ng, 256, 0, c->stream>>>(d.nnodes, d.narrive);
     k_node_lengths<<<ng, 128, 0, c->stream>>>(d.nnodes, n_gas, d.nbeg, d.nend, d.nnext, d.nparent,
-                                              d.nnch, d.narrive, d.orig, d.len_eps, d.len_h, d.nB, d.nC);
+                                              d.nnch, d.narrive, d.orig, d.len_eps, d.len_h, d.nB, d.nC, d.err);
     return evol_cuda_ok(cudaGetLastError());
 }

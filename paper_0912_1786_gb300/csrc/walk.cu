@@ -56,8 +56,10 @@ struct Acc {
     float hx = 0.f, hy = 0.f, hz = 0.f, du = 0.f;       // SPH
 };
 
+// Single-physics variants carry a minimum of one block per SM: the compiler then keeps their
+// state in registers instead of spilling it to local memory.
 template <bool GRAV, bool SPH, bool MIXED, bool CHECK>
-__global__ void __launch_bounds__(WK_THREADS) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH) ? 0 : 1) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
     const int lane = threadIdx.x & 31;
@@ -103,21 +105,30 @@ __global__ void __launch_bounds__(WK_THREADS) k_walk(evol_dev d, evol_kparams kp
 
         auto flush_far = [&]() {
             __syncwarp();
-            for (int l = lane; l < nfar; l += 32) {
+            // pad to a multiple of 4 with empty-mask entries (node 0 is always valid)
+            const int padded = (nfar + 3) & ~3;
+            if (lane < padded - nfar) {
+                sm.far_id[w][nfar + lane] = 0;
+                sm.far_mask[w][nfar + lane] = 0u;
+            }
+            __syncwarp();
+            for (int l = lane; l < padded; l += 32) {
                 const int id = sm.far_id[w][l];
                 sm.fA[w][l] = d.nA[id];
                 sm.fQ0[w][l] = d.nQ0[id];
                 sm.fQ1[w][l] = d.nQ1[id];
             }
             __syncwarp();
-            for (int e = 0; e < nfar; ++e) {
-                const unsigned msk = sm.far_mask[w][e];
-                wfar += __popc(msk);
-                if ((msk >> lane) & 1u) {
-                    const float4 A = sm.fA[w][e], Q0 = sm.fQ0[w][e], Q1 = sm.fQ1[w][e];
+            for (int e = 0; e < padded; e += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned msk = sm.far_mask[w][e + u];
+                    wfar += __popc(msk);
+                    const float4 A = sm.fA[w][e + u], Q0 = sm.fQ0[w][e + u], Q1 = sm.fQ1[w][e + u];
                     const float dx = pi.x - A.x, dy = pi.y - A.y, dz = pi.z - A.z;
                     const float d2 = dx * dx + dy * dy + dz * dz;
-                    const float rinv = rsqrtf(d2);
+                    // lanes outside the mask get rinv = 0, so every term below vanishes for them
+                    const float rinv = ((msk >> lane) & 1u) ? rsqrtf(d2) : 0.f;
                     const float rinv2 = rinv * rinv;
                     const float r3 = rinv * rinv2, r5 = r3 * rinv2, r7 = r5 * rinv2;
                     const float qx = Q0.x * dx + Q1.x * dy + Q1.y * dz;
@@ -255,13 +266,29 @@ __global__ void __launch_bounds__(WK_THREADS) k_walk(evol_dev d, evol_kparams kp
         if (!GRAV) emin = 0.f;
 
         int2 *stk = d.wstack + (size_t)(blockIdx.x * WK_WARPS + w) * kp.stack_cap;
+        // one stack entry per system present in the group: its root with the mask of its lanes
         int top = 0;
-        if (rootmask) {
-            if (lane == 0) stk[0] = make_int2(0, (int)rootmask);
-            top = 1;
+        {
+            const int myroot = active ? d.sys_root[d.sys_sorted[s]] : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, myroot);
+            const bool leader = active && (__ffs(peers) - 1) == lane;
+            const unsigned leaders = __ballot_sync(0xffffffffu, leader);
+            if (leader) stk[__popc(leaders & ltmask)] = make_int2(myroot, (int)peers);
+            top = __popc(leaders);
         }
         __syncwarp();
+        // a traversal pops every node at most once; a larger count can only come from a corrupt
+        // tree: stop, flag it and report where
+        long long pops = 0;
+        const long long pop_cap = 2ll * (long long)(*d.nnodes) + 64;
         while (top > 0) {
+            if (++pops > pop_cap) {
+                if (lane == 0) {
+                    evol_flag(d.err, EVOL_ETIMEOUT);
+                    atomicMax(&d.counters[7], 1ull);
+                }
+                break;
+            }
             const int k = min(top, 32);
             top -= k;
             int node = -1;
@@ -365,7 +392,7 @@ __global__ void __launch_bounds__(WK_THREADS) k_walk(evol_dev d, evol_kparams kp
             }
             if (GRAV && fa) {
                 const int cnt = __popc(fa);
-                if (nfar + cnt > FARCAP) flush_far();
+                if (nfar + cnt > FARCAP - 3) flush_far();
                 if (Ak) {
                     const int pos = nfar + __popc(fa & ltmask);
                     sm.far_id[w][pos] = node;
@@ -480,6 +507,7 @@ void launch_walk(evol_ctx *c, const evol_kparams &kp)
     if (blocks_per_sm < 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walk<GRAV, SPH, MIXED, CHECK>, WK_THREADS, 0);
         if (blocks_per_sm < 1) blocks_per_sm = 1;
+        if (blocks_per_sm > 8) blocks_per_sm = 8;          // stack slots exist for 32 warps per SM
     }
     unsigned long long *q = c->d.counters + 4;
     cudaMemsetAsync(q, 0, sizeof(unsigned long long), c->stream);

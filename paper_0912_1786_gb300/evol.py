@@ -63,6 +63,11 @@ def lib():
             getattr(L, name).argtypes = [vp, pp(EvolParticles), pp(EvolParams)]
         for name in ("evol_sph_density", "evol_gravity", "evol_sph_forces", "evol_step", "evol_step_host"):
             getattr(L, name).argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs)]
+        L.evol_step_batched.argtypes = [vp, C.POINTER(C.c_int64), C.c_int, pp(EvolParticles), pp(EvolParams),
+                                         pp(EvolOutputs)]
+        L.evol_autotune.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs), C.POINTER(C.c_int),
+                                     C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
+        L.evol_kdk.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs), C.c_float, C.c_int]
         L.evol_sync.argtypes = [vp]
         L.evol_get_diagnostics.argtypes = [vp, pp(C.c_double)]
         L.evol_get_timings.argtypes = [vp, pp(C.c_float)]
@@ -172,6 +177,30 @@ def evol_step(ctx, particles, params, outputs):
 def evol_step_host(ctx, particles, params, outputs):
     return _check(lib().evol_step_host(ctx, C.byref(particles), C.byref(params), C.byref(outputs)),
                   "evol_step_host")
+
+
+def evol_step_batched(ctx, sys_offsets, particles, params, outputs):
+    """Independent systems in one step; sys_offsets: host sequence of nsys + 1 particle offsets."""
+    offs = (C.c_int64 * len(sys_offsets))(*[int(v) for v in sys_offsets])
+    return _check(lib().evol_step_batched(ctx, offs, len(sys_offsets) - 1, C.byref(particles), C.byref(params),
+                                          C.byref(outputs)), "evol_step_batched")
+
+
+def evol_autotune(ctx, particles, params, outputs, candidates=None, reps=3):
+    """Fastest leaf size for these particles; returns (best_leaf, {leaf: median ms})."""
+    cand = list(candidates) if candidates is not None else [4, 8, 12, 16, 24, 32]
+    carr = (C.c_int * len(cand))(*cand)
+    ms = (C.c_float * len(cand))()
+    best = C.c_int()
+    _check(lib().evol_autotune(ctx, C.byref(particles), C.byref(params), C.byref(outputs), carr, len(cand),
+                               int(reps), C.byref(best), ms), "evol_autotune")
+    return best.value, dict(zip(cand, list(ms)))
+
+
+def evol_kdk(ctx, particles, params, outputs, dt: float, nsteps: int):
+    """Fixed-step kick-drift-kick; updates the particle arrays in place (device tensors)."""
+    return _check(lib().evol_kdk(ctx, C.byref(particles), C.byref(params), C.byref(outputs), float(dt), int(nsteps)),
+                  "evol_kdk")
 
 
 def evol_sync(ctx, raise_on_error=True):

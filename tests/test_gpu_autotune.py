@@ -1,0 +1,32 @@
+"""The autotuner picks one of the candidate leaf sizes by timing; the step with the chosen leaf
+size still matches the oracle run with the same leaf size (theta and N_nei untouched)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0912_1786_gb300 import workloads as W
+
+from gpu_common import acc, assert_tol, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_returns_candidate_and_parity_holds():
+    import torch
+    from paper_0912_1786_gb300 import build, evol as E
+    from paper_0912_1786_gb300.device import DeviceSet
+    build.build()
+    w = W.hernquist_gas(n_dm=1 << 14, n_gas=1 << 13, seed=3)
+    ds = DeviceSet(w)
+    ctx = E.evol_create(w.n, torch.cuda.current_stream().cuda_stream)
+    try:
+        best, ms = E.evol_autotune(ctx, ds.particles, ds.params, ds.outputs, candidates=[4, 8, 16], reps=2)
+    finally:
+        E.evol_destroy(ctx)
+    assert best in (4, 8, 16)
+    assert all(v > 0 for v in ms.values())
+    assert ds.params.theta == w.params.theta and ds.params.n_nei_sph == w.params.n_nei_sph
+    p = W.Params(theta=w.params.theta, leaf_size=best)
+    g = run_gpu(w, p, check=False)
+    o = oracle.force_step(w, params=p)
+    assert_tol("acc", acc(g), np.stack([o["ax"], o["ay"], o["az"]], 1), scale=o["aabs"])
