@@ -291,6 +291,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--leaf", type=int, default=0, help="fixed leaf size (skips the autotune)")
     ap.add_argument("--ref-budget", type=float, default=20.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -323,7 +324,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
     ctx = E.evol_create(w.n, stream.cuda_stream)
     autotune = None
-    if not args.no_autotune and w.sys_offsets is None:
+    if args.leaf > 0:
+        ds.params.leaf_size = args.leaf
+    elif not args.no_autotune and w.sys_offsets is None:
         best, ms = E.evol_autotune(ctx, ds.particles, ds.params, ds.outputs, candidates=[8, 12, 16, 24, 32], reps=2)
         ds.params.leaf_size = best
         autotune = {"leaf_size": best, "median_ms_by_leaf": ms}

@@ -15,9 +15,10 @@ SOURCES = ["evol_api.cu", "tree.cu", "lengths.cu", "walk.cu", "post.cu", "noallo
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
-# sources whose kernels must compile without a local-memory stack frame (register spills): the
-# force walk's single-physics variants that spilled faulted on GB300, so a spilling build is refused
-NO_SPILL = {"walk.cu": "k_walk"}
+# kernels that must compile without a local-memory stack frame (register spills): the force
+# walk's single-physics variants that spilled faulted on GB300, so a spilling build of the walks
+# (force walk and length-solve walk) is refused
+NO_SPILL = {"walk.cu": "k_walk", "lengths.cu": "k_lengths"}
 
 
 def _spilling_kernels(ptxas_log: str, prefix: str):

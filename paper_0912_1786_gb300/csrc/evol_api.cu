@@ -20,7 +20,6 @@ int evol_launch_drift(evol_ctx *c, const evol_particles *p, const evol_params *p
 
 namespace {
 
-constexpr int64_t CAND_CAP = 192;        // neighbour-list entries per lane in the length solve
 constexpr int64_t NODE_FACTOR = 3;       // node capacity = 3 * particles + 64
 constexpr int64_t WSTACK_CAP = 4096;     // traversal stack entries per warp in the force walk
 constexpr int NSYS_CAP = 65536;          // independent systems per batched call
@@ -189,8 +188,8 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     c->sort_blocks = (max_n + 4095) / 4096;
     c->bbox_blocks = c->num_sms * 2;
     c->diag_blocks = c->num_sms * 2;
-    c->cand_cap = CAND_CAP;
-    c->cand_slots = (int64_t)c->num_sms * 6 * evol_lengths_warps_per_block();
+    c->cand_cap = 0;
+    c->cand_slots = (int64_t)c->num_sms * 6 * evol_lengths_warps_per_block();   // length-solve warps
     c->wstack_slots = (int64_t)c->num_sms * 32;      // the walk and length grids use at most 32 warps per SM
     c->wstack_cap = WSTACK_CAP;
     int64_t n = max_n, nn = c->node_cap;
@@ -213,7 +212,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.nBmin, nn); rc |= dalloc(&d.nBmax, nn); rc |= dalloc(&d.nI, nn);
     rc |= dalloc(&d.nK0, nn); rc |= dalloc(&d.nK1, nn);
     rc |= dalloc(&d.wstack, c->wstack_slots * c->wstack_cap);
-    rc |= dalloc(&d.cand_leaf, 2 * 32 * c->cand_slots * c->cand_cap);   // float2 per lane entry
+    rc |= dalloc(&d.cand_leaf, 1);                                      // unused
     rc |= dalloc(&d.cand_mask, 1);
     rc |= dalloc(&d.diag_part, 16 * c->diag_blocks); rc |= dalloc(&d.diag, 16);
     rc |= dalloc(&d.counters, 8); rc |= dalloc(&d.err, 1); rc |= dalloc(&d.nnodes, 1);
