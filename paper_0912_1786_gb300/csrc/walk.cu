@@ -50,16 +50,52 @@ struct WalkSmem {
     int norig[WK_WARPS][NEARCAP];
 };
 
+// The kernel functions of the pair loop in a division-free form: each takes u and iu = 1/u (iu is
+// read only where u >= 1, and where u < 2/3 for the Thomas-Couchman gradient), with 1/u formed
+// from quantities already at hand (eps/r, h/r).  Same polynomials as the FP32 kernel functions:
+//   gsoft_over_r: eps^3 phi'(r)/r,  phisoft: eps phi(r),  dw_over_u: pi h^5 (dW/dr)/r,
+//   tc_over_u: the Thomas-Couchman form of the latter.
+__device__ __forceinline__ float gsoft_over_r_u(float u, float iu)
+{
+    const float u2 = u * u;
+    const float in = 4.f / 3.f - 1.2f * u2 + 0.5f * u2 * u;
+    const float out = 8.f / 3.f - 3.f * u + 1.2f * u2 - u2 * u * (1.f / 6.f) - (1.f / 15.f) * iu * iu * iu;
+    return u < 1.f ? in : out;
+}
+
+__device__ __forceinline__ float phisoft_u(float u, float iu)
+{
+    const float u2 = u * u;
+    const float in = (2.f / 3.f) * u2 - 0.3f * u2 * u2 + 0.1f * u2 * u2 * u - 1.4f;
+    const float out = (4.f / 3.f) * u2 - u2 * u + 0.3f * u2 * u2 - u2 * u2 * u * (1.f / 30.f) - 1.6f + (1.f / 15.f) * iu;
+    return u < 1.f ? in : out;
+}
+
+__device__ __forceinline__ float dw_over_u_u(float u, float iu)
+{
+    const float a = fmaxf(2.f - u, 0.f);
+    return u < 1.f ? -3.f + 2.25f * u : -0.75f * a * a * iu;
+}
+
+__device__ __forceinline__ float tc_over_u_u(float u, float iu)
+{
+    const float a = fmaxf(2.f - u, 0.f);
+    return u < 2.f / 3.f ? -iu : (u < 1.f ? -0.75f * (4.f - 3.f * u) : -0.75f * a * a * iu);
+}
+
+// 1/x from the hardware reciprocal (about 1 ulp), for operands of the pair loop
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.f, x); }
+
 template <bool MIXED>
 struct Acc {
     float ax = 0.f, ay = 0.f, az = 0.f, pot = 0.f;      // gravity (without G)
     float hx = 0.f, hy = 0.f, hz = 0.f, du = 0.f;       // SPH
 };
 
-// Single-physics variants carry a minimum of one block per SM: the compiler then keeps their
-// state in registers instead of spilling it to local memory.
+// Every variant but the plain gravity + SPH one carries a minimum of one block per SM: the
+// compiler then keeps its state in registers instead of spilling it to local memory.
 template <bool GRAV, bool SPH, bool MIXED, bool CHECK>
-__global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH) ? 0 : 1) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED) ? 0 : 1) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
     const int lane = threadIdx.x & 31;
@@ -86,6 +122,7 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH) ? 0 : 1) k_walk(evol
         const float ie_i = gi.x, two_eps_i = GRAV && active ? 2.f / gi.x : 0.f;
         const float two_h_i = gas_i ? 2.f * gi.z : 0.f;
         const float inv_mi = valid ? 1.f / pi.w : 0.f;
+        const float eps_i = GRAV && valid ? 1.f / gi.x : 0.f;
 
         Acc<MIXED> acc;
         double tax = 0, tay = 0, taz = 0, tpot = 0, thx = 0, thy = 0, thz = 0, tdu = 0;
@@ -177,19 +214,21 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH) ? 0 : 1) k_walk(evol
                 const float dy = evol_wrap(pi.y - pj.y, plen1, pm & 2);
                 const float dz = evol_wrap(pi.z - pj.z, plen2, pm & 4);
                 const float r2 = dx * dx + dy * dy + dz * dz;
-                const float r = sqrtf(r2);
+                // r and 1/r from one reciprocal square root (coincident particles: both 0)
+                const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                const float r = r2 * rinv;
                 if (GRAV) {
-                    const float rinv = rsqrtf(r2);
                     const float ui = r * ie_i, uj = r * gj.x;
+                    const float iui = rinv * eps_i, iuj = rinv * rcp_fast(gj.x);
                     const float rinv3 = rinv * rinv * rinv;
-                    const float fi = ui < 2.f ? evol_gsoft_over_r(ui) * ie_i * ie_i * ie_i : rinv3;
-                    const float fj = uj < 2.f ? evol_gsoft_over_r(uj) * gj.x * gj.x * gj.x : rinv3;
+                    const float fi = ui < 2.f ? gsoft_over_r_u(ui, iui) * ie_i * ie_i * ie_i : rinv3;
+                    const float fj = uj < 2.f ? gsoft_over_r_u(uj, iuj) * gj.x * gj.x * gj.x : rinv3;
                     float f = -0.5f * pj.w * (fi + fj);
-                    acc.pot += pj.w * (ui < 2.f ? evol_phisoft(ui) * ie_i : -rinv);
+                    acc.pot += pj.w * (ui < 2.f ? phisoft_u(ui, iui) * ie_i : -rinv);
                     if (kp.adaptive) {
                         const float ie2 = ie_i * ie_i, je2 = gj.x * gj.x;
-                        const float ci = ui < 2.f ? gi.y * evol_dw_over_u(ui) * ie2 * ie2 * ie_i : 0.f;
-                        const float cj = uj < 2.f ? gj.y * evol_dw_over_u(uj) * je2 * je2 * gj.x : 0.f;
+                        const float ci = ui < 2.f ? gi.y * dw_over_u_u(ui, iui) * ie2 * ie2 * ie_i : 0.f;
+                        const float cj = uj < 2.f ? gj.y * dw_over_u_u(uj, iuj) * je2 * je2 * gj.x : 0.f;
                         f += -0.5f * inv_pi * (ci + pj.w * inv_mi * cj);
                     }
                     acc.ax += f * dx;
@@ -209,20 +248,21 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH) ? 0 : 1) k_walk(evol
                             const float4 sj = sm.ns[w][t];
                             const float ihi = si.z, ihj = sj.z;
                             const float uhi = r * ihi, uhj = r * ihj;
+                            const float iuhi = rinv * gi.z, iuhj = rinv * gj.z;     // h / r
                             const float ihi2 = ihi * ihi, ihj2 = ihj * ihj;
-                            const float kgi = (kp.use_tc ? evol_tc_over_u(uhi) : evol_dw_over_u(uhi)) * ihi2 * ihi2 * ihi * inv_pi;
-                            const float kgj = (kp.use_tc ? evol_tc_over_u(uhj) : evol_dw_over_u(uhj)) * ihj2 * ihj2 * ihj * inv_pi;
-                            const float fi = 1.f + gi.w / pj.w;       // 1 + zeta_i / (m_j Omega*_i)
+                            const float kgi = (kp.use_tc ? tc_over_u_u(uhi, iuhi) : dw_over_u_u(uhi, iuhi)) * ihi2 * ihi2 * ihi * inv_pi;
+                            const float kgj = (kp.use_tc ? tc_over_u_u(uhj, iuhj) : dw_over_u_u(uhj, iuhj)) * ihj2 * ihj2 * ihj * inv_pi;
+                            const float fi = 1.f + gi.w * rcp_fast(pj.w);     // 1 + zeta_i / (m_j Omega*_i)
                             const float fj = 1.f + gj.w * inv_mi;     // 1 + zeta_j / (m_i Omega*_j)
                             const float vx = hi.x - hj.x, vy = hi.y - hj.y, vz = hi.z - hj.z;
                             const float vr = vx * dx + vy * dy + vz * dz;
                             float visc = 0.f;
                             if (vr < 0.f) {
                                 const float hb = 0.5f * (gi.z + gj.z);
-                                const float mu = hb * vr / (r2 + 0.01f * hb * hb);
+                                const float mu = hb * vr * rcp_fast(r2 + 0.01f * hb * hb);
                                 const float cb = 0.5f * (si.x + sj.x);
                                 const float rb = 0.5f * (si.y + sj.y);
-                                visc = (-kp.alpha * cb * mu + kp.beta * mu * mu) / rb;
+                                visc = (-kp.alpha * cb * mu + kp.beta * mu * mu) * rcp_fast(rb);
                             }
                             const float gbar = 0.5f * (kgi * fi + kgj * fj);
                             const float pterm_i = hi.w * fi * kgi;
