@@ -197,81 +197,107 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED) ? 0 : 1) k
                 if (CHECK) sm.norig[w][l] = d.orig[j];
             }
             __syncwarp();
-            for (int t = 0; t < nnear; ++t) {
-                const unsigned msk = sm.near_mask[w][t];
-                const int j = sm.near_j[w][t];
-                const bool mine = ((msk >> lane) & 1u) && j != s;
-                {
-                    const int sl = j - g * 32;
-                    const unsigned self = (sl >= 0 && sl < 32) ? ((msk >> sl) & 1u) : 0u;
-                    wpp += __popc(msk) - self;
-                }
-                if (!mine) continue;
-                if (CHECK) ++cpp;
-                const float4 pj = sm.np[w][t];
-                const float4 gj = sm.ng[w][t];
-                const float dx = evol_wrap(pi.x - pj.x, plen0, pm & 1);
-                const float dy = evol_wrap(pi.y - pj.y, plen1, pm & 2);
-                const float dz = evol_wrap(pi.z - pj.z, plen2, pm & 4);
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                // r and 1/r from one reciprocal square root (coincident particles: both 0)
-                const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                const float r = r2 * rinv;
-                if (GRAV) {
-                    const float ui = r * ie_i, uj = r * gj.x;
-                    const float iui = rinv * eps_i, iuj = rinv * rcp_fast(gj.x);
-                    const float rinv3 = rinv * rinv * rinv;
-                    const float fi = ui < 2.f ? gsoft_over_r_u(ui, iui) * ie_i * ie_i * ie_i : rinv3;
-                    const float fj = uj < 2.f ? gsoft_over_r_u(uj, iuj) * gj.x * gj.x * gj.x : rinv3;
-                    float f = -0.5f * pj.w * (fi + fj);
-                    acc.pot += pj.w * (ui < 2.f ? phisoft_u(ui, iui) * ie_i : -rinv);
-                    if (kp.adaptive) {
-                        const float ie2 = ie_i * ie_i, je2 = gj.x * gj.x;
-                        const float ci = ui < 2.f ? gi.y * dw_over_u_u(ui, iui) * ie2 * ie2 * ie_i : 0.f;
-                        const float cj = uj < 2.f ? gj.y * dw_over_u_u(uj, iuj) * je2 * je2 * gj.x : 0.f;
-                        f += -0.5f * inv_pi * (ci + pj.w * inv_mi * cj);
+            // gravity for every pair; the SPH pairs are marked per lane (bit t of sbits) and
+            // evaluated afterwards, each lane taking its own pairs, so that a warp runs the SPH
+            // terms about as often as its busiest lane has SPH pairs
+            unsigned long long sbits = 0ull;
+            // two entries per step, branch-free: lanes outside an entry's mask (and the lane of
+            // the particle itself) take it with zero mass, so both chains can be in flight
+            for (int t = 0; t < nnear; t += 2) {
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const bool ok = t + hh < nnear;
+                    const int tt = ok ? t + hh : t;
+                    const unsigned msk = ok ? sm.near_mask[w][tt] : 0u;
+                    const int j = sm.near_j[w][tt];
+                    const bool mine = ((msk >> lane) & 1u) && j != s;
+                    {
+                        const int sl = j - g * 32;
+                        const unsigned self = (sl >= 0 && sl < 32) ? ((msk >> sl) & 1u) : 0u;
+                        wpp += __popc(msk) - self;
                     }
-                    acc.ax += f * dx;
-                    acc.ay += f * dy;
-                    acc.az += f * dz;
-                }
-                if (SPH && gas_i && gj.z > 0.f) {
-                    const float two_h = fmaxf(two_h_i, 2.f * gj.z);
-                    if (r2 < two_h * two_h) {
-                        if (CHECK) {
-                            ++csph;
-                            hsph += evol_mix64((unsigned long long)sm.norig[w][t]);
+                    if (CHECK && mine) ++cpp;
+                    const float4 pj = sm.np[w][tt];
+                    const float4 gj = sm.ng[w][tt];
+                    const float dx = evol_wrap(pi.x - pj.x, plen0, pm & 1);
+                    const float dy = evol_wrap(pi.y - pj.y, plen1, pm & 2);
+                    const float dz = evol_wrap(pi.z - pj.z, plen2, pm & 4);
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (GRAV) {
+                        const float mj = mine ? pj.w : 0.f;
+                        // r and 1/r from one reciprocal square root (coincident particles: both 0)
+                        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                        const float r = r2 * rinv;
+                        const float ui = r * ie_i, uj = r * gj.x;
+                        const float iui = rinv * eps_i, iuj = rinv * rcp_fast(gj.x);
+                        const float rinv3 = rinv * rinv * rinv;
+                        const float fi = ui < 2.f ? gsoft_over_r_u(ui, iui) * ie_i * ie_i * ie_i : rinv3;
+                        const float fj = uj < 2.f ? gsoft_over_r_u(uj, iuj) * gj.x * gj.x * gj.x : rinv3;
+                        float f = -0.5f * mj * (fi + fj);
+                        acc.pot += mj * (ui < 2.f ? phisoft_u(ui, iui) * ie_i : -rinv);
+                        if (kp.adaptive) {
+                            const float ie2 = ie_i * ie_i, je2 = gj.x * gj.x;
+                            const float ci = (mine && ui < 2.f) ? gi.y * dw_over_u_u(ui, iui) * ie2 * ie2 * ie_i : 0.f;
+                            const float cj = uj < 2.f ? gj.y * dw_over_u_u(uj, iuj) * je2 * je2 * gj.x : 0.f;
+                            f += -0.5f * inv_pi * (ci + mj * inv_mi * cj);
                         }
-                        ++wsph;
-                        if (r2 > 0.f) {
-                            const float4 hj = sm.nh[w][t];
-                            const float4 sj = sm.ns[w][t];
-                            const float ihi = si.z, ihj = sj.z;
-                            const float uhi = r * ihi, uhj = r * ihj;
-                            const float iuhi = rinv * gi.z, iuhj = rinv * gj.z;     // h / r
-                            const float ihi2 = ihi * ihi, ihj2 = ihj * ihj;
-                            const float kgi = (kp.use_tc ? tc_over_u_u(uhi, iuhi) : dw_over_u_u(uhi, iuhi)) * ihi2 * ihi2 * ihi * inv_pi;
-                            const float kgj = (kp.use_tc ? tc_over_u_u(uhj, iuhj) : dw_over_u_u(uhj, iuhj)) * ihj2 * ihj2 * ihj * inv_pi;
-                            const float fi = 1.f + gi.w * rcp_fast(pj.w);     // 1 + zeta_i / (m_j Omega*_i)
-                            const float fj = 1.f + gj.w * inv_mi;     // 1 + zeta_j / (m_i Omega*_j)
-                            const float vx = hi.x - hj.x, vy = hi.y - hj.y, vz = hi.z - hj.z;
-                            const float vr = vx * dx + vy * dy + vz * dz;
-                            float visc = 0.f;
-                            if (vr < 0.f) {
-                                const float hb = 0.5f * (gi.z + gj.z);
-                                const float mu = hb * vr * rcp_fast(r2 + 0.01f * hb * hb);
-                                const float cb = 0.5f * (si.x + sj.x);
-                                const float rb = 0.5f * (si.y + sj.y);
-                                visc = (-kp.alpha * cb * mu + kp.beta * mu * mu) * rcp_fast(rb);
+                        acc.ax += f * dx;
+                        acc.ay += f * dy;
+                        acc.az += f * dz;
+                    }
+                    if (SPH && mine && gas_i && gj.z > 0.f) {
+                        const float two_h = fmaxf(two_h_i, 2.f * gj.z);
+                        if (r2 < two_h * two_h) {
+                            if (CHECK) {
+                                ++csph;
+                                hsph += evol_mix64((unsigned long long)sm.norig[w][tt]);
                             }
-                            const float gbar = 0.5f * (kgi * fi + kgj * fj);
-                            const float pterm_i = hi.w * fi * kgi;
-                            const float sc = -pj.w * (pterm_i + hj.w * fj * kgj + visc * gbar);
-                            acc.hx += sc * dx;
-                            acc.hy += sc * dy;
-                            acc.hz += sc * dz;
-                            acc.du += pj.w * (pterm_i + 0.5f * visc * gbar) * vr;
+                            ++wsph;
+                            if (r2 > 0.f) sbits |= 1ull << tt;
                         }
+                    }
+                }
+            }
+            if (SPH) {
+                while (__any_sync(0xffffffffu, sbits != 0ull)) {
+                    if (sbits) {
+                        const int t = __ffsll((long long)sbits) - 1;
+                        sbits &= sbits - 1ull;
+                        const float4 pj = sm.np[w][t];
+                        const float4 gj = sm.ng[w][t];
+                        const float4 hj = sm.nh[w][t];
+                        const float4 sj = sm.ns[w][t];
+                        const float dx = evol_wrap(pi.x - pj.x, plen0, pm & 1);
+                        const float dy = evol_wrap(pi.y - pj.y, plen1, pm & 2);
+                        const float dz = evol_wrap(pi.z - pj.z, plen2, pm & 4);
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const float rinv = rsqrtf(r2);
+                        const float r = r2 * rinv;
+                        const float ihi = si.z, ihj = sj.z;
+                        const float uhi = r * ihi, uhj = r * ihj;
+                        const float iuhi = rinv * gi.z, iuhj = rinv * gj.z;     // h / r
+                        const float ihi2 = ihi * ihi, ihj2 = ihj * ihj;
+                        const float kgi = (kp.use_tc ? tc_over_u_u(uhi, iuhi) : dw_over_u_u(uhi, iuhi)) * ihi2 * ihi2 * ihi * inv_pi;
+                        const float kgj = (kp.use_tc ? tc_over_u_u(uhj, iuhj) : dw_over_u_u(uhj, iuhj)) * ihj2 * ihj2 * ihj * inv_pi;
+                        const float fi = 1.f + gi.w * rcp_fast(pj.w);     // 1 + zeta_i / (m_j Omega*_i)
+                        const float fj = 1.f + gj.w * inv_mi;             // 1 + zeta_j / (m_i Omega*_j)
+                        const float vx = hi.x - hj.x, vy = hi.y - hj.y, vz = hi.z - hj.z;
+                        const float vr = vx * dx + vy * dy + vz * dz;
+                        float visc = 0.f;
+                        if (vr < 0.f) {
+                            const float hb = 0.5f * (gi.z + gj.z);
+                            const float mu = hb * vr * rcp_fast(r2 + 0.01f * hb * hb);
+                            const float cb = 0.5f * (si.x + sj.x);
+                            const float rb = 0.5f * (si.y + sj.y);
+                            visc = (-kp.alpha * cb * mu + kp.beta * mu * mu) * rcp_fast(rb);
+                        }
+                        const float gbar = 0.5f * (kgi * fi + kgj * fj);
+                        const float pterm_i = hi.w * fi * kgi;
+                        const float sc = -pj.w * (pterm_i + hj.w * fj * kgj + visc * gbar);
+                        acc.hx += sc * dx;
+                        acc.hy += sc * dy;
+                        acc.hz += sc * dz;
+                        acc.du += pj.w * (pterm_i + 0.5f * visc * gbar) * vr;
                     }
                 }
             }
