@@ -39,6 +39,9 @@ FLOPS_FAR = 54
 FLOPS_PP = 60
 FLOPS_SPH = 85
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + written) per particle of one force-walk launch: ncu capture of k_walk<1,1,0,0>
+# on 2^18 DM + 2^17 gas (leaf 16, plain FP32): 38.09 MB read + 3.02 MB written, 393,216 particles
+WALK_DRAM_BYTES_PER_PARTICLE = (38.093056e6 + 3.023616e6) / 393216
 
 
 def log(*a):
@@ -414,6 +417,11 @@ def main():
                                  int(ds.params.leaf_size)))
 
     # ---- roofline of the dominant kernel (the force walk) ----
+    # DRAM bytes of one walk launch, scaled by particle count from an ncu capture of the same kernel
+    # on the 1/8-size mixed-species workload (leaf 16, plain FP32; profiles/k_walk_hernquist_1of8.md)
+    traffic = None
+    if args.workload in ("c3", "c3s") and prec == E.EVOL_FP32_PLAIN and int(ds.params.leaf_size) == 16:
+        traffic = WALK_DRAM_BYTES_PER_PARTICLE * w.n
     far, pp, sph = diag[12], diag[13], diag[14]
     flops = far * FLOPS_FAR + pp * FLOPS_PP + sph * FLOPS_SPH
     walk_s = statistics.mean(walk_ms) / 1e3
@@ -423,7 +431,8 @@ def main():
     achieved = flops / walk_s / 1e12
     clk = clocks["sm_mhz"] if clocks else None
     roofline = {"bound": "alu", "kernel": "k_walk (gravity + SPH force walk)", "achieved": achieved,
-                "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max, "traffic": None,
+                "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max, "traffic": traffic,
+                "traffic_basis": "ncu dram bytes of the 1/8-size capture scaled by particles" if traffic else None,
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
                 "frac_at_sampled_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12)) if clk else None,
                 "walk_ms": walk_s * 1e3,
