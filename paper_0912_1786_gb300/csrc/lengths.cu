@@ -3,9 +3,12 @@
 //
 // Each particle i needs the particles within its search radius R_i = 2 L_i (1 + 0.1).  A warp
 // takes 32 consecutive particles in key order and solves them one after the other, all 32 lanes
-// on one particle: the warp walks the tree from the particle's root, popping up to 32 nodes at a
-// time and opening those whose particle box comes within R_i; the leaves reached are listed in
-// shared memory, and their particles are then tested 32 at a time across the listed leaves.  The
+// on one particle.  For every 8 consecutive particles the warp first walks the tree once,
+// popping up to 32 nodes at a time and opening those whose particle box comes within
+// R_g = max R_i of the 8 particles' bounding box; the leaves reached are listed in shared memory.
+// A particle then tests the listed leaves against its own ball, and the particles of the leaves
+// that pass, 32 at a time across leaves.  A particle whose radius grows beyond R_g, or whose
+// group list overflowed, walks the tree on its own (same walk, from the particle's root).  The
 // neighbours found are appended, as (distance, mass) pairs, to a shared-memory list.
 // On that list the particle solves
 //     F(L) = L^3 n(L) - eta^3 = 0,   n(L) = sum_j W(r_ij, L)  (self term included)
@@ -27,8 +30,10 @@ namespace {
 
 constexpr int LW_THREADS = 128;
 constexpr int LW_WARPS = LW_THREADS / 32;
-constexpr int HCAP = 96;              // leaves listed per pass of a walk
-constexpr int PCAP = 448;             // neighbour entries of the particle being solved
+constexpr int HCAP = 96;              // leaves listed per pass of a particle's gather
+constexpr int PCAP = 400;             // neighbour entries of the particle being solved
+constexpr int SUB = 8;                // particles sharing one group walk
+constexpr int GCAP = 192;             // leaves in a group walk's list
 constexpr int MAX_ITERS = 60;
 constexpr int MAX_WALKS = 24;
 constexpr float SEARCH_MARGIN = 1.1f;
@@ -37,6 +42,9 @@ constexpr float CONV_TOL = 1e-6f;     // relative step below which one last eval
 enum { ST_DONE = 0, ST_ACTIVE = 1, ST_LAST = 2 };
 
 struct LenSmem {
+    float4 gc[LW_WARPS][GCAP];        // group list: leaf box centre (w unused)
+    float4 gh[LW_WARPS][GCAP];        // leaf box half widths
+    int2 gr[LW_WARPS][GCAP];          // leaf particle range [begin, end)
     int hb[LW_WARPS][HCAP + 1];       // listed leaves: exclusive prefix of their particle counts
     int hs[LW_WARPS][HCAP];           // and the first particle of each
     float2 nb[LW_WARPS][PCAP];        // (distance, mass) of the neighbours of the particle solved
@@ -194,8 +202,159 @@ __device__ int gather_ball(const evol_dev &d, const evol_kparams &kp, int *hb, i
     return cnt;
 }
 
+// Group walk: the leaves whose particle box comes within sqrt(R2) of the box (c, hw) (gas
+// leaves only in mode 0), from one root per system present among the `seed` lanes.  The
+// leaves go to the group list; returns their number, GCAP + 1 when they do not fit, or -1 when
+// the walk had to stop (corrupt tree or stack overflow; the error word is set).
 template <int MODE>
-__global__ void __launch_bounds__(LW_THREADS) k_lengths(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__device__ int collect_leaves(const evol_dev &d, const evol_kparams &kp, float4 *gc, float4 *gh, int2 *gr, int lane,
+                              int *stk, int stack_cap, long long pop_cap, float cx, float cy, float cz, float hx,
+                              float hy, float hz, float R2, int myroot, bool seed)
+{
+    const unsigned ltmask = (1u << lane) - 1u;
+    const float p0 = kp.plen[0], p1 = kp.plen[1], p2 = kp.plen[2];
+    const int pm = kp.periodic_mask;
+    int top = 0;
+    {
+        const unsigned peers = __match_any_sync(0xffffffffu, seed ? myroot : -1);
+        const bool leader = seed && (__ffs(peers) - 1) == lane;
+        const unsigned leaders = __ballot_sync(0xffffffffu, leader);
+        if (leader) stk[__popc(leaders & ltmask)] = myroot;
+        top = __popc(leaders);
+    }
+    __syncwarp();
+    int count = 0;
+    long long pops = 0;
+    while (top > 0) {
+        if (++pops > pop_cap) {
+            if (lane == 0) {
+                evol_flag(d.err, EVOL_ETIMEOUT);
+                atomicMax(&d.counters[7], 2ull);
+            }
+            return -1;
+        }
+        const int k = min(top, 32);
+        top -= k;
+        const int node = lane < k ? stk[top + lane] : -1;
+        __syncwarp();
+        bool open = false, leaf = false;
+        int4 I = make_int4(0, 0, 0, 0);
+        float4 B = make_float4(0.f, 0.f, 0.f, 0.f), C = B;
+        if (lane < k) {
+            I = d.nI[node];
+            B = d.nB[node];
+            C = d.nC[node];
+            if (MODE == 1 || B.w >= 0.f) {
+                const float ex = fmaxf(fabsf(evol_wrap(B.x - cx, p0, pm & 1)) - (C.x + hx), 0.f);
+                const float ey = fmaxf(fabsf(evol_wrap(B.y - cy, p1, pm & 2)) - (C.y + hy), 0.f);
+                const float ez = fmaxf(fabsf(evol_wrap(B.z - cz, p2, pm & 4)) - (C.z + hz), 0.f);
+                open = ex * ex + ey * ey + ez * ez < R2;
+            }
+            leaf = (I.x >> 8) & 1;
+        }
+        const unsigned lv = __ballot_sync(0xffffffffu, open && leaf);
+        if (open && leaf) {
+            const int e = count + __popc(lv & ltmask);
+            if (e < GCAP) {
+                gc[e] = B;
+                gh[e] = C;
+                gr[e] = make_int2(I.z, I.w);
+            }
+        }
+        count += __popc(lv);
+        if (count > GCAP) return GCAP + 1;
+        // opened internal nodes: push their children
+        const bool io = open && !leaf;
+        int nch = 0;
+        int ch[8];
+        if (io) {
+            const int4 K0 = d.nK0[node], K1 = d.nK1[node];
+            ch[0] = K0.x; ch[1] = K0.y; ch[2] = K0.z; ch[3] = K0.w;
+            ch[4] = K1.x; ch[5] = K1.y; ch[6] = K1.z; ch[7] = K1.w;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) nch += ch[t] >= 0 ? 1 : 0;
+        }
+        int incl = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (top + total > stack_cap) {
+            if (lane == 0) evol_flag(d.err, EVOL_EOVERFLOW);
+            return -1;
+        }
+        if (io) {
+            const int pos = top + incl - nch;
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if (t < nch) stk[pos + t] = ch[t];
+        }
+        top += total;
+        __syncwarp();
+    }
+    return count;
+}
+
+// A particle's gather from its group list: the listed leaves of its own system (particle range
+// inside [sbeg, send)) whose box comes within sqrt(R2) of (px, py, pz), then their particles.
+template <int MODE>
+__device__ int gather_from_list(const evol_dev &d, const evol_kparams &kp, const float4 *gc, const float4 *gh,
+                                const int2 *gr, int nleaf, int *hb, int *hs, float2 *nb, int lane, float px, float py,
+                                float pz, float R2, int sbeg, int send)
+{
+    const unsigned ltmask = (1u << lane) - 1u;
+    const float p0 = kp.plen[0], p1 = kp.plen[1], p2 = kp.plen[2];
+    const int pm = kp.periodic_mask;
+    int cnt = 0, nh = 0;
+    for (int base = 0; base < nleaf; base += 32) {
+        const int l = base + lane;
+        bool hit = false;
+        int2 r = make_int2(0, 0);
+        if (l < nleaf) {
+            r = gr[l];
+            const float4 B = gc[l], C = gh[l];
+            const float ex = fmaxf(fabsf(evol_wrap(B.x - px, p0, pm & 1)) - C.x, 0.f);
+            const float ey = fmaxf(fabsf(evol_wrap(B.y - py, p1, pm & 2)) - C.y, 0.f);
+            const float ez = fmaxf(fabsf(evol_wrap(B.z - pz, p2, pm & 4)) - C.z, 0.f);
+            hit = r.x >= sbeg && r.x < send && ex * ex + ey * ey + ez * ez < R2;
+        }
+        const unsigned hm = __ballot_sync(0xffffffffu, hit);
+        const int nl = __popc(hm);
+        if (nl) {
+            if (nh + nl > HCAP) {
+                __syncwarp();
+                cnt = gather_listed<MODE>(d, kp, hb, hs, nh, nb, cnt, px, py, pz, R2, lane);
+                __syncwarp();
+                nh = 0;
+            }
+            const int c = hit ? r.y - r.x : 0;
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int base_cnt = nh == 0 ? 0 : hb[nh];
+            __syncwarp();
+            if (hit) {
+                const int e = nh + __popc(hm & ltmask);
+                hs[e] = r.x;
+                hb[e] = base_cnt + incl - c;
+            }
+            if (lane == 31) hb[nh + nl] = base_cnt + incl;
+            nh += nl;
+            __syncwarp();
+        }
+    }
+    if (nh) cnt = gather_listed<MODE>(d, kp, hb, hs, nh, nb, cnt, px, py, pz, R2, lane);
+    __syncwarp();
+    return cnt;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ LenSmem sm;
     const int lane = threadIdx.x & 31;
@@ -228,6 +387,8 @@ __global__ void __launch_bounds__(LW_THREADS) k_lengths(evol_dev d, evol_kparams
         const int sys = valid ? d.sys_sorted[s] : 0;
         const float side = valid ? d.fcube[4 * sys + 3] : 1.f;     // the system's root cube
         const int root = act ? d.sys_root[sys] : -1;
+        // the system's particles in key order: [sbeg, send)
+        const int sbeg = act ? d.nbeg[root] : 0, send = act ? d.nend[root] : 0;
         float L0 = 0.f;
         if (act) {
             L0 = MODE == 0 ? d.len_h[s] : d.len_eps[s];
@@ -236,8 +397,35 @@ __global__ void __launch_bounds__(LW_THREADS) k_lengths(evol_dev d, evol_kparams
         int iters_total = 0;
         bool broken = false;
 
-        unsigned todo = todo0;
-        while (todo && !broken) {
+        for (int q = 0; q < 32 / SUB && !broken; ++q) {
+          const unsigned subm = todo0 & (((1u << SUB) - 1u) << (SUB * q));
+          if (!subm) continue;
+          // one walk for the SUB particles: their box and largest search radius
+          const bool insub = (subm >> lane) & 1u;
+          float gx0 = insub ? pi4.x : INFINITY, gy0 = insub ? pi4.y : INFINITY, gz0 = insub ? pi4.z : INFINITY;
+          float gx1 = insub ? pi4.x : -INFINITY, gy1 = insub ? pi4.y : -INFINITY, gz1 = insub ? pi4.z : -INFINITY;
+          float Rg = insub ? 2.f * L0 * SEARCH_MARGIN : 0.f;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+              gx0 = fminf(gx0, __shfl_xor_sync(0xffffffffu, gx0, o));
+              gy0 = fminf(gy0, __shfl_xor_sync(0xffffffffu, gy0, o));
+              gz0 = fminf(gz0, __shfl_xor_sync(0xffffffffu, gz0, o));
+              gx1 = fmaxf(gx1, __shfl_xor_sync(0xffffffffu, gx1, o));
+              gy1 = fmaxf(gy1, __shfl_xor_sync(0xffffffffu, gy1, o));
+              gz1 = fmaxf(gz1, __shfl_xor_sync(0xffffffffu, gz1, o));
+              Rg = fmaxf(Rg, __shfl_xor_sync(0xffffffffu, Rg, o));
+          }
+          const int nleaf = collect_leaves<MODE>(d, kp, sm.gc[w], sm.gh[w], sm.gr[w], lane, stk, stack_cap, pop_cap,
+                                                 0.5f * (gx0 + gx1), 0.5f * (gy0 + gy1), 0.5f * (gz0 + gz1),
+                                                 0.5f * (gx1 - gx0), 0.5f * (gy1 - gy0), 0.5f * (gz1 - gz0), Rg * Rg,
+                                                 root, insub);
+          if (nleaf < 0) {
+              broken = true;
+              break;
+          }
+          const bool glist = nleaf <= GCAP;
+          unsigned todo = subm;
+          while (todo && !broken) {
             const int t = __ffs(todo) - 1;
             todo &= todo - 1u;
             const float px = __shfl_sync(0xffffffffu, pi4.x, t);
@@ -245,6 +433,8 @@ __global__ void __launch_bounds__(LW_THREADS) k_lengths(evol_dev d, evol_kparams
             const float pz = __shfl_sync(0xffffffffu, pi4.z, t);
             const float sd = __shfl_sync(0xffffffffu, side, t);
             const int rt = __shfl_sync(0xffffffffu, root, t);
+            const int sb = __shfl_sync(0xffffffffu, sbeg, t);
+            const int se = __shfl_sync(0xffffffffu, send, t);
             float L = __shfl_sync(0xffffffffu, L0, t);
             // every lane holds the same solver state for particle t
             float lo = 0.f, hi = INFINITY, Rc = 0.f;
@@ -262,8 +452,12 @@ __global__ void __launch_bounds__(LW_THREADS) k_lengths(evol_dev d, evol_kparams
                     const float R2 = Rc * Rc;
                     cnt = 0;
                     __syncwarp();
-                    cnt = gather_ball<MODE>(d, kp, sm.hb[w], sm.hs[w], nb, lane, stk, stack_cap, pop_cap, rt, px,
-                                            py, pz, R2);
+                    if (glist && Rc <= Rg)
+                        cnt = gather_from_list<MODE>(d, kp, sm.gc[w], sm.gh[w], sm.gr[w], nleaf, sm.hb[w], sm.hs[w], nb,
+                                                     lane, px, py, pz, R2, sb, se);
+                    else
+                        cnt = gather_ball<MODE>(d, kp, sm.hb[w], sm.hs[w], nb, lane, stk, stack_cap, pop_cap, rt, px,
+                                                py, pz, R2);
                     if (cnt < 0) {
                         broken = true;
                         break;
@@ -357,6 +551,7 @@ __global__ void __launch_bounds__(LW_THREADS) k_lengths(evol_dev d, evol_kparams
                 }
             }
             iters_total += iters;
+          }
         }
         if (lane == 0) atomicAdd(&d.counters[3], (unsigned long long)iters_total);
         if (broken) break;
