@@ -62,32 +62,44 @@ __device__ __forceinline__ int gather_listed(const evol_dev &d, const evol_kpara
     const float p0 = kp.plen[0], p1 = kp.plen[1], p2 = kp.plen[2];
     const int pm = kp.periodic_mask;
     const int total = hb[nh];
-    for (int c0 = 0; c0 < total; c0 += 32) {
-        const int x = c0 + lane;
-        bool in = false;
-        float r2 = 0.f, m = 0.f;
-        if (x < total) {
-            // the listed leaf holding flattened index x: last k with hb[k] <= x
-            int lo = 0, hi = nh - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (hb[mid] <= x) lo = mid; else hi = mid - 1;
+    constexpr int U = 2;              // chunks whose loads are issued together (more costs occupancy)
+    for (int c0 = 0; c0 < total; c0 += 32 * U) {
+        int jj[U];
+#pragma unroll
+        for (int h = 0; h < U; ++h) {
+            const int x = c0 + 32 * h + lane;
+            jj[h] = -1;
+            if (x < total) {
+                // the listed leaf holding flattened index x: last k with hb[k] <= x
+                int lo = 0, hi = nh - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (hb[mid] <= x) lo = mid; else hi = mid - 1;
+                }
+                jj[h] = hs[lo] + (x - hb[lo]);
             }
-            const int j = hs[lo] + (x - hb[lo]);
-            const float4 pj = d.pos[j];
-            const float dx = evol_wrap(px - pj.x, p0, pm & 1);
-            const float dy = evol_wrap(py - pj.y, p1, pm & 2);
-            const float dz = evol_wrap(pz - pj.z, p2, pm & 4);
-            r2 = dx * dx + dy * dy + dz * dz;
-            m = pj.w;
-            in = r2 < R2 && (MODE == 1 || d.orig[j] < kp.n_gas);
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, in);
-        if (in) {
-            const int e = cnt + __popc(bal & ltmask);
-            if (e < PCAP) nb[e] = make_float2(sqrtf(r2), m);
+        float4 pj[U];
+        bool gas[U];
+#pragma unroll
+        for (int h = 0; h < U; ++h) {
+            pj[h] = jj[h] >= 0 ? d.pos[jj[h]] : make_float4(0.f, 0.f, 0.f, -1.f);
+            gas[h] = MODE == 1 || (jj[h] >= 0 && d.orig[jj[h]] < kp.n_gas);
         }
-        cnt += __popc(bal);
+#pragma unroll
+        for (int h = 0; h < U; ++h) {
+            const float dx = evol_wrap(px - pj[h].x, p0, pm & 1);
+            const float dy = evol_wrap(py - pj[h].y, p1, pm & 2);
+            const float dz = evol_wrap(pz - pj[h].z, p2, pm & 4);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const bool in = jj[h] >= 0 && r2 < R2 && gas[h];
+            const unsigned bal = __ballot_sync(0xffffffffu, in);
+            if (in) {
+                const int e = cnt + __popc(bal & ltmask);
+                if (e < PCAP) nb[e] = make_float2(sqrtf(r2), pj[h].w);
+            }
+            cnt += __popc(bal);
+        }
     }
     return cnt;
 }
