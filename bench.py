@@ -394,7 +394,23 @@ def main():
         d2h = sum(int(t.numel()) * 4 for t in host_out.values()) + (w.n_gas + w.n) * 4
         ke = max(1, min(args.steps, 5))
         h0, e0 = host_in["h"].clone(), host_in["eps"].clone()
-        E.evol_step_host(ctx, hp, ds.params, ho)           # warm (captures the host-path graph)
+
+        def host_step():
+            if offsets is None:
+                E.evol_step_host(ctx, hp, ds.params, ho)
+                return
+            # independent systems: no host-buffer entry point takes offsets, so the inputs are
+            # copied to the device set, the batched step runs, and the outputs come back
+            for k, t in host_in.items():
+                ds.inp[k].copy_(t[: ds.inp[k].numel()], non_blocking=True)
+            E.evol_step_batched(ctx, offsets, ds.particles, ds.params, ds.outputs)
+            for k, t in host_out.items():
+                t.copy_(ds.out[k][: t.numel()], non_blocking=True)
+            for k in ("h", "eps"):
+                host_in[k][: ds.inp[k].numel()].copy_(ds.inp[k], non_blocking=True)
+            E.evol_sync(ctx)
+
+        host_step()                                        # warm (captures the host-path graph)
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
@@ -402,7 +418,7 @@ def main():
         for _ in range(ke):
             host_in["h"].copy_(h0)
             host_in["eps"].copy_(e0)
-            E.evol_step_host(ctx, hp, ds.params, ho)
+            host_step()
         te = time.perf_counter() - t0
         if dist:
             t = torch.tensor([te], device=dev)
