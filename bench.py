@@ -369,14 +369,9 @@ def main():
         dist.barrier()
     ms = t_start.elapsed_time(t_end)
     clocks = sampler.stop()
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    value, ms_max = replica_rate(dist, dev, ms, w.n, args.steps, world)
     diag = E.evol_get_diagnostics(ctx)
     n_total = w.n * world
-    value = n_total * args.steps / (ms_max / 1e3)
 
     # ---- e2e through the host-buffer entry point (pinned host memory) ----
     e2e = None
@@ -499,6 +494,19 @@ def launches_per_step(w):
     k += 1 if (p.sph and w.n_gas) else 0
     k += 1 + 2 + 1 + 1 + 2
     return k
+
+
+def replica_rate(dist, device, ms_local, units_per_rank, steps, world):
+    """Whole-job rate of `world` independent replicas (one system does not shard on this path):
+    the units all ranks processed over the slowest rank's time (max over ranks).  Returns the rate
+    in units/s and that time in ms."""
+    ms_max = ms_local
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(ms_local)], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    return units_per_rank * world * steps / (ms_max / 1e3), ms_max
 
 
 if __name__ == "__main__":
