@@ -154,13 +154,13 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED) ? 0 : 1) k
                 sm.fA[w][l] = d.nA[id];
                 sm.fQ0[w][l] = d.nQ0[id];
                 sm.fQ1[w][l] = d.nQ1[id];
+                wfar += __popc(sm.far_mask[w][l]);     // interaction count (this lane's share)
             }
             __syncwarp();
             for (int e = 0; e < padded; e += 4) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const unsigned msk = sm.far_mask[w][e + u];
-                    wfar += __popc(msk);
                     const float4 A = sm.fA[w][e + u], Q0 = sm.fQ0[w][e + u], Q1 = sm.fQ1[w][e + u];
                     const float dx = pi.x - A.x, dy = pi.y - A.y, dz = pi.z - A.z;
                     const float d2 = dx * dx + dy * dy + dz * dz;
@@ -188,6 +188,13 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED) ? 0 : 1) k
             __syncwarp();
             for (int l = lane; l < nnear; l += 32) {
                 const int j = sm.near_j[w][l];
+                {
+                    // interaction count (this lane's share): the entry's lanes, less the particle itself
+                    const unsigned msk = sm.near_mask[w][l];
+                    const int sl = j - g * 32;
+                    const unsigned self = (sl >= 0 && sl < 32) ? ((msk >> sl) & 1u) : 0u;
+                    wpp += __popc(msk) - self;
+                }
                 sm.np[w][l] = d.pos[j];
                 sm.ng[w][l] = d.grav[j];
                 if (SPH) {
@@ -211,11 +218,6 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED) ? 0 : 1) k
                     const unsigned msk = ok ? sm.near_mask[w][tt] : 0u;
                     const int j = sm.near_j[w][tt];
                     const bool mine = ((msk >> lane) & 1u) && j != s;
-                    {
-                        const int sl = j - g * 32;
-                        const unsigned self = (sl >= 0 && sl < 32) ? ((msk >> sl) & 1u) : 0u;
-                        wpp += __popc(msk) - self;
-                    }
                     if (CHECK && mine) ++cpp;
                     const float4 pj = sm.np[w][tt];
                     const float4 gj = sm.ng[w][tt];
@@ -554,13 +556,17 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED) ? 0 : 1) k
                 d.cnt3[3 * s + 2] = csph;
             }
         }
-        // interaction counters: wfar / wpp are warp-uniform; wsph is per lane
-        unsigned long long ws = wsph;
+        // interaction counters, per lane: summed over the warp
+        unsigned long long wf = wfar, wp = wpp, ws = wsph;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            wf += __shfl_xor_sync(0xffffffffu, wf, o);
+            wp += __shfl_xor_sync(0xffffffffu, wp, o);
+            ws += __shfl_xor_sync(0xffffffffu, ws, o);
+        }
         if (lane == 0) {
-            atomicAdd(&d.counters[0], wfar);
-            atomicAdd(&d.counters[1], wpp);
+            atomicAdd(&d.counters[0], wf);
+            atomicAdd(&d.counters[1], wp);
             atomicAdd(&d.counters[2], ws);
         }
     }
