@@ -40,8 +40,8 @@ FLOPS_PP = 60
 FLOPS_SPH = 85
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + written) per particle of one force-walk launch: ncu capture of k_walk<1,1,0,0>
-# on 2^18 DM + 2^17 gas (leaf 16, plain FP32): 38.09 MB read + 3.02 MB written, 393,216 particles
-WALK_DRAM_BYTES_PER_PARTICLE = (38.093056e6 + 3.023616e6) / 393216
+# on 2^18 DM + 2^17 gas (leaf 16, plain FP32): 38.09 MB read + 2.62 MB written, 393,216 particles
+WALK_DRAM_BYTES_PER_PARTICLE = (38.090240e6 + 2.622976e6) / 393216
 
 
 def log(*a):
