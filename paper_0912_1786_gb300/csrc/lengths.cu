@@ -31,7 +31,7 @@ namespace {
 constexpr int LW_THREADS = 128;
 constexpr int LW_WARPS = LW_THREADS / 32;
 constexpr int HCAP = 96;              // leaves listed per pass of a particle's gather
-constexpr int PCAP = 400;             // neighbour entries of the particle being solved
+constexpr int PCAP = 336;             // neighbour entries of the particle being solved
 constexpr int SUB = 8;                // particles sharing one group walk
 constexpr int GCAP = 192;             // leaves in a group walk's list
 constexpr int MAX_ITERS = 60;
