@@ -92,10 +92,11 @@ struct Acc {
     float hx = 0.f, hy = 0.f, hz = 0.f, du = 0.f;       // SPH
 };
 
-// Every variant but the plain gravity + SPH one carries a minimum of one block per SM: the
-// compiler then keeps its state in registers instead of spilling it to local memory.
+// Register budgets: the plain gravity + SPH walk (the production form) fits five blocks per SM
+// (at most 102 registers) without spilling; every other variant carries a minimum of one block
+// per SM, so that the compiler keeps its state in registers instead of spilling to local memory.
 template <bool GRAV, bool SPH, bool MIXED, bool CHECK>
-__global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED) ? 0 : 1) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) ? 5 : 1) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
     const int lane = threadIdx.x & 31;
@@ -114,15 +115,16 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED) ? 0 : 1) k
         const int s = g * 32 + lane;
         const bool valid = s < n;
         const float4 pi = valid ? d.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 gi = valid ? d.grav[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 hi = (valid && SPH) ? d.hydro[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 si = (valid && SPH) ? d.snd[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const bool gas_i = SPH && valid && gi.z > 0.f;
+        // this lane's hydro operands (v, P/rho^2, c, rho, 1/h, zeta/Omega*) are read where they are
+        // used, in the SPH pass, which keeps them out of the traversal's live registers
+        const float4 g0 = valid ? d.grav[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float xu_i = g0.y;                   // X/Upsilon (adaptive-softening correction)
+        const bool gas_i = SPH && valid && g0.z > 0.f;
         const bool active = valid && (GRAV || gas_i);
-        const float ie_i = gi.x, two_eps_i = GRAV && active ? 2.f / gi.x : 0.f;
-        const float two_h_i = gas_i ? 2.f * gi.z : 0.f;
+        const float ie_i = g0.x, two_eps_i = GRAV && active ? 2.f / g0.x : 0.f;
+        const float two_h_i = gas_i ? 2.f * g0.z : 0.f;
         const float inv_mi = valid ? 1.f / pi.w : 0.f;
-        const float eps_i = GRAV && valid ? 1.f / gi.x : 0.f;
+        const float eps_i = GRAV && valid ? 1.f / ie_i : 0.f;
 
         Acc<MIXED> acc;
         double tax = 0, tay = 0, taz = 0, tpot = 0, thx = 0, thy = 0, thz = 0, tdu = 0;
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED) ? 0 : 1) k
                         acc.pot += mj * (ui < 2.f ? phisoft_u(ui, iui) * ie_i : -rinv);
                         if (kp.adaptive) {
                             const float ie2 = ie_i * ie_i, je2 = gj.x * gj.x;
-                            const float ci = (mine && ui < 2.f) ? gi.y * dw_over_u_u(ui, iui) * ie2 * ie2 * ie_i : 0.f;
+                            const float ci = (mine && ui < 2.f) ? xu_i * dw_over_u_u(ui, iui) * ie2 * ie2 * ie_i : 0.f;
                             const float cj = uj < 2.f ? gj.y * dw_over_u_u(uj, iuj) * je2 * je2 * gj.x : 0.f;
                             f += -0.5f * inv_pi * (ci + mj * inv_mi * cj);
                         }
@@ -260,7 +262,10 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED) ? 0 : 1) k
                     }
                 }
             }
-            if (SPH) {
+            if (SPH && __any_sync(0xffffffffu, sbits != 0ull)) {
+                const float4 gi = d.grav[s];       // sbits != 0 only on valid gas lanes
+                const float4 hi = d.hydro[s];
+                const float4 si = d.snd[s];
                 while (__any_sync(0xffffffffu, sbits != 0ull)) {
                     if (sbits) {
                         const int t = __ffsll((long long)sbits) - 1;
@@ -545,7 +550,8 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED) ? 0 : 1) k
             d.acc[s] = make_float4(ax, ay, az, pot);
             if (SPH) {
                 d.dudt[s] = gas_i ? (float)tdu : 0.f;
-                d.vah[s] = gas_i ? (float)(hi.x * thx + hi.y * thy + hi.z * thz) : 0.f;
+                const float4 hv = d.hydro[s];
+                d.vah[s] = gas_i ? (float)(hv.x * thx + hv.y * thy + hv.z * thz) : 0.f;
             }
             if (CHECK) {
                 d.hash3[3 * s + 0] = hfar;
