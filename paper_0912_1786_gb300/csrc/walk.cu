@@ -263,9 +263,11 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
                 }
             }
             if (SPH && __any_sync(0xffffffffu, sbits != 0ull)) {
-                const float4 gi = d.grav[s];       // sbits != 0 only on valid gas lanes
-                const float4 hi = d.hydro[s];
-                const float4 si = d.snd[s];
+                // every lane of the warp runs this pass; lanes past the end read nothing
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 gi = valid ? d.grav[s] : z4;
+                const float4 hi = valid ? d.hydro[s] : z4;
+                const float4 si = valid ? d.snd[s] : z4;
                 while (__any_sync(0xffffffffu, sbits != 0ull)) {
                     if (sbits) {
                         const int t = __ffsll((long long)sbits) - 1;
