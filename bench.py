@@ -39,9 +39,10 @@ FLOPS_FAR = 54
 FLOPS_PP = 60
 FLOPS_SPH = 85
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + written) per particle of one force-walk launch: ncu capture of k_walk<1,1,0,0>
-# on 2^18 DM + 2^17 gas (leaf 16, plain FP32): 38.09 MB read + 2.62 MB written, 393,216 particles
-WALK_DRAM_BYTES_PER_PARTICLE = (38.090240e6 + 2.622976e6) / 393216
+# DRAM bytes (read + written) per particle of one force-walk launch, by leaf size: ncu capture of
+# k_walk<1,1,0,0> on 2^18 DM + 2^17 gas (plain FP32), 393,216 particles; leaf 16: 38.81 MB read +
+# 3.20 MB written; leaf 24: 35.29 MB + 2.66 MB
+WALK_DRAM_BYTES_PER_PARTICLE = {16: (38.809088e6 + 3.197440e6) / 393216, 24: (35.294720e6 + 2.662144e6) / 393216}
 
 
 def log(*a):
@@ -429,10 +430,11 @@ def main():
 
     # ---- roofline of the dominant kernel (the force walk) ----
     # DRAM bytes of one walk launch, scaled by particle count from an ncu capture of the same kernel
-    # on the 1/8-size mixed-species workload (leaf 16, plain FP32; profiles/k_walk_hernquist_1of8.md)
+    # on the 1/8-size mixed-species workload (plain FP32; profiles/k_walk_hernquist_1of8.md)
     traffic = None
-    if args.workload in ("c3", "c3s") and prec == E.EVOL_FP32_PLAIN and int(ds.params.leaf_size) == 16:
-        traffic = WALK_DRAM_BYTES_PER_PARTICLE * w.n
+    leaf_used = int(ds.params.leaf_size)
+    if args.workload in ("c3", "c3s") and prec == E.EVOL_FP32_PLAIN and leaf_used in WALK_DRAM_BYTES_PER_PARTICLE:
+        traffic = WALK_DRAM_BYTES_PER_PARTICLE[leaf_used] * w.n
     far, pp, sph = diag[12], diag[13], diag[14]
     flops = far * FLOPS_FAR + pp * FLOPS_PP + sph * FLOPS_SPH
     walk_s = statistics.mean(walk_ms) / 1e3
