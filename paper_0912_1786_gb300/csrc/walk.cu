@@ -55,20 +55,25 @@ struct WalkSmem {
 // from quantities already at hand (eps/r, h/r).  Same polynomials as the FP32 kernel functions:
 //   gsoft_over_r: eps^3 phi'(r)/r,  phisoft: eps phi(r),  dw_over_u: pi h^5 (dW/dr)/r,
 //   tc_over_u: the Thomas-Couchman form of the latter.
+// The two branches share one Horner form in u whose coefficients are selected by u < 1.
 __device__ __forceinline__ float gsoft_over_r_u(float u, float iu)
 {
-    const float u2 = u * u;
-    const float in = 4.f / 3.f - 1.2f * u2 + 0.5f * u2 * u;
-    const float out = 8.f / 3.f - 3.f * u + 1.2f * u2 - u2 * u * (1.f / 6.f) - (1.f / 15.f) * iu * iu * iu;
-    return u < 1.f ? in : out;
+    // u < 1: 4/3 - 6/5 u^2 + 1/2 u^3;   1 <= u < 2: 8/3 - 3u + 6/5 u^2 - 1/6 u^3 - 1/(15 u^3)
+    const bool in = u < 1.f;
+    const float c1 = in ? 0.f : -3.f, c2 = in ? -1.2f : 1.2f, c3 = in ? 0.5f : -1.f / 6.f;
+    const float c0 = in ? 4.f / 3.f : 8.f / 3.f, e = in ? 0.f : -1.f / 15.f;
+    return fmaf(u, fmaf(u, fmaf(u, c3, c2), c1), c0) + e * (iu * iu * iu);
 }
 
 __device__ __forceinline__ float phisoft_u(float u, float iu)
 {
+    // u < 1: -7/5 + 2/3 u^2 - 3/10 u^4 + 1/10 u^5
+    // 1 <= u < 2: -8/5 + 4/3 u^2 - u^3 + 3/10 u^4 - 1/30 u^5 + 1/(15 u)
+    const bool in = u < 1.f;
+    const float c2 = in ? 2.f / 3.f : 4.f / 3.f, c3 = in ? 0.f : -1.f, c4 = in ? -0.3f : 0.3f;
+    const float c5 = in ? 0.1f : -1.f / 30.f, c0 = in ? -1.4f : -1.6f, e = in ? 0.f : 1.f / 15.f;
     const float u2 = u * u;
-    const float in = (2.f / 3.f) * u2 - 0.3f * u2 * u2 + 0.1f * u2 * u2 * u - 1.4f;
-    const float out = (4.f / 3.f) * u2 - u2 * u + 0.3f * u2 * u2 - u2 * u2 * u * (1.f / 30.f) - 1.6f + (1.f / 15.f) * iu;
-    return u < 1.f ? in : out;
+    return fmaf(u2, fmaf(u, fmaf(u, fmaf(u, c5, c4), c3), c2), c0) + e * iu;
 }
 
 __device__ __forceinline__ float dw_over_u_u(float u, float iu)
