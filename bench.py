@@ -40,9 +40,9 @@ FLOPS_PP = 60
 FLOPS_SPH = 85
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + written) per particle of one force-walk launch, by leaf size: ncu capture of
-# k_walk<1,1,0,0> on 2^18 DM + 2^17 gas (plain FP32), 393,216 particles; leaf 16: 38.81 MB read +
-# 3.20 MB written; leaf 24: 35.29 MB + 2.66 MB
-WALK_DRAM_BYTES_PER_PARTICLE = {16: (38.809088e6 + 3.197440e6) / 393216, 24: (35.294720e6 + 2.662144e6) / 393216}
+# k_walk<1,1,0,0> on 2^18 DM + 2^17 gas (plain FP32), 393,216 particles; leaf 16: 39.10 MB read +
+# 3.40 MB written; leaf 24: 35.32 MB + 2.68 MB
+WALK_DRAM_BYTES_PER_PARTICLE = {16: (39.099648e6 + 3.401728e6) / 393216, 24: (35.320064e6 + 2.677248e6) / 393216}
 
 
 def log(*a):
