@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
     int *stk = reinterpret_cast<int *>(d.wstack + (size_t)wslot * kp.stack_cap);
     const int stack_cap = 2 * kp.stack_cap;
     const int n = kp.n;
-    const int ngroups = (n + 31) >> 5;
+    const int ngroups = (n + SUB - 1) / SUB;       // the queue hands out SUB particles at a time
     const float eta = MODE == 0 ? kp.eta_h : kp.eta_e;
     const float eta3 = eta * eta * eta;
     const float inv_pi = 1.f / EVOL_PI_F;
@@ -389,8 +389,8 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
         if (lane == 0) g = (int)atomicAdd(queue, 1ull);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ngroups) break;
-        const int s = g * 32 + lane;
-        const bool valid = s < n;
+        const int s = g * SUB + lane;                 // lanes 0 .. SUB-1 hold the particles
+        const bool valid = lane < SUB && s < n;
         const float4 pi4 = valid ? d.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
         const bool gas_i = valid && d.orig[s] < kp.n_gas;
         const bool act = MODE == 0 ? gas_i : valid;
@@ -409,9 +409,8 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
         int iters_total = 0;
         bool broken = false;
 
-        for (int q = 0; q < 32 / SUB && !broken; ++q) {
-          const unsigned subm = todo0 & (((1u << SUB) - 1u) << (SUB * q));
-          if (!subm) continue;
+        do {                                           // one group walk for the SUB particles
+          const unsigned subm = todo0;
           // one walk for the SUB particles: their box and largest search radius
           const bool insub = (subm >> lane) & 1u;
           float gx0 = insub ? pi4.x : INFINITY, gy0 = insub ? pi4.y : INFINITY, gz0 = insub ? pi4.z : INFINITY;
@@ -516,7 +515,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                 if (MODE == 0) Smuw = __shfl_sync(0xffffffffu, Smuw, 0);
                 if (status == ST_LAST) {
                     if (lane == t) {
-                        const int si = g * 32 + t;
+                        const int si = g * SUB + t;
                         const float nsum = Sw * inv_pi * Linv * Linv * Linv;
                         if (MODE == 0) {
                             d.len_h[si] = L;
@@ -556,7 +555,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                     if (L > 4.f * sd) {               // no root: fewer neighbours than required
                         if (lane == 0) evol_flag(d.err, EVOL_ENOCONV);
                         if (lane == t) {
-                            if (MODE == 0) d.len_h[g * 32 + t] = L; else d.len_eps[g * 32 + t] = L;
+                            if (MODE == 0) d.len_h[g * SUB + t] = L; else d.len_eps[g * SUB + t] = L;
                         }
                         status = ST_DONE;
                     }
@@ -564,7 +563,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
             }
             iters_total += iters;
           }
-        }
+        } while (0);
         if (lane == 0) atomicAdd(&d.counters[3], (unsigned long long)iters_total);
         if (broken) break;
     }
