@@ -2,10 +2,10 @@
 // densitySPH, drhodr; Sect. 3.1 "gather" view with an enlarged search radius).
 //
 // Each particle i needs the particles within its search radius R_i = 2 L_i (1 + 0.1).  A warp
-// takes 32 consecutive particles in key order and solves them one after the other, all 32 lanes
-// on one particle.  For every 8 consecutive particles the warp first walks the tree once,
-// popping up to 32 nodes at a time and opening those whose particle box comes within
-// R_g = max R_i of the 8 particles' bounding box; the leaves reached are listed in shared memory.
+// takes 8 consecutive particles in key order and solves them one after the other, all 32 lanes
+// on one particle.  For the 8 particles the warp first walks the tree once, popping up to 32
+// nodes at a time and opening those whose particle box comes within R_g = max R_i of the 8
+// particles' bounding box; the leaves reached are listed in shared memory.
 // A particle then tests the listed leaves against its own ball, and the particles of the leaves
 // that pass, 32 at a time across leaves.  A particle whose radius grows beyond R_g, or whose
 // group list overflowed, walks the tree on its own (same walk, from the particle's root).  The
