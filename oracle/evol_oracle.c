@@ -639,14 +639,20 @@ typedef struct {
     double ahyd[3];
     uint64_t hfar, hnear, hsph;
     int64_t nfar, npp, nsph;
-    double margin;      /* smallest relative distance of any decision from its threshold */
+    double margin;      /* smallest distance of any decision from its threshold, relative to
+                           (threshold + coordinate scale of the particle) */
+    double scale;       /* max |coordinate| of the particle: the scale of FP32 position rounding */
     double aabs, duabs; /* sums of the magnitudes of the individual contributions to a and du/dt */
 } orc_result;
 
+/* Distance of one decision (value v against threshold thr) from its threshold.  It is taken
+ * relative to thr + the particle's coordinate scale: an FP32 evaluation of the same test rounds
+ * positions, centres of mass and box bounds on the scale of the coordinates and the threshold on
+ * its own scale, so a decision closer than a few FP32 ulps of that sum can go either way. */
 static void orc_margin(orc_result *res, double v, double thr)
 {
     if (thr > 0 && isfinite(thr)) {
-        double mg = fabs(v - thr) / thr;
+        double mg = fabs(v - thr) / (thr + res->scale);
         if (mg < res->margin) res->margin = mg;
     }
 }
@@ -779,6 +785,7 @@ static void orc_force_one(const orc_tree *t, const orc_params *pr, const orc_per
     memset(res, 0, sizeof *res);
     res->margin = INFINITY;
     double p[3] = {t->x[i], t->y[i], t->z[i]};
+    res->scale = fmax(fabs(p[0]), fmax(fabs(p[1]), fabs(p[2])));
     int64_t id = 0, nn = t->nnodes;
     /* Pre-order walk; nnext skips a subtree. */
     while (id < nn) {

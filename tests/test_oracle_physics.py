@@ -288,3 +288,76 @@ def test_length_solve_independent_of_guess_and_fails_without_root():
     t4 = oracle.OracleTree(w.x[:4], w.y[:4], w.z[:4], w.m[:4], 4, 1)
     with pytest.raises(RuntimeError):
         t4.solve_lengths(0, 50.0)
+
+
+# ---- Monaghan viscosity (Sect. 3.3.1, Eq. mu_visc) ----------------------------------------------
+# Two gas particles on the x axis approach head-on with speed s; the pressure is switched off
+# (P = 0 in the force pass's state) so that only the viscosity acts.  With v_ij . r_ij = -s r the
+# paper's Pi_ij = (-alpha cbar mu + beta mu^2) / rhobar, mu = hbar v_ij.r_ij / (r^2 + eta^2),
+# eta^2 = 0.01 hbar^2, makes the acceleration of particle i a quadratic a(s) = A s + B s^2 whose
+# kernel-gradient factor cancels in B/A = beta kappa / (alpha cbar), kappa = hbar r / (r^2 + eta^2).
+# From two speeds the tests recover eta^2 and the means independently of the kernel gradient.
+_VR = 0.375                 # separation (exact in float32)
+
+
+def _visc_pair(s, h=(0.25, 0.3125), c=(0.5, 1.5), rho=(1.0, 3.0), m=(0.5, 0.75), alpha=1.0, beta=2.0):
+    P = np.array([[0.5 * _VR, 0.0, 0.0], [-0.5 * _VR, 0.0, 0.0]])
+    v = np.array([[-0.5 * s, 0.0, 0.0], [0.5 * s, 0.0, 0.0]])
+    p = W.Params(theta=0.5, gravity=0, sph=1, adaptive_softening=0, leaf_size=1, alpha=alpha, beta=beta)
+    w = _wl(P, np.asarray(m, np.float64), 2, v=v, u=np.full(2, 1.0), params=p, h=np.asarray(h))
+    st = dict(h=np.asarray(h, np.float64), rho=np.asarray(rho, np.float64), P=np.zeros(2),
+              c=np.asarray(c, np.float64), omega=np.ones(2), zeta=np.zeros(2))
+    r = oracle.force_step(w, params=p, fixed_lengths=st)
+    return r["ax"][0], r["dudt"][0]
+
+
+def _quadratic_coeffs(**kw):
+    a1, _ = _visc_pair(1.0, **kw)
+    a2, _ = _visc_pair(2.0, **kw)
+    B = 0.5 * (a2 - 2.0 * a1)
+    return a1 - B, B
+
+
+def test_viscosity_softening_constant_and_means():
+    h, c = (0.25, 0.3125), (0.5, 1.5)
+    A, B = _quadratic_coeffs(h=h, c=c)
+    alpha, beta = 1.0, 2.0
+    hbar, cbar = 0.5 * (h[0] + h[1]), 0.5 * (c[0] + c[1])      # arithmetic means of Sect. 3.3.1
+    kappa = (B / A) * alpha * cbar / beta
+    eta2 = hbar * _VR / kappa - _VR ** 2
+    # eta = 0.1 h (Sect. 3.3.1): eta^2 = 0.01 hbar^2; 0.1 hbar^2, a geometric hbar or a cbar taken
+    # as max(c_i, c_j) give 0.05, 0.0100-0.0011 shifted, or a 40 % larger kappa respectively
+    assert abs(eta2 / hbar ** 2 - 0.01) < 1e-9, eta2 / hbar ** 2
+    # the viscous force pushes the approaching particle back (i sits at +x)
+    assert A > 0 and B > 0
+
+
+def test_viscosity_density_mean_is_arithmetic():
+    a13, _ = _visc_pair(1.0, rho=(1.0, 3.0))
+    a22, _ = _visc_pair(1.0, rho=(2.0, 2.0))
+    a11, _ = _visc_pair(1.0, rho=(1.0, 1.0))
+    # same arithmetic mean -> same force (a geometric mean would differ by 2/sqrt(3), a harmonic by 4/3)
+    assert abs(a13 - a22) <= 1e-14 * abs(a22)
+    # Pi ~ 1/rhobar
+    assert abs(a11 / a22 - 2.0) < 1e-13
+
+
+def test_viscosity_sound_speed_mean_is_arithmetic():
+    # alpha term only: a ~ cbar, so (c_i, c_j) = (0.5, 1.5) and (1, 1) agree; max(c) would not
+    a1, _ = _visc_pair(1.0, c=(0.5, 1.5), beta=0.0)
+    a2, _ = _visc_pair(1.0, c=(1.0, 1.0), beta=0.0)
+    assert abs(a1 - a2) <= 1e-14 * abs(a2)
+
+
+def test_viscous_heating_is_half_the_pair_work():
+    # du_i/dt = 1/2 m_j Pi_ij v_ij . gradbar W = -1/2 v_ij . a_i(visc): each particle of the pair
+    # receives half of the kinetic energy the viscous pair force removes (Eq. thermalvarmass1)
+    for s in (0.5, 1.0, 3.0):
+        a, du = _visc_pair(s)
+        assert abs(du - 0.5 * s * a) <= 1e-13 * abs(du), (s, a, du)
+        assert du > 0
+
+
+def test_viscosity_off_for_receding_pairs():
+    a, du = _visc_pair(-1.0)
+    assert a == 0.0 and du == 0.0

@@ -153,12 +153,13 @@ def test_moments_by_definition_and_geometry():
 
 def test_quadrupole_far_field_error_law():
     # A far node's monopole+quadrupole field differs from the exact sum at octupole order: the
-    # error falls as d^-5 in the acceleration (d^-3 relative to the monopole term).  A sign or
+    # error falls as d^-5 in the acceleration (d^-3 relative to the monopole term) and as d^-4 in
+    # the potential.  A sign or
     # transposition mistake in the quadrupole leaves a d^-4 error instead.
     rng = np.random.default_rng(11)
     k = 64
     cl = rng.normal(0, 0.05, (k, 3)) + np.array([0.013, -0.021, 0.007])
-    errs = []
+    errs, perrs = [], []
     for dist in (1.0, 2.0, 4.0):
         probe = np.array([[dist, 0.37 * dist, -0.21 * dist]])
         P = np.concatenate([cl, probe]).astype(np.float32)
@@ -173,6 +174,11 @@ def test_quadrupole_far_field_error_law():
         a_far = np.array([far["ax"][k], far["ay"][k], far["az"][k]])
         a_ex = np.array([ex["ax"][k], ex["ay"][k], ex["az"][k]])
         errs.append(np.linalg.norm(a_far - a_ex))
+        perrs.append(abs(far["pot"][k] - ex["pot"][k]))
     # d^-5 law: x32 per doubling (allow 20 .. 50); a d^-4 law would give x16
     for e1, e2 in zip(errs, errs[1:]):
         assert 20.0 < e1 / e2 < 50.0, errs
+    # the potential's error is of octupole order too, d^-4: x16 per doubling (a wrong quadrupole
+    # potential term -(1/2) d.Q.d / d^5 would leave a d^-3 error, x8)
+    for e1, e2 in zip(perrs, perrs[1:]):
+        assert 11.0 < e1 / e2 < 24.0, perrs
