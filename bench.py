@@ -430,7 +430,7 @@ def main():
 
     # ---- roofline of the dominant kernel (the force walk) ----
     # DRAM bytes of one walk launch, scaled by particle count from an ncu capture of the same kernel
-    # on the 1/8-size mixed-species workload (plain FP32; profiles/k_walk_hernquist_1of8.md)
+    # on the 1/8-size mixed-species workload (plain FP32)
     traffic = None
     leaf_used = int(ds.params.leaf_size)
     if args.workload in ("c3", "c3s") and prec == E.EVOL_FP32_PLAIN and leaf_used in WALK_DRAM_BYTES_PER_PARTICLE:

@@ -204,6 +204,12 @@ int64_t evol_get_debug(evol_ctx *ctx, int what, void *host_dst, int64_t cap_byte
  * neighbour set, and their sizes.  Slower; off by default. */
 int evol_set_check_mode(evol_ctx *ctx, int on);
 
+/* Per-warp traversal-stack capacity of the tree walks, in entries: 32 <= entries <= the
+ * capacity evol_create allocated (4096); 0 restores that capacity.  A walk that would need more
+ * stops before writing past it and the step reports EVOL_EOVERFLOW.  Lowering it serves to test
+ * that path.  Takes effect from the next call.  Returns EVOL_EINVAL out of range. */
+int evol_set_stack_limit(evol_ctx *ctx, int64_t entries);
+
 /* Event timings (ms) of the phases of the last evol_step: [0] build, [1] eps solve,
  * [2] h solve, [3] force walk, [4] total. Valid after evol_sync. */
 int evol_get_timings(evol_ctx *ctx, float out[5]);
@@ -217,14 +223,27 @@ int evol_get_timings(evol_ctx *ctx, float out[5]);
  * owned by the caller; keys_sorted and perm are also used as working space.  cube (device,
  * 4 doubles: corner x, y, z, side) may be NULL.  stream: a cudaStream_t (NULL = legacy stream).
  * Allocates nothing: its scratch is a static device array of EVOL_NOALLOC_MAX_N * 12 bytes
- * (768 KiB) held by every GPU that loads the library until the process exits.  The array's
- * address is looked up on the first call made on each device (with that device current), so
- * make that first call before any stream capture.  All calls share the array: calls that
- * overlap on the GPU race.  Returns EVOL_EINVAL if n < 0 or n > EVOL_NOALLOC_MAX_N, or a pointer
- * is NULL; EVOL_OK for n == 0 (nothing launched); asynchronous otherwise. */
+ * (768 KiB) held by every GPU that loads the library until the process exits.
+ * Set-up: the array lives in the library's device module, which the CUDA runtime loads on a
+ * device at its first use there -- that load is what places the array in device memory.  A call
+ * with n == 0 (pointers may be NULL) does this set-up for the current device and launches
+ * nothing; evol_create also does it for its device.  Make that call at start-up, where
+ * allocating is still allowed, before any stream capture, and again after a cudaDeviceReset
+ * (which unloads the module).  Without it, the first call with n > 0 on a device does the set-up.
+ * All calls share the array: calls that overlap on the GPU race.  Returns EVOL_EINVAL if n < 0
+ * or n > EVOL_NOALLOC_MAX_N, or a pointer is NULL (n > 0); EVOL_ECUDA if the set-up fails;
+ * asynchronous otherwise. */
 #define EVOL_NOALLOC_MAX_N 65536
 int evol_sort_keys_noalloc(int64_t n, const float *x, const float *y, const float *z, uint64_t *keys_sorted,
                            int32_t *perm, double *cube, void *stream);
+
+/* Measurement helper (not part of the paper's method): the device's FP32 throughput, measured
+ * by one kernel in which every thread runs eight independent chains of `iters` x 64 fused
+ * multiply-adds (2 operations each) over 2048 resident threads per SM, on the current device.
+ * Writes TFLOP/s to *tflops and the kernel's duration to *ms (may be NULL).  Synchronous;
+ * allocates a few bytes of device memory for the duration of the call.  This is the peak the
+ * force walk's FP32 roofline fraction is quoted against. */
+int evol_fp32_peak(int iters, double *tflops, float *ms);
 
 const char *evol_strerror(int code);
 

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libevol.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["evol_api.cu", "tree.cu", "lengths.cu", "walk.cu", "post.cu", "noalloc.cu"]
+SOURCES = ["evol_api.cu", "tree.cu", "lengths.cu", "walk.cu", "post.cu", "noalloc.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]

@@ -17,6 +17,7 @@ int evol_lengths_warps_per_block();
 int evol_launch_kick(evol_ctx *c, const evol_particles *p, float half_dt, const float *ax, const float *ay,
                      const float *az, const float *dudt);
 int evol_launch_drift(evol_ctx *c, const evol_particles *p, const evol_params *prm, float dt);
+int evol_noalloc_setup_current_device();
 
 namespace {
 
@@ -39,7 +40,7 @@ void free_all(evol_ctx *c)
                     d.zeta, d.rho, d.neps, d.ups, d.X, d.acc, d.dudt, d.keys_a, d.keys_b, d.vals_a, d.vals_b,
                     d.hist, d.lcp, d.cnt, d.base, d.scan_part, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
                     d.nnch, d.narrive, d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nM64, d.nC64, d.nQ64, d.nBmin,
-                    d.nBmax, d.nI, d.nK0, d.nK1, d.wstack, d.cand_leaf, d.cand_mask, d.diag_part, d.diag, d.counters, d.err, d.nnodes,
+                    d.nBmax, d.nCoff, d.nI, d.nK0, d.nK1, d.wstack, d.cand_leaf, d.cand_mask, d.diag_part, d.diag, d.counters, d.err, d.nnodes,
                     d.cube, d.fcube, d.bbox_part, d.hash3, d.cnt3, c->stage, c->kdk_acc, d.sys_off, d.sys_root, d.sys_sorted};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -192,6 +193,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     c->cand_slots = (int64_t)c->num_sms * 6 * evol_lengths_warps_per_block();   // length-solve warps
     c->wstack_slots = (int64_t)c->num_sms * 32;      // the walk and length grids use at most 32 warps per SM
     c->wstack_cap = WSTACK_CAP;
+    c->wstack_lim = WSTACK_CAP;
     int64_t n = max_n, nn = c->node_cap;
     int64_t scan_parts = (256 * c->sort_blocks > n + 1 ? 256 * c->sort_blocks : n + 1) / 4096 + 2;
     evol_dev &d = c->d;
@@ -209,7 +211,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.nparent, nn); rc |= dalloc(&d.nnch, nn); rc |= dalloc(&d.narrive, nn);
     rc |= dalloc(&d.nA, nn); rc |= dalloc(&d.nB, nn); rc |= dalloc(&d.nC, nn); rc |= dalloc(&d.nQ0, nn);
     rc |= dalloc(&d.nQ1, nn); rc |= dalloc(&d.nM64, nn); rc |= dalloc(&d.nC64, 3 * nn); rc |= dalloc(&d.nQ64, 6 * nn);
-    rc |= dalloc(&d.nBmin, nn); rc |= dalloc(&d.nBmax, nn); rc |= dalloc(&d.nI, nn);
+    rc |= dalloc(&d.nBmin, nn); rc |= dalloc(&d.nBmax, nn); rc |= dalloc(&d.nCoff, nn); rc |= dalloc(&d.nI, nn);
     rc |= dalloc(&d.nK0, nn); rc |= dalloc(&d.nK1, nn);
     rc |= dalloc(&d.wstack, c->wstack_slots * c->wstack_cap);
     rc |= dalloc(&d.cand_leaf, 1);                                      // unused
@@ -240,6 +242,10 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
         return rc < 0 ? (rc == EVOL_ECUDA ? EVOL_ECUDA : EVOL_ENOMEM) : EVOL_ENOMEM;
     }
     c->built_n = -1;
+    // the allocation-free entry point's static scratch: placed and looked up on this device now,
+    // while allocating is allowed (a failure here is retried by that entry point's own set-up)
+    evol_noalloc_setup_current_device();
+    cudaGetLastError();
     *out = c;
     return EVOL_OK;
 }
@@ -257,6 +263,15 @@ int evol_set_check_mode(evol_ctx *c, int on)
 {
     if (!c) return EVOL_EINVAL;
     c->check_mode = on ? 1 : 0;
+    return EVOL_OK;
+}
+
+int evol_set_stack_limit(evol_ctx *c, int64_t entries)
+{
+    if (!c) return EVOL_EINVAL;
+    if (entries == 0) entries = c->wstack_cap;
+    if (entries < 32 || entries > c->wstack_cap) return EVOL_EINVAL;
+    c->wstack_lim = entries;
     return EVOL_OK;
 }
 
@@ -322,6 +337,7 @@ static int run_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol
     sig = fnv(sig, prm, sizeof *prm);
     sig = fnv(sig, out, sizeof *out);
     sig = fnv(sig, &c->check_mode, sizeof c->check_mode);
+    sig = fnv(sig, &c->wstack_lim, sizeof c->wstack_lim);
     sig = fnv(sig, &c->stream, sizeof c->stream);
     if (!c->graph_exec[0] || sig != c->graph_sig) {
         for (int k = 0; k < NPHASE; ++k)
@@ -430,6 +446,7 @@ int evol_kdk(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_output
         sig = fnv(sig, &o, sizeof o);
         sig = fnv(sig, &dt, sizeof dt);
         sig = fnv(sig, &c->check_mode, sizeof c->check_mode);
+        sig = fnv(sig, &c->wstack_lim, sizeof c->wstack_lim);
         sig = fnv(sig, &c->stream, sizeof c->stream);
         if (!c->kdk_exec || sig != c->kdk_sig) {
             if (c->kdk_exec) {

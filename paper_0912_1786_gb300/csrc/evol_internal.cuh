@@ -49,6 +49,7 @@ struct evol_dev {
     float4 *nQ1;             // Qxy, Qxz, Qyz, delta
     double *nM64, *nC64, *nQ64;         // FP64 moments (mixed precision): M, com[3], Q[6]
     float4 *nBmin, *nBmax;              // particle bounding box (w of nBmin: node holds gas)
+    float4 *nCoff;                      // FP32 moments: centre of mass - geometric centre, M
     int4 *nI;                           // walk copy: level | leaf << 8, next, begin, end
     int4 *nK0, *nK1;                    // child ids (up to 8, -1 padded) of internal nodes
     int2 *wstack;                       // per-warp traversal stacks of the force walk
@@ -82,6 +83,7 @@ struct evol_ctx {
     int64_t bbox_blocks;
     int64_t cand_slots, cand_cap;
     int64_t wstack_slots, wstack_cap;
+    int64_t wstack_lim;      // entries the walks may use per warp (<= wstack_cap)
     int64_t diag_blocks;
     int host_err;            // first error seen on the host side
     int check_mode;
@@ -195,6 +197,7 @@ struct evol_kparams {
     int gravity, sph, adaptive, use_tc, periodic_mask, mixed;
     float plen[3];
     int n, n_gas, leaf;
-    int stack_cap;
+    int stack_cap;           // traversal-stack entries a warp may use
+    int stack_stride;        // entries allocated per warp (>= stack_cap)
     int nsys;
 };

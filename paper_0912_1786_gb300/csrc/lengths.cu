@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
     const int w = threadIdx.x >> 5;
     const int wslot = blockIdx.x * LW_WARPS + w;
     // the warp's stack: node ids, two per int2 slot of the shared traversal-stack buffer
-    int *stk = reinterpret_cast<int *>(d.wstack + (size_t)wslot * kp.stack_cap);
+    int *stk = reinterpret_cast<int *>(d.wstack + (size_t)wslot * kp.stack_stride);
     const int stack_cap = 2 * kp.stack_cap;
     const int n = kp.n;
     const int ngroups = (n + SUB - 1) / SUB;       // the queue hands out SUB particles at a time
@@ -449,17 +449,39 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
             float L = __shfl_sync(0xffffffffu, L0, t);
             // every lane holds the same solver state for particle t
             float lo = 0.f, hi = INFINITY, Rc = 0.f;
+            // after a neighbour-list overflow at search radius Rlim no length with 2 L >= Rlim can
+            // be evaluated: the bracket's upper end is kept below Rlim / 2 and every later gather
+            // radius below Rlim
+            float Rlim = INFINITY;
             int status = ST_ACTIVE;
             bool stale = true;
             int cnt = 0, iters = 0, walks = 0;
+            // a particle whose length cannot be found still gets every output written: its length
+            // as reached, NaN for the quantities derived from the (missing) root
+            auto give_up = [&](int code) {
+                if (lane == 0) evol_flag(d.err, code);
+                if (lane == t) {
+                    const int si = g * SUB + t;
+                    const float qnan = __int_as_float(0x7fc00000);
+                    if (MODE == 0) {
+                        d.len_h[si] = L;
+                        d.nh[si] = qnan; d.rho[si] = qnan; d.omega[si] = qnan; d.zeta[si] = qnan;
+                    } else {
+                        d.len_eps[si] = L;
+                        d.neps[si] = qnan; d.ups[si] = qnan; d.X[si] = qnan;
+                    }
+                }
+                status = ST_DONE;
+            };
             while (status != ST_DONE) {
                 if (stale) {
                     if (walks >= MAX_WALKS) {
-                        if (lane == 0) evol_flag(d.err, EVOL_ENOCONV);
+                        give_up(EVOL_ENOCONV);
                         break;
                     }
                     ++walks;
-                    Rc = 2.f * L * SEARCH_MARGIN;
+                    // gather radius: 2 L (1 + margin), and strictly between 2 L and Rlim
+                    Rc = fminf(2.f * L * SEARCH_MARGIN, L + 0.5f * Rlim);
                     const float R2 = Rc * Rc;
                     cnt = 0;
                     __syncwarp();
@@ -477,8 +499,14 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                     stale = false;
                     if (cnt > PCAP) {
                         // more neighbours than the list holds: the radius is too large; shrink, gather again
+                        Rlim = fminf(Rlim, Rc);
+                        hi = fminf(hi, 0.5f * Rlim * (1.f - 1e-6f));
                         float Ln = 0.75f * L;
-                        if (Ln <= lo) Ln = 0.5f * (lo + L);
+                        if (Ln <= lo) Ln = 0.5f * (lo + fminf(L, hi));
+                        if (!(Ln > lo && Ln < hi)) {          // nothing left to evaluate
+                            give_up(EVOL_EOVERFLOW);
+                            break;
+                        }
                         L = Ln;
                         stale = true;
                         continue;
@@ -552,13 +580,10 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         status = ST_LAST;
                     }
                     if (2.f * L >= Rc) stale = true;
-                    if (L > 4.f * sd) {               // no root: fewer neighbours than required
-                        if (lane == 0) evol_flag(d.err, EVOL_ENOCONV);
-                        if (lane == t) {
-                            if (MODE == 0) d.len_h[g * SUB + t] = L; else d.len_eps[g * SUB + t] = L;
-                        }
-                        status = ST_DONE;
-                    }
+                    if (L > 4.f * sd)                 // no root: fewer neighbours than required
+                        give_up(EVOL_ENOCONV);
+                    else if (stale && 2.f * L >= Rlim)   // the next gather would overflow again
+                        give_up(EVOL_EOVERFLOW);
                 }
             }
             iters_total += iters;
@@ -580,7 +605,8 @@ int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params 
     kp.eta_e = 0.5f * cbrtf(3.f * prm->n_nei_grav / (4.f * EVOL_PI_F));
     kp.periodic_mask = prm->periodic_mask;
     for (int a = 0; a < 3; ++a) kp.plen[a] = prm->periodic_hi[a] - prm->periodic_lo[a];
-    kp.stack_cap = (int)c->wstack_cap;
+    kp.stack_cap = (int)c->wstack_lim;
+    kp.stack_stride = (int)c->wstack_cap;
     unsigned long long *q = c->d.counters + (mode == 0 ? 5 : 6);
     cudaMemsetAsync(q, 0, sizeof(unsigned long long), c->stream);
     int blocks = (int)(c->cand_slots / LW_WARPS);

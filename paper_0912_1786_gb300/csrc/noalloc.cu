@@ -8,11 +8,16 @@
 // start-up and may not grow.  Such callers pass their own input and output buffers and this
 // entry point allocates nothing: no cudaMalloc, no cudaFree, no library routine that allocates.
 //
-// The static array is part of the loaded module, so every GPU that loads the library holds it
-// until the process exits.  Its device address is looked up once per device (on the first call
-// made with that device current) with cudaGetSymbolAddress.  All calls share the one array,
-// which keeps whatever the previous call left in it; calls whose executions overlap on the GPU
-// therefore race and must be ordered by the caller (for example by using one stream).
+// The static array belongs to this file's device module.  The CUDA runtime loads a module on a
+// device lazily, at its first use there, and loading it is what places the array (and the
+// kernel's code) in device memory.  So the set-up -- loading the module and looking up the
+// array's device address with cudaGetSymbolAddress, with the device current -- is done by a
+// call with n == 0 (which launches nothing), by evol_create for its device, or else by the first
+// call on each device.  A caller that may not allocate later makes the n == 0 call at start-up,
+// before any stream capture; after a cudaDeviceReset it makes it again (the reset unloads the
+// module and with it the array).  All calls share the one array, which keeps whatever the
+// previous call left in it; calls whose executions overlap on the GPU therefore race and must be
+// ordered by the caller (for example by using one stream).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -176,14 +181,15 @@ __global__ void __launch_bounds__(NA_THREADS) k_sort_keys_single_block(int n, co
     }
 }
 
-// Look up the device address of the static scratch once per device (the device must be current).
-int scratch_for_current_device(void **out)
+// Device address of the static scratch on the current device, looked up once per device (or
+// again when `refresh` is set).
+int scratch_for_current_device(void **out, bool refresh)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return EVOL_ECUDA;
     if (dev < 0 || dev >= NA_MAX_DEVICES) return EVOL_EINVAL;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ready[dev]) {
+    if (!g_scratch_ready[dev] || refresh) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
@@ -198,14 +204,21 @@ int scratch_for_current_device(void **out)
 
 }  // namespace
 
+// Set-up for the current device (module load + address lookup); evol_create calls it.
+int evol_noalloc_setup_current_device()
+{
+    void *p = nullptr;
+    return scratch_for_current_device(&p, false);
+}
+
 extern "C" int evol_sort_keys_noalloc(int64_t n, const float *x, const float *y, const float *z, uint64_t *keys_sorted,
                                       int32_t *perm, double *cube, void *stream)
 {
     if (n < 0 || n > EVOL_NOALLOC_MAX_N) return EVOL_EINVAL;
-    if (n == 0) return EVOL_OK;
-    if (!x || !y || !z || !keys_sorted || !perm) return EVOL_EINVAL;
     void *scratch = nullptr;
-    int rc = scratch_for_current_device(&scratch);
+    if (n == 0) return scratch_for_current_device(&scratch, true);     // set-up call: nothing launched
+    if (!x || !y || !z || !keys_sorted || !perm) return EVOL_EINVAL;
+    int rc = scratch_for_current_device(&scratch, false);
     if (rc) return rc;
     k_sort_keys_single_block<<<1, NA_THREADS, 0, (cudaStream_t)stream>>>(
         (int)n, x, y, z, keys_sorted, perm, static_cast<unsigned char *>(scratch), cube);

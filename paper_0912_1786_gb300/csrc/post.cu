@@ -40,6 +40,8 @@ __global__ void k_pack(int n, int n_gas, int do_grav, int adaptive, int do_sph, 
     d.snd[s] = sn;
 }
 
+// Results into the caller's order.  Every value written is checked: a non-finite one is flagged
+// as EVOL_ENAN (the first error recorded wins, so a length that had no root reports ENOCONV).
 __global__ void k_unpermute(int n, int n_gas, int what, int add_acc, evol_dev d, float *h, float *eps, float *ax,
                             float *ay, float *az, float *pot, float *rho, float *P, float *c, float *omega,
                             float *zeta, float *dudt, float *ups, float *X)
@@ -48,38 +50,43 @@ __global__ void k_unpermute(int n, int n_gas, int what, int add_acc, evol_dev d,
     if (s >= n) return;
     int j = d.orig[s];
     bool gas = j < n_gas;
+    bool fin = true;
+    auto put = [&](float *dst, float v) {
+        fin = fin && isfinite(v);
+        if (dst) dst[j] = v;
+    };
     if (what & EVOL_UNPERM_LENGTHS) {
-        if (h && gas) h[j] = d.len_h[s];
+        if (gas) put(h, d.len_h[s]);
     }
     if (what & EVOL_UNPERM_EPSOUT) {
-        if (eps) eps[j] = d.len_eps[s];
-        if (ups) ups[j] = d.ups[s];
-        if (X) X[j] = d.X[s];
+        put(eps, d.len_eps[s]);
+        put(ups, d.ups[s]);
+        put(X, d.X[s]);
     }
     if ((what & EVOL_UNPERM_DENSITY) && gas) {
         float4 sn = d.snd[s];
-        if (rho) rho[j] = d.rho[s];
-        if (P) P[j] = sn.w;
-        if (c) c[j] = sn.x;
-        if (omega) omega[j] = d.omega[s];
-        if (zeta) zeta[j] = d.zeta[s];
+        put(rho, d.rho[s]);
+        put(P, sn.w);
+        put(c, sn.x);
+        put(omega, d.omega[s]);
+        put(zeta, d.zeta[s]);
     }
     if (what & EVOL_UNPERM_ACC) {
         float4 a = d.acc[s];
         if (add_acc) {
+            fin = fin && isfinite(a.x) && isfinite(a.y) && isfinite(a.z);
             if (ax) ax[j] += a.x;
             if (ay) ay[j] += a.y;
             if (az) az[j] += a.z;
         } else {
-            if (ax) ax[j] = a.x;
-            if (ay) ay[j] = a.y;
-            if (az) az[j] = a.z;
-            if (pot) pot[j] = a.w;
+            put(ax, a.x);
+            put(ay, a.y);
+            put(az, a.z);
+            put(pot, a.w);
         }
     }
-    if ((what & EVOL_UNPERM_DUDT) && gas) {
-        if (dudt) dudt[j] = d.dudt[s];
-    }
+    if ((what & EVOL_UNPERM_DUDT) && gas) put(dudt, d.dudt[s]);
+    if (!fin) evol_flag(d.err, EVOL_ENAN);
 }
 
 constexpr int DG_THREADS = 256;

@@ -29,12 +29,15 @@ constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
 // ---------------------------------------------------------------------------------------
 // Root cube
 // ---------------------------------------------------------------------------------------
+// A non-finite position is flagged as EVOL_ENAN (the min/max below ignore NaN, and every later
+// phase keeps its loops bounded on such input, so the step completes and reports the error).
 __global__ void k_bbox_partial(int n, const float *__restrict__ x, const float *__restrict__ y,
-                               const float *__restrict__ z, float *__restrict__ part)
+                               const float *__restrict__ z, float *__restrict__ part, int *err)
 {
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float v[3] = {x[i], y[i], z[i]};
+        if (!(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]))) evol_flag(err, EVOL_ENAN);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             lo[a] = fminf(lo[a], v[a]);
@@ -442,24 +445,29 @@ __global__ void k_link(const int32_t *__restrict__ nnodes, int leaf, const int32
 // ---------------------------------------------------------------------------------------
 // Moments, leaf-up.  A leaf sums its particles; the last child to finish a parent (atomic
 // arrival count) combines the children with the parallel-axis shift of the quadrupole.
+//
+// FP32 (plain) moments take every position relative to the node's geometric centre (exact in
+// double: a dyadic point of the root cube), so the centre of mass and the quadrupole carry
+// rounding on the scale of the node, not of the coordinates; a parent combines its children's
+// centre-of-mass offsets shifted by the (power-of-two) difference of the two centres, which is
+// exact in float.  The absolute centre of mass is formed once, in double, when the node is
+// written.  FP64 (mixed) moments use absolute coordinates.
 // ---------------------------------------------------------------------------------------
 template <typename T>
 struct Mom {
-    T M, c[3], q[6];       // mass, centre of mass, traceless quadrupole about it (xx yy zz xy xz yz)
+    T M, c[3], q[6];       // mass, centre of mass (FP32: offset from the node centre), traceless
+                           // quadrupole about it (xx yy zz xy xz yz)
 };
 
 struct NodeOut {
-    float4 *nA, *nB, *nC, *nQ0, *nQ1, *bmin, *bmax;
+    float4 *nA, *nB, *nC, *nQ0, *nQ1, *bmin, *bmax, *coff;
     double *M64, *C64, *Q64;
 };
 
-template <typename T>
-__device__ void write_node(const NodeOut &o, int id, const Mom<T> &mm, float3 lo, float3 hi, int hasgas, int lev,
-                           const double *__restrict__ cube, uint64_t key0, float theta, bool mixed)
+// geometric centre of the node whose first key is key0 at level lev (exact in double)
+__device__ __forceinline__ void node_centre(const double *__restrict__ cube, uint64_t key0, int lev, double cg[3])
 {
-    // geometric centre of the node's cube
     double side = ldexp(cube[3], -lev);
-    double cg[3];
     uint64_t qa[3] = {0, 0, 0};
     for (int l = 1; l <= lev; ++l) {
         unsigned dg = (unsigned)(key0 >> (3 * (EVOL_MAXLEVEL - l))) & 7u;
@@ -467,16 +475,24 @@ __device__ void write_node(const NodeOut &o, int id, const Mom<T> &mm, float3 lo
         qa[1] = (qa[1] << 1) | ((dg >> 1) & 1u);
         qa[2] = (qa[2] << 1) | (dg & 1u);
     }
-    double dd = 0.0;
+    for (int a = 0; a < 3; ++a) cg[a] = cube[a] + ((double)qa[a] + 0.5) * side;
+}
+
+template <typename T>
+__device__ void write_node(const NodeOut &o, int id, const Mom<T> &mm, float3 lo, float3 hi, int hasgas, int lev,
+                           const double cg[3], double side, float theta, bool mixed)
+{
+    constexpr bool rel = sizeof(T) == sizeof(float);
+    double com[3], dd = 0.0;
     for (int a = 0; a < 3; ++a) {
-        cg[a] = cube[a] + ((double)qa[a] + 0.5) * side;
-        double t = (double)mm.c[a] - cg[a];
-        dd += t * t;
+        const double off = rel ? (double)mm.c[a] : (double)mm.c[a] - cg[a];
+        com[a] = rel ? cg[a] + off : (double)mm.c[a];
+        dd += off * off;
     }
     float delta = (float)sqrt(dd);
     float l = (float)side;
     float ropen = theta > 0.f ? l / theta + delta : INFINITY;
-    o.nA[id] = make_float4((float)mm.c[0], (float)mm.c[1], (float)mm.c[2], ropen * ropen);
+    o.nA[id] = make_float4((float)com[0], (float)com[1], (float)com[2], ropen * ropen);
     float4 bb = make_float4(0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z), hasgas ? 0.f : -1.f);
     o.nB[id] = bb;
     o.nC[id] = make_float4(0.5f * (hi.x - lo.x), 0.5f * (hi.y - lo.y), 0.5f * (hi.z - lo.z), 0.f);
@@ -484,6 +500,7 @@ __device__ void write_node(const NodeOut &o, int id, const Mom<T> &mm, float3 lo
     o.nQ1[id] = make_float4((float)mm.q[3], (float)mm.q[4], (float)mm.q[5], delta);
     o.bmin[id] = make_float4(lo.x, lo.y, lo.z, (float)hasgas);
     o.bmax[id] = make_float4(hi.x, hi.y, hi.z, 0.f);
+    if (rel) o.coff[id] = make_float4((float)mm.c[0], (float)mm.c[1], (float)mm.c[2], (float)mm.M);
     if (mixed) {
         o.M64[id] = (double)mm.M;
         for (int a = 0; a < 3; ++a) o.C64[3 * id + a] = (double)mm.c[a];
@@ -493,18 +510,20 @@ __device__ void write_node(const NodeOut &o, int id, const Mom<T> &mm, float3 lo
 
 template <typename T>
 __device__ void leaf_moments(int b, int e, int n_gas, const float4 *__restrict__ pos, const int32_t *__restrict__ orig,
-                             Mom<T> &mm, float3 &lo, float3 &hi, int &hasgas)
+                             const double cg[3], Mom<T> &mm, float3 &lo, float3 &hi, int &hasgas)
 {
+    constexpr bool rel = sizeof(T) == sizeof(float);
     T M = 0, s0 = 0, s1 = 0, s2 = 0;
     lo = make_float3(INFINITY, INFINITY, INFINITY);
     hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
     hasgas = 0;
+    auto coord = [&](float x, int a) -> T { return rel ? (T)((double)x - cg[a]) : (T)x; };
     for (int s = b; s < e; ++s) {
         float4 p = pos[s];
         M += (T)p.w;
-        s0 += (T)p.w * (T)p.x;
-        s1 += (T)p.w * (T)p.y;
-        s2 += (T)p.w * (T)p.z;
+        s0 += (T)p.w * coord(p.x, 0);
+        s1 += (T)p.w * coord(p.y, 1);
+        s2 += (T)p.w * coord(p.z, 2);
         lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
         hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
         if (orig[s] < n_gas) hasgas = 1;
@@ -513,12 +532,14 @@ __device__ void leaf_moments(int b, int e, int n_gas, const float4 *__restrict__
     if (M > 0) {
         mm.c[0] = s0 / M; mm.c[1] = s1 / M; mm.c[2] = s2 / M;
     } else {
-        mm.c[0] = (T)(0.5f * (lo.x + hi.x)); mm.c[1] = (T)(0.5f * (lo.y + hi.y)); mm.c[2] = (T)(0.5f * (lo.z + hi.z));
+        mm.c[0] = coord(0.5f * (lo.x + hi.x), 0);
+        mm.c[1] = coord(0.5f * (lo.y + hi.y), 1);
+        mm.c[2] = coord(0.5f * (lo.z + hi.z), 2);
     }
     for (int a = 0; a < 6; ++a) mm.q[a] = 0;
     for (int s = b; s < e; ++s) {
         float4 p = pos[s];
-        T d0 = (T)p.x - mm.c[0], d1 = (T)p.y - mm.c[1], d2 = (T)p.z - mm.c[2];
+        T d0 = coord(p.x, 0) - mm.c[0], d1 = coord(p.y, 1) - mm.c[1], d2 = coord(p.z, 2) - mm.c[2];
         T r2 = d0 * d0 + d1 * d1 + d2 * d2, w = (T)p.w;
         mm.q[0] += w * (3 * d0 * d0 - r2);
         mm.q[1] += w * (3 * d1 * d1 - r2);
@@ -529,30 +550,52 @@ __device__ void leaf_moments(int b, int e, int n_gas, const float4 *__restrict__
     }
 }
 
+// child c's moments; FP32: its centre-of-mass offset re-expressed about the parent's centre
+// (cg_c - cg_p is a power of two per axis: exact in float)
 template <typename T>
-__device__ void load_child(const NodeOut &o, int c, Mom<T> &mm, float3 &lo, float3 &hi, int &hasgas, bool mixed)
+__device__ void load_child(const NodeOut &o, int c, const double cgp[3], const double *__restrict__ cube,
+                           const uint64_t *__restrict__ keys, const int32_t *__restrict__ nbeg,
+                           const int32_t *__restrict__ nlev, Mom<T> &mm, float3 &lo, float3 &hi, int &hasgas,
+                           bool mixed)
 {
+    constexpr bool rel = sizeof(T) == sizeof(float);
     float4 bl = __ldcg(&o.bmin[c]), bh = __ldcg(&o.bmax[c]);
     lo = make_float3(bl.x, bl.y, bl.z);
     hi = make_float3(bh.x, bh.y, bh.z);
     hasgas = bl.w != 0.f;
+    float4 Q0, Q1;
     if (mixed) {
         mm.M = (T)__ldcg(&o.M64[c]);
         for (int a = 0; a < 3; ++a) mm.c[a] = (T)__ldcg(&o.C64[3 * c + a]);
         for (int a = 0; a < 6; ++a) mm.q[a] = (T)__ldcg(&o.Q64[6 * c + a]);
+        return;
+    }
+    Q0 = __ldcg(&o.nQ0[c]);
+    Q1 = __ldcg(&o.nQ1[c]);
+    mm.q[0] = (T)Q0.x; mm.q[1] = (T)Q0.y; mm.q[2] = (T)Q0.z;
+    mm.q[3] = (T)Q1.x; mm.q[4] = (T)Q1.y; mm.q[5] = (T)Q1.z;
+    if (rel) {
+        const float4 co = __ldcg(&o.coff[c]);
+        double cgc[3];
+        node_centre(cube, __ldcg(&keys[__ldcg(&nbeg[c])]), __ldcg(&nlev[c]), cgc);
+        mm.M = (T)co.w;
+        mm.c[0] = (T)co.x + (T)(cgc[0] - cgp[0]);
+        mm.c[1] = (T)co.y + (T)(cgc[1] - cgp[1]);
+        mm.c[2] = (T)co.z + (T)(cgc[2] - cgp[2]);
     } else {
-        float4 A = __ldcg(&o.nA[c]), Q0 = __ldcg(&o.nQ0[c]), Q1 = __ldcg(&o.nQ1[c]);
+        const float4 A = __ldcg(&o.nA[c]);
         mm.M = (T)Q0.w;
         mm.c[0] = (T)A.x; mm.c[1] = (T)A.y; mm.c[2] = (T)A.z;
-        mm.q[0] = (T)Q0.x; mm.q[1] = (T)Q0.y; mm.q[2] = (T)Q0.z;
-        mm.q[3] = (T)Q1.x; mm.q[4] = (T)Q1.y; mm.q[5] = (T)Q1.z;
     }
 }
 
 template <typename T>
-__device__ void combine(const NodeOut &o, int id, int nch, const int32_t *__restrict__ nnext, Mom<T> &mm,
-                        float3 &lo, float3 &hi, int &hasgas, bool mixed)
+__device__ void combine(const NodeOut &o, int id, int nch, const int32_t *__restrict__ nnext, const double cgp[3],
+                        const double *__restrict__ cube, const uint64_t *__restrict__ keys,
+                        const int32_t *__restrict__ nbeg, const int32_t *__restrict__ nlev, Mom<T> &mm, float3 &lo,
+                        float3 &hi, int &hasgas, bool mixed)
 {
+    constexpr bool rel = sizeof(T) == sizeof(float);
     Mom<T> ch[8];
     lo = make_float3(INFINITY, INFINITY, INFINITY);
     hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
@@ -562,7 +605,7 @@ __device__ void combine(const NodeOut &o, int id, int nch, const int32_t *__rest
     for (int k = 0; k < nch; ++k) {
         float3 cl, chh;
         int cg;
-        load_child(o, c, ch[k], cl, chh, cg, mixed);
+        load_child(o, c, cgp, cube, keys, nbeg, nlev, ch[k], cl, chh, cg, mixed);
         lo.x = fminf(lo.x, cl.x); lo.y = fminf(lo.y, cl.y); lo.z = fminf(lo.z, cl.z);
         hi.x = fmaxf(hi.x, chh.x); hi.y = fmaxf(hi.y, chh.y); hi.z = fmaxf(hi.z, chh.z);
         hasgas |= cg;
@@ -572,7 +615,7 @@ __device__ void combine(const NodeOut &o, int id, int nch, const int32_t *__rest
     }
     mm.M = M;
     float cen[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
-    for (int a = 0; a < 3; ++a) mm.c[a] = M > 0 ? s[a] / M : (T)cen[a];
+    for (int a = 0; a < 3; ++a) mm.c[a] = M > 0 ? s[a] / M : (rel ? (T)((double)cen[a] - cgp[a]) : (T)cen[a]);
     for (int a = 0; a < 6; ++a) mm.q[a] = 0;
     for (int j = 0; j < nch; ++j) {
         T d0 = ch[j].c[0] - mm.c[0], d1 = ch[j].c[1] - mm.c[1], d2 = ch[j].c[2] - mm.c[2];
@@ -601,9 +644,11 @@ __global__ void k_moments(const int32_t *__restrict__ nnodes, int n_gas, const i
         Mom<T> mm;
         float3 lo, hi;
         int hg;
-        leaf_moments<T>(nbeg[id], nend[id], n_gas, pos, orig, mm, lo, hi, hg);
-        write_node<T>(o, id, mm, lo, hi, hg, nlev[id], cube + 4 * sys_sorted[nbeg[id]], keys[nbeg[id]], theta,
-                      mixed != 0);
+        const double *cb = cube + 4 * sys_sorted[nbeg[id]];
+        double cg[3];
+        node_centre(cb, keys[nbeg[id]], nlev[id], cg);
+        leaf_moments<T>(nbeg[id], nend[id], n_gas, pos, orig, cg, mm, lo, hi, hg);
+        write_node<T>(o, id, mm, lo, hi, hg, nlev[id], cg, ldexp(cb[3], -nlev[id]), theta, mixed != 0);
         __threadfence();
         int p = nparent[id];
         for (int climb = 0; p >= 0 && p < nn; ++climb) {
@@ -614,9 +659,11 @@ __global__ void k_moments(const int32_t *__restrict__ nnodes, int n_gas, const i
             int old = atomicAdd(&narrive[p], 1);
             if (old != nnch[p] - 1) break;
             __threadfence();
-            combine<T>(o, p, nnch[p], nnext, mm, lo, hi, hg, mixed != 0);
-            write_node<T>(o, p, mm, lo, hi, hg, nlev[p], cube + 4 * sys_sorted[nbeg[p]], keys[nbeg[p]], theta,
-                          mixed != 0);
+            const double *cbp = cube + 4 * sys_sorted[nbeg[p]];
+            double cgp[3];
+            node_centre(cbp, keys[nbeg[p]], nlev[p], cgp);
+            combine<T>(o, p, nnch[p], nnext, cgp, cbp, keys, nbeg, nlev, mm, lo, hi, hg, mixed != 0);
+            write_node<T>(o, p, mm, lo, hi, hg, nlev[p], cgp, ldexp(cbp[3], -nlev[p]), theta, mixed != 0);
             __threadfence();
             p = nparent[p];
         }
@@ -684,13 +731,15 @@ __global__ void k_set_single(int n, int32_t *sys_off)
 
 // one block per system: its cube from its own particles
 __global__ void k_bbox_sys(const int32_t *__restrict__ sys_off, const float *__restrict__ x,
-                           const float *__restrict__ y, const float *__restrict__ z, double *cube, float *fcube)
+                           const float *__restrict__ y, const float *__restrict__ z, double *cube, float *fcube,
+                           int *err)
 {
     const int k = blockIdx.x;
     const int b = sys_off[k], e = sys_off[k + 1];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
         float v[3] = {x[i], y[i], z[i]};
+        if (!(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]))) evol_flag(err, EVOL_ENAN);
         for (int a = 0; a < 3; ++a) {
             lo[a] = fminf(lo[a], v[a]);
             hi[a] = fmaxf(hi[a], v[a]);
@@ -825,12 +874,12 @@ int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *p
     if (nsys == 1) {
         int nb = (int)c->bbox_blocks;
         k_set_single<<<1, 32, 0, st>>>(n, d.sys_off);
-        k_bbox_partial<<<nb, BB_THREADS, 0, st>>>(n, p->x, p->y, p->z, d.bbox_part);
+        k_bbox_partial<<<nb, BB_THREADS, 0, st>>>(n, p->x, p->y, p->z, d.bbox_part, d.err);
         k_bbox_final<<<1, 32, 0, st>>>(nb, d.bbox_part, d.cube, d.fcube);
         k_keys<<<gb, tb, 0, st>>>(n, p->x, p->y, p->z, d.cube, d.keys_a, d.vals_a);
     } else {
         // the offsets were copied into d.sys_off by the caller of this launcher
-        k_bbox_sys<<<nsys, BB_THREADS, 0, st>>>(d.sys_off, p->x, p->y, p->z, d.cube, d.fcube);
+        k_bbox_sys<<<nsys, BB_THREADS, 0, st>>>(d.sys_off, p->x, p->y, p->z, d.cube, d.fcube, d.err);
         k_keys_sys<<<gb, tb, 0, st>>>(n, p->x, p->y, p->z, d.sys_off, nsys, d.cube, d.keys_a, d.vals_a);
     }
     int rsb = (n + RS_TILE - 1) / RS_TILE;
@@ -873,7 +922,7 @@ int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *p
     int ng = c->num_sms * 8;
     k_link<<<ng, 256, 0, st>>>(d.nnodes, leaf, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent, d.nnch, d.narrive, d.nI,
                                d.nK0, d.nK1);
-    NodeOut o{d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nBmin, d.nBmax, d.nM64, d.nC64, d.nQ64};
+    NodeOut o{d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nBmin, d.nBmax, d.nCoff, d.nM64, d.nC64, d.nQ64};
     float theta = prm->theta;
     if (prm->precision == EVOL_FP32_MIXED)
         k_moments<double><<<ng, 128, 0, st>>>(d.nnodes, (int)p->n_gas, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,

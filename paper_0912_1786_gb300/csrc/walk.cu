@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
         const bool all_gas = SPH && __all_sync(0xffffffffu, !active || gas_i);
         if (!GRAV) emin = 0.f;
 
-        int2 *stk = d.wstack + (size_t)(blockIdx.x * WK_WARPS + w) * kp.stack_cap;
+        int2 *stk = d.wstack + (size_t)(blockIdx.x * WK_WARPS + w) * kp.stack_stride;
         // one stack entry per system present in the group: its root with the mask of its lanes
         int top = 0;
         {
@@ -627,7 +627,8 @@ int evol_launch_walk(evol_ctx *c, const evol_particles *p, const evol_params *pr
     kp.use_tc = prm->use_tc_gradient;
     kp.periodic_mask = prm->periodic_mask;
     for (int a = 0; a < 3; ++a) kp.plen[a] = prm->periodic_hi[a] - prm->periodic_lo[a];
-    kp.stack_cap = (int)c->wstack_cap;
+    kp.stack_cap = (int)c->wstack_lim;
+    kp.stack_stride = (int)c->wstack_cap;
     bool mixed = prm->precision == EVOL_FP32_MIXED;
     bool check = c->check_mode != 0;
     if (do_grav && do_sph) launch_walk_pc<true, true>(c, kp, mixed, check);

@@ -74,7 +74,9 @@ def lib():
         L.evol_get_debug.argtypes = [vp, C.c_int, vp, C.c_int64]
         L.evol_get_debug.restype = C.c_int64
         L.evol_set_check_mode.argtypes = [vp, C.c_int]
+        L.evol_set_stack_limit.argtypes = [vp, C.c_int64]
         L.evol_sort_keys_noalloc.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, vp]
+        L.evol_fp32_peak.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_float)]
         L.evol_strerror.argtypes = [C.c_int]
         L.evol_strerror.restype = C.c_char_p
         _lib = L
@@ -224,6 +226,17 @@ def evol_get_timings(ctx):
 
 def evol_set_check_mode(ctx, on: bool):
     _check(lib().evol_set_check_mode(ctx, int(bool(on))), "evol_set_check_mode")
+
+
+def evol_fp32_peak(iters: int = 20000):
+    """Measured FP32 throughput of the current device: (TFLOP/s, kernel ms)."""
+    t, ms = C.c_double(), C.c_float()
+    _check(lib().evol_fp32_peak(int(iters), C.byref(t), C.byref(ms)), "evol_fp32_peak")
+    return t.value, ms.value
+
+
+def evol_set_stack_limit(ctx, entries: int):
+    _check(lib().evol_set_stack_limit(ctx, int(entries)), "evol_set_stack_limit")
 
 
 EVOL_NOALLOC_MAX_N = 65536

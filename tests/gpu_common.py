@@ -1,13 +1,41 @@
 """Helpers shared by the GPU parity tests: run a workload through the C ABI and compare with the
 FP64 oracle.  The tolerance is the one the force step is specified to: median relative error
-<= 1e-5 and 99th percentile <= 1e-4 for accelerations, densities and du/dt."""
+<= 1e-5 and 99th percentile <= 1e-4 for accelerations, densities and du/dt, the relative error
+being |got - ref| / |ref|.
+
+Every comparison is also appended as one JSON line to the file named by the environment
+variable EVOL_PARITY_REPORT (when set), so that a GPU run leaves a record of the errors."""
 from __future__ import annotations
+
+import json
+import os
 
 import numpy as np
 
 MEDIAN_TOL = 1e-5
 P99_TOL = 1e-4
-EXPLAIN_MARGIN = 1e-5      # a set mismatch is explained if the oracle saw a decision this close
+# A set mismatch is explained if the oracle saw a decision closer to its threshold than this,
+# relative to (threshold + the particle's coordinate scale).  The GPU takes each opening and
+# near decision in FP32 on float positions, centres of mass taken relative to node centres,
+# float box bounds and float lengths: its error is a few FP32 ulps (u = 6e-8) of the coordinate
+# scale plus the lengths' own error relative to the threshold (h and eps agree with the oracle
+# to about 1e-7), which stays below 16 u = 1e-6.
+EXPLAIN_MARGIN = 1e-6
+# Below this fraction of the sum of its terms' magnitudes a sum is dominated by cancellation;
+# such particles are judged by |d| / sum |terms| (and counted) instead of |d| / |ref|.
+CANCEL_FLOOR = 1e-2
+
+
+def report(record: dict):
+    """Print one comparison record and append it to $EVOL_PARITY_REPORT."""
+    import inspect
+    caller = next((f.function for f in inspect.stack() if f.function.startswith("test_")), None)
+    record = {"test": caller, **record}
+    print(json.dumps(record))
+    path = os.environ.get("EVOL_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(record) + "\n")
 
 
 def run_gpu(w, params=None, check=True, precision=0, api="step", max_n=None):
@@ -63,25 +91,39 @@ def rel_stats(got, ref, sel=None):
 
 
 def assert_tol(name, got, ref, sel=None, med=MEDIAN_TOL, p99=P99_TOL, scale=None):
-    """Relative error |got - ref| / |ref|; with `scale` (the oracle's sum of the magnitudes of the
-    individual contributions) the error of a sum with cancellation is taken relative to
-    max(|ref|, scale * 1e-2): a result that is less than 1% of its own terms is judged on
-    the terms' scale."""
-    if scale is None:
-        m, p, _ = rel_stats(got, ref, sel)
+    """Plain relative error |got - ref| / |ref| must meet the median and p99 tolerances.
+
+    With `scale` (the oracle's sum of the magnitudes of the individual contributions to each
+    result), particles whose |ref| is below CANCEL_FLOOR of their scale -- sums dominated by
+    cancellation, e.g. the acceleration at the centre of a sphere -- are taken out of the plain
+    statistics and judged by |got - ref| / scale against the same tolerances; their number and
+    that error are reported.  The plain relative error over all particles is reported too."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    sc = None if scale is None else np.asarray(scale, np.float64)
+    if sel is not None:
+        got, ref = got[sel], ref[sel]
+        sc = None if sc is None else sc[sel]
+    if got.ndim == 2:
+        d, r = np.linalg.norm(got - ref, axis=1), np.linalg.norm(ref, axis=1)
     else:
-        got = np.asarray(got, np.float64)
-        ref = np.asarray(ref, np.float64)
-        sc = np.asarray(scale, np.float64)
-        if sel is not None:
-            got, ref, sc = got[sel], ref[sel], sc[sel]
-        if got.ndim == 2:
-            d, r = np.linalg.norm(got - ref, axis=1), np.linalg.norm(ref, axis=1)
-        else:
-            d, r = np.abs(got - ref), np.abs(ref)
-        err = d / np.maximum(np.maximum(r, 1e-2 * sc), 1e-300)
-        m, p = float(np.median(err)), float(np.percentile(err, 99))
-    assert m <= med and p <= p99, f"{name}: median {m:.3g} (tol {med}), p99 {p:.3g} (tol {p99})"
+        d, r = np.abs(got - ref), np.abs(ref)
+    plain = d / np.maximum(r, 1e-300)
+    floor = np.zeros(len(d), bool) if sc is None else r < CANCEL_FLOOR * sc
+    judged = plain[~floor]
+    m, p = (float(np.median(judged)), float(np.percentile(judged, 99))) if judged.size else (0.0, 0.0)
+    rec = {"quantity": name, "n": int(len(d)), "median": m, "p99": p,
+           "all_median": float(np.median(plain)) if len(d) else 0.0,
+           "all_p99": float(np.percentile(plain, 99)) if len(d) else 0.0,
+           "max": float(judged.max()) if judged.size else 0.0, "n_floor": int(floor.sum())}
+    ok = m <= med and p <= p99
+    if floor.any():
+        fe = d[floor] / sc[floor]
+        fm, fp = float(np.median(fe)), float(np.percentile(fe, 99))
+        rec.update(floor_median=fm, floor_p99=fp)
+        ok = ok and fm <= med and fp <= p99
+    report(rec)
+    assert ok, f"{name}: {rec}"
     return m, p
 
 
@@ -91,11 +133,15 @@ def acc(res):
 
 def set_mismatches(gpu_hash, ora, margin_key="margin", active=None):
     """Particles whose interaction-set hashes differ, and how many of them the oracle's own
-    decision margins explain (a decision within EXPLAIN_MARGIN of its threshold)."""
+    decision margins explain (a decision within EXPLAIN_MARGIN of its threshold).  The counts
+    are reported."""
     oh = np.stack([ora["hfar"], ora["hnear"], ora["hsph"]], 1)
     bad = np.any(gpu_hash != oh, axis=1)
     if active is not None:
         bad &= active
     idx = np.flatnonzero(bad)
-    explained = ora[margin_key][idx] < EXPLAIN_MARGIN
+    mg = ora[margin_key][idx]
+    explained = mg < EXPLAIN_MARGIN
+    report({"quantity": "interaction_sets", "n": int(len(gpu_hash)), "mismatches": int(len(idx)),
+            "explained": int(explained.sum()), "largest_margin": float(mg.max()) if len(idx) else None})
     return idx, int(explained.sum())

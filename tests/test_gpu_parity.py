@@ -2,16 +2,17 @@
 
 Integer structure (cube, keys, permutation, nodes) must be bit-exact.  Opening / neighbour
 decisions are compared as per-particle set hashes: every mismatch must be explained by an
-oracle decision within 1e-5 of its threshold.  Floating results must meet median <= 1e-5 and
-p99 <= 1e-4 relative error against the oracle; accelerations and du/dt, which are sums with
-cancellation, are judged relative to max(|ref|, 1% of the sum of their terms' magnitudes)."""
+oracle decision within 1e-6 of its threshold (relative to threshold + coordinate scale).
+Floating results must meet median <= 1e-5 and p99 <= 1e-4 plain relative error |d|/|ref|
+against the oracle; particles whose acceleration or du/dt is below 1% of the sum of its terms'
+magnitudes (cancellation) are counted and judged by |d| / sum |terms| instead."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_0912_1786_gb300 import workloads as W
 
-from gpu_common import acc, assert_tol, rel_stats, run_gpu, set_mismatches
+from gpu_common import acc, assert_tol, rel_stats, report, run_gpu, set_mismatches
 
 pytestmark = pytest.mark.gpu
 
@@ -33,6 +34,16 @@ def _structure(g, o):
     assert np.allclose(gm[:, 14:17], mo["bmax"], rtol=0, atol=0)
     scale = np.abs(mo["com"]).max()
     assert np.abs(gm[:, 1:4] - mo["com"]).max() <= 2e-6 * scale
+    # quadrupole (traceless, about the centre of mass) on its natural scale M l^2, and delta on l
+    l = mo["l"]
+    qerr = np.abs(gm[:, 4:10] - mo["Q"]).max(1) / (mo["M"] * l * l)
+    derr = np.abs(gm[:, 10] - mo["delta"]) / l
+    report({"quantity": "node_Q", "n": int(len(l)), "median": float(np.median(qerr)),
+            "p99": float(np.percentile(qerr, 99)), "max": float(qerr.max())})
+    report({"quantity": "node_delta", "n": int(len(l)), "median": float(np.median(derr)),
+            "p99": float(np.percentile(derr, 99)), "max": float(derr.max())})
+    assert np.median(qerr) <= 1e-5 and np.percentile(qerr, 99) <= 1e-4
+    assert np.median(derr) <= 1e-5 and np.percentile(derr, 99) <= 1e-4
 
 
 def _sets(g, o, n_active=None):
@@ -52,8 +63,14 @@ def _compare(w, params=None, precision=0, api="step", med=1e-5, p99=1e-4):
         assert_tol("h", g["h"], o["h"][:ng], med=med, p99=p99)
         assert_tol("rho", g["rho"], o["rho"][:ng], med=med, p99=p99)
         assert_tol("omega", g["omega"], o["omega"][:ng], med=med, p99=p99)
+        assert_tol("P", g["P"], o["P"][:ng], med=med, p99=p99)
+        assert_tol("c", g["c"], o["c"][:ng], med=med, p99=p99)
+        # zeta = m (1 - Omega*) for equal masses: it can vanish, so it is judged on the mass scale
+        assert_tol("zeta", g["zeta"], o["zeta"][:ng], med=med, p99=p99, scale=w.m[:ng].astype(np.float64))
     if p.gravity and p.adaptive_softening:
         assert_tol("eps", g["eps"], o["eps"], med=med, p99=p99)
+        assert_tol("ups", g["ups"], o["ups"], med=med, p99=p99)
+        assert_tol("X", g["X"], o["X"], med=med, p99=p99)
     a_ref = np.stack([o["ax"], o["ay"], o["az"]], 1)
     if p.gravity or p.sph:
         sel = None if p.gravity else np.arange(ng)
@@ -64,7 +81,37 @@ def _compare(w, params=None, precision=0, api="step", med=1e-5, p99=1e-4):
         assert_tol("dudt", g["dudt"], o["dudt"][:ng], med=med, p99=p99, scale=o["duabs"][:ng])
     if api == "step":
         _sets(g, o)
+        _diagnostics(w, p, g, o)
     return g, o
+
+
+def _diagnostics(w, p, g, o):
+    """The FP64 totals of the step against the same sums of the oracle's results."""
+    d = g["diag"]
+    m = w.m.astype(np.float64)
+    v = np.stack([w.vx, w.vy, w.vz], 1).astype(np.float64)
+    a = np.stack([o["ax"], o["ay"], o["az"]], 1)
+    ng = w.n_gas
+    ref = {"sum_mv": (m[:, None] * v).sum(0), "E_kin": 0.5 * float((m * (v * v).sum(1)).sum()),
+           "E_th": float((m[:ng] * w.u[:ng].astype(np.float64)).sum()) if ng else 0.0,
+           "M": float(m.sum())}
+    got = {"sum_mv": np.array(d[0:3]), "E_kin": d[6], "E_th": d[7], "M": d[10]}
+    for k in ref:
+        sc = np.abs(ref[k]).max() if np.ndim(ref[k]) else abs(ref[k])
+        err = float(np.abs(np.asarray(got[k]) - ref[k]).max() / max(sc, 1e-300))
+        report({"quantity": "diag_" + k, "err": err})
+        assert err <= 1e-12 or sc == 0.0, (k, got[k], ref[k])
+    # sum m a: a cancellation sum, judged against sum m |a|
+    sma = (m[:, None] * a).sum(0)
+    scale = float((m * np.linalg.norm(a, axis=1)).sum())
+    err = float(np.abs(np.array(d[3:6]) - sma).max() / scale)
+    report({"quantity": "diag_sum_ma", "err": err})
+    assert err <= 1e-5
+    if p.gravity:
+        epot = 0.5 * float((m * o["pot"]).sum())
+        err = abs(d[8] - epot) / abs(epot)
+        report({"quantity": "diag_E_pot", "err": err})
+        assert err <= 1e-5
 
 
 def test_c1_evrard_leaf1():
@@ -216,3 +263,46 @@ def test_host_buffer_step_matches_device_step():
     for k in ("ax", "ay", "az", "pot"):
         assert np.array_equal(outs[k], g[k].astype(np.float32)), k
     assert np.array_equal(outs["dudt"][: w.n_gas], g["dudt"].astype(np.float32))
+
+
+def test_nan_position_reports_enan():
+    # a non-finite input position: the step completes (every loop stays bounded) and reports it
+    from paper_0912_1786_gb300 import evol as E
+    w = W.evrard_sphere(2048, seed=15, sigma_v=0.1)
+    w.x[77] = np.float32(np.nan)
+    g = run_gpu(w, check=False)
+    assert g["status"] == E.EVOL_ENAN
+
+
+def test_nonfinite_output_reports_enan():
+    # zero internal energy everywhere but one particle at +inf: P and c are infinite there
+    from paper_0912_1786_gb300 import evol as E
+    w = W.evrard_sphere(2048, seed=16)
+    w.u[5] = np.float32(np.inf)
+    g = run_gpu(w, check=False)
+    assert g["status"] == E.EVOL_ENAN
+
+
+def test_walk_stack_overflow_reports_eoverflow():
+    # the walks check the stack bound before every push: a 32-entry stack overflows on a
+    # 4096-particle sphere and the step reports EVOL_EOVERFLOW instead of writing past it
+    import torch
+    from paper_0912_1786_gb300 import build, evol as E
+    from paper_0912_1786_gb300.device import DeviceSet
+    build.build()
+    w = W.evrard_sphere(4096, seed=17)
+    ds = DeviceSet(w)
+    ctx = E.evol_create(w.n, torch.cuda.current_stream().cuda_stream)
+    try:
+        with pytest.raises(E.EvolError):
+            E.evol_set_stack_limit(ctx, 31)
+        E.evol_set_stack_limit(ctx, 32)
+        E.evol_step(ctx, ds.particles, ds.params, ds.outputs)
+        assert E.evol_sync(ctx, raise_on_error=False) == E.EVOL_EOVERFLOW
+        # restored capacity: the same context runs the step cleanly again
+        E.evol_set_stack_limit(ctx, 0)
+        ds.reset_lengths()
+        E.evol_step(ctx, ds.particles, ds.params, ds.outputs)
+        assert E.evol_sync(ctx, raise_on_error=False) == 0
+    finally:
+        E.evol_destroy(ctx)

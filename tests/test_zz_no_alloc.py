@@ -38,6 +38,8 @@ def test_noalloc_sort_matches_tree_build_on_two_calls_in_a_row():
     from paper_0912_1786_gb300 import build, evol as E
     build.build()
     stream = torch.cuda.current_stream().cuda_stream
+    # the set-up call a caller that may not allocate later makes at start-up: n = 0, no pointers
+    E.evol_sort_keys_noalloc(0, None, None, None, None, None, None, stream)
     ctx = E.evol_create(E.EVOL_NOALLOC_MAX_N, stream)
     try:
         # two different particle sets back to back: the second call must not see the first's leftovers
