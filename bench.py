@@ -32,17 +32,35 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 # Algorithmic FP32 operations per interaction of the force walk, counted from the source
-# (FFMA = 2, FADD/FMUL = 1, MUFU = 1): far node monopole + quadrupole + potential; gravity
-# particle pair (symmetrised softened force, potential, adaptive correction); SPH pair
-# (pressure + grad-h factors, Monaghan viscosity, du/dt).
+# (FFMA = 2, FADD/FMUL = 1, MUFU = 1): far node monopole + quadrupole + potential; Newtonian
+# particle pair (r >= 2 max(eps_i, eps_j): point-mass force and potential); softened particle pair
+# (both softened kernels, potential, adaptive-softening correction); SPH pair (pressure with the
+# grad-h factors, Monaghan viscosity, du/dt).
 FLOPS_FAR = 54
-FLOPS_PP = 60
+FLOPS_PP_NEWTON = 19
+FLOPS_PP_SOFT = 89
 FLOPS_SPH = 85
-FP32_LANES_PER_SM = 128
-# DRAM bytes (read + written) per particle of one force-walk launch, by leaf size: ncu capture of
-# k_walk<1,1,0,0> on 2^18 DM + 2^17 gas (plain FP32), 393,216 particles; leaf 16: 39.10 MB read +
-# 3.40 MB written; leaf 24: 35.32 MB + 2.68 MB
-WALK_DRAM_BYTES_PER_PARTICLE = {16: (39.099648e6 + 3.401728e6) / 393216, 24: (35.320064e6 + 2.677248e6) / 393216}
+# Algorithmic DRAM bytes per particle of the tree build (one pass over each kernel's inputs and
+# outputs): bbox 12, keys 12 + 12, 8 radix passes x (histogram 8 + scatter 24), permute 40 + 44,
+# common prefixes 8 + 5, node counts 5, their scan 16, moments 20; plus per node: fill 16,
+# link 80, moments 150.
+BUILD_BYTES_PER_PARTICLE = 12 + 24 + 8 * 32 + 84 + 13 + 5 + 16 + 20
+BUILD_BYTES_PER_NODE = 16 + 80 + 150
+
+
+# Measured copy bandwidth of the GB300s (GB/s), the build's HBM roofline denominator.
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6766.0
+
+
+HBM_PEAK_GBS = _hbm_peak()
+# DRAM bytes (read + written) of one force-walk launch from an ncu capture of the same build and
+# command, keyed by (workload, leaf size); empty until a capture of the current walk is recorded.
+WALK_TRAFFIC = {}
 
 
 def log(*a):
@@ -90,6 +108,15 @@ class ClockSampler:
             self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def current_mhz(self):
+        """Most recent SM clock sample (MHz), or None."""
+        try:
+            self.f.flush()
+            rows = [ln.split(",") for ln in open(self.path) if ln.count(",") >= 7]
+            return float(rows[-1][0]) if rows else None
+        except Exception:
+            return None
 
     def stop(self):
         if self.proc is None:
@@ -351,6 +378,9 @@ def main():
     sampler = ClockSampler(gpu_uuid(torch, dev))
     sampler.start()
     time.sleep(0.5)
+    # the FP32 roofline's denominator, measured on this GPU now (one ~80 ms FMA-chain kernel)
+    peak_tflops, _ = E.evol_fp32_peak(20000)
+    peak_clock = sampler.current_mhz()
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -372,6 +402,7 @@ def main():
     clocks = sampler.stop()
     value, ms_max = replica_rate(dist, dev, ms, w.n, args.steps, world)
     diag = E.evol_get_diagnostics(ctx)
+    cnt = E.evol_get_counters(ctx)               # work counters of the last timed step
     n_total = w.n * world
 
     # ---- e2e through the host-buffer entry point (pinned host memory) ----
@@ -429,29 +460,24 @@ def main():
                                  int(ds.params.leaf_size)))
 
     # ---- roofline of the dominant kernel (the force walk) ----
-    # DRAM bytes of one walk launch, scaled by particle count from an ncu capture of the same kernel
-    # on the 1/8-size mixed-species workload (plain FP32)
-    traffic = None
-    leaf_used = int(ds.params.leaf_size)
-    if args.workload in ("c3", "c3s") and prec == E.EVOL_FP32_PLAIN and leaf_used in WALK_DRAM_BYTES_PER_PARTICLE:
-        traffic = WALK_DRAM_BYTES_PER_PARTICLE[leaf_used] * w.n
-    far, pp, sph = diag[12], diag[13], diag[14]
-    flops = far * FLOPS_FAR + pp * FLOPS_PP + sph * FLOPS_SPH
+    far, pp, sph, soft = float(cnt[0]), float(cnt[1]), float(cnt[2]), float(cnt[8])
+    flops = far * FLOPS_FAR + (pp - soft) * FLOPS_PP_NEWTON + soft * FLOPS_PP_SOFT + sph * FLOPS_SPH
     walk_s = statistics.mean(walk_ms) / 1e3
-    props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
-    peak_max = sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     achieved = flops / walk_s / 1e12
     clk = clocks["sm_mhz"] if clocks else None
     roofline = {"bound": "alu", "kernel": "k_walk (gravity + SPH force walk)", "achieved": achieved,
-                "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max, "traffic": traffic,
-                "traffic_basis": "ncu dram bytes of the 1/8-size capture scaled by particles" if traffic else None,
-                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
-                "frac_at_sampled_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12)) if clk else None,
+                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                "traffic": WALK_TRAFFIC.get((args.workload, int(ds.params.leaf_size))) if prec == E.EVOL_FP32_PLAIN else None,
+                "peak_basis": f"measured: FMA-chain kernel (evol_fp32_peak) in this run at {peak_clock} MHz",
                 "walk_ms": walk_s * 1e3,
-                "interactions_per_step": {"far": far, "pp": pp, "sph": sph},
-                "flops_per_interaction": {"far": FLOPS_FAR, "pp": FLOPS_PP, "sph": FLOPS_SPH}}
+                "flops_per_step": flops,
+                "interactions_per_step": {"far": far, "pp_newtonian": pp - soft, "pp_softened": soft, "sph": sph},
+                "flops_per_interaction": {"far": FLOPS_FAR, "pp_newtonian": FLOPS_PP_NEWTON,
+                                          "pp_softened": FLOPS_PP_SOFT, "sph": FLOPS_SPH},
+                "lane_fill": {"far": far / max(cnt[9], 1), "pair_pass1": pp / max(cnt[10], 1),
+                              "pair_pass2": (soft + sph) / max(cnt[11], 1)}}
     ph = np.mean(np.array(phase), axis=0).tolist()
+    build_bytes = float(w.n * BUILD_BYTES_PER_PARTICLE + diag[11] * BUILD_BYTES_PER_NODE)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -473,6 +499,10 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "working set > L2 (inputs 40 B/particle x 3.1M + tree), no flush"},
                 "phase_ms": {"build": ph[0], "eps_solve": ph[1], "h_solve": ph[2], "walk": ph[3], "total": ph[4]},
+                "build_roofline": {"bound": "hbm", "achieved": build_bytes / (ph[0] * 1e-3) / 1e9,
+                                   "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                   "frac": build_bytes / (ph[0] * 1e-3) / 1e9 / HBM_PEAK_GBS,
+                                   "algorithmic_bytes": build_bytes},
                 "interactions_per_s": {"far": far / walk_s, "pp": pp / walk_s, "sph": sph / walk_s},
                 "length_iterations_per_particle": diag[15] / max(1, w.n + w.n_gas),
                 "status_last_step": rc,

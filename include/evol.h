@@ -178,6 +178,17 @@ int evol_sync(evol_ctx *ctx);
  * [15] length-solve iterations (sum over particles). */
 int evol_get_diagnostics(evol_ctx *ctx, double out[16]);
 
+/* Work counters of the last step (valid after evol_sync), 16 values:
+ *   [0] far-node interactions   [1] particle pairs (all)   [2] SPH pairs
+ *   [3] length-solve iterations (sum over particles)
+ *   [4] [5] [6] work-queue positions of the walk, the h solve and the eps solve
+ *   [7] nonzero if a traversal hit its pop or climb cap
+ *   [8] gravity pairs inside 2 max(eps_i, eps_j) (softened; the rest are Newtonian)
+ *   [9] lane slots of the far-node loop, [10] of the pair loop's first pass, [11] of its second
+ *       pass (32 per entry or trip: interactions / slots is the fraction of busy lanes)
+ *   [12..15] zero */
+int evol_get_counters(evol_ctx *ctx, uint64_t out[16]);
+
 /* Debug copies of internal state (valid after evol_sync), into host memory of cap bytes.
  * Returns the number of ELEMENTS available (whatever cap), or a negative status.
  *   EVOL_DBG_KEYS   uint64[n]   Morton keys in sorted order

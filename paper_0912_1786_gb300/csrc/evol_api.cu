@@ -91,7 +91,7 @@ uint64_t fnv(uint64_t h, const void *data, size_t len)
 
 void reset_counters(evol_ctx *c)
 {
-    cudaMemsetAsync(c->d.counters, 0, 8 * sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(c->d.counters, 0, EVOL_NCOUNTERS * sizeof(unsigned long long), c->stream);
 }
 
 int ensure_tree(evol_ctx *c, const evol_particles *p, const evol_params *prm)
@@ -217,7 +217,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.cand_leaf, 1);                                      // unused
     rc |= dalloc(&d.cand_mask, 1);
     rc |= dalloc(&d.diag_part, 16 * c->diag_blocks); rc |= dalloc(&d.diag, 16);
-    rc |= dalloc(&d.counters, 8); rc |= dalloc(&d.err, 1); rc |= dalloc(&d.nnodes, 1);
+    rc |= dalloc(&d.counters, EVOL_NCOUNTERS); rc |= dalloc(&d.err, 1); rc |= dalloc(&d.nnodes, 1);
     c->nsys_cap = NSYS_CAP;
     rc |= dalloc(&d.cube, 4 * (int64_t)NSYS_CAP); rc |= dalloc(&d.fcube, 4 * (int64_t)NSYS_CAP);
     rc |= dalloc(&d.bbox_part, 6 * c->bbox_blocks);
@@ -230,7 +230,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) rc = EVOL_ECUDA;
     if (!rc) {
         cudaMemset(d.err, 0, sizeof(int));
-        cudaMemset(d.counters, 0, 8 * sizeof(unsigned long long));
+        cudaMemset(d.counters, 0, EVOL_NCOUNTERS * sizeof(unsigned long long));
         cudaMemset(d.nnodes, 0, sizeof(int32_t));
         cudaMemset(d.diag, 0, 16 * sizeof(double));
         if (cudaDeviceSynchronize() != cudaSuccess) rc = EVOL_ECUDA;
@@ -619,6 +619,16 @@ int evol_get_diagnostics(evol_ctx *c, double out[16])
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return EVOL_ECUDA;
     return cudaMemcpy(out, c->d.diag, 16 * sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess ? EVOL_OK
                                                                                                  : EVOL_ECUDA;
+}
+
+int evol_get_counters(evol_ctx *c, uint64_t out[16])
+{
+    if (!c || !out) return EVOL_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return EVOL_ECUDA;
+    unsigned long long v[EVOL_NCOUNTERS];
+    if (cudaMemcpy(v, c->d.counters, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return EVOL_ECUDA;
+    for (int k = 0; k < 16; ++k) out[k] = k < EVOL_NCOUNTERS ? (uint64_t)v[k] : 0;
+    return EVOL_OK;
 }
 
 int evol_get_timings(evol_ctx *c, float out[5])

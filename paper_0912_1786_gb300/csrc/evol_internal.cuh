@@ -9,6 +9,7 @@
 
 #define EVOL_MAXLEVEL 21          // 21 bits per axis, 63-bit Morton keys
 #define EVOL_WARP 32
+#define EVOL_NCOUNTERS 16
 #define EVOL_PI_F 3.14159265358979f
 
 // ---- device error word: first error wins ------------------------------------------------
@@ -59,7 +60,7 @@ struct evol_dev {
     // reductions / counters
     double *diag_part;       // per-block partials of diagnostics
     double *diag;            // 16
-    unsigned long long *counters;   // [0] far [1] pp [2] sph [3] iters [4] work queue [5] q2 [6] q3
+    unsigned long long *counters;   // EVOL_NCOUNTERS; indices as evol_get_counters documents
     int *err;
     int32_t *nnodes;         // device node count
     double *cube;            // corner x, y, z, side of every system (4 per system)

@@ -48,6 +48,7 @@ struct WalkSmem {
     float4 nh[WK_WARPS][NEARCAP];
     float4 ns[WK_WARPS][NEARCAP];
     int norig[WK_WARPS][NEARCAP];
+    float4 gbox[WK_WARPS][3];     // group bounds: centre, 0 | half widths, 0 | emax, emin, hmax, hmin
 };
 
 // The kernel functions of the pair loop in a division-free form: each takes u and iu = 1/u (iu is
@@ -55,14 +56,17 @@ struct WalkSmem {
 // from quantities already at hand (eps/r, h/r).  Same polynomials as the FP32 kernel functions:
 //   gsoft_over_r: eps^3 phi'(r)/r,  phisoft: eps phi(r),  dw_over_u: pi h^5 (dW/dr)/r,
 //   tc_over_u: the Thomas-Couchman form of the latter.
-// The two branches share one Horner form in u whose coefficients are selected by u < 1.
+// The two branches share one Horner form in u whose coefficients are selected by u < 1; the
+// outer branch's 1/u terms are selected, not multiplied by zero, so that a huge 1/u (a pair far
+// closer than the softening length) cannot turn into 0 * inf.
 __device__ __forceinline__ float gsoft_over_r_u(float u, float iu)
 {
     // u < 1: 4/3 - 6/5 u^2 + 1/2 u^3;   1 <= u < 2: 8/3 - 3u + 6/5 u^2 - 1/6 u^3 - 1/(15 u^3)
     const bool in = u < 1.f;
     const float c1 = in ? 0.f : -3.f, c2 = in ? -1.2f : 1.2f, c3 = in ? 0.5f : -1.f / 6.f;
-    const float c0 = in ? 4.f / 3.f : 8.f / 3.f, e = in ? 0.f : -1.f / 15.f;
-    return fmaf(u, fmaf(u, fmaf(u, c3, c2), c1), c0) + e * (iu * iu * iu);
+    const float c0 = in ? 4.f / 3.f : 8.f / 3.f;
+    const float tail = in ? 0.f : (-1.f / 15.f) * (iu * iu * iu);
+    return fmaf(u, fmaf(u, fmaf(u, c3, c2), c1), c0) + tail;
 }
 
 __device__ __forceinline__ float phisoft_u(float u, float iu)
@@ -71,9 +75,10 @@ __device__ __forceinline__ float phisoft_u(float u, float iu)
     // 1 <= u < 2: -8/5 + 4/3 u^2 - u^3 + 3/10 u^4 - 1/30 u^5 + 1/(15 u)
     const bool in = u < 1.f;
     const float c2 = in ? 2.f / 3.f : 4.f / 3.f, c3 = in ? 0.f : -1.f, c4 = in ? -0.3f : 0.3f;
-    const float c5 = in ? 0.1f : -1.f / 30.f, c0 = in ? -1.4f : -1.6f, e = in ? 0.f : 1.f / 15.f;
+    const float c5 = in ? 0.1f : -1.f / 30.f, c0 = in ? -1.4f : -1.6f;
+    const float tail = in ? 0.f : (1.f / 15.f) * iu;
     const float u2 = u * u;
-    return fmaf(u2, fmaf(u, fmaf(u, fmaf(u, c5, c4), c3), c2), c0) + e * iu;
+    return fmaf(u2, fmaf(u, fmaf(u, fmaf(u, c5, c4), c3), c2), c0) + tail;
 }
 
 __device__ __forceinline__ float dw_over_u_u(float u, float iu)
@@ -135,7 +140,11 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
         double tax = 0, tay = 0, taz = 0, tpot = 0, thx = 0, thy = 0, thz = 0, tdu = 0;
         unsigned long long hfar = 0, hnear = 0, hsph = 0;
         int cfar = 0, cpp = 0, csph = 0;
-        unsigned long long wfar = 0, wpp = 0, wsph = 0;
+        // interaction counts of this lane (one group's counts fit 32 bits)
+        unsigned wfar = 0, wpp = 0, wsph = 0, wsoft = 0;
+        // lane slots issued (32 per entry or per loop trip; kept by lane 0): fill of the far loop,
+        // of pass 1 and of pass 2 of the near loop
+        unsigned wfar_slots = 0, wnear_slots = 0, wpass2_slots = 0;
 
         auto fold = [&]() {
             if (MIXED) {
@@ -163,6 +172,7 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
                 sm.fQ1[w][l] = d.nQ1[id];
                 wfar += __popc(sm.far_mask[w][l]);     // interaction count (this lane's share)
             }
+            if (lane == 0) wfar_slots += 32u * (unsigned)padded;
             __syncwarp();
             for (int e = 0; e < padded; e += 4) {
 #pragma unroll
@@ -210,13 +220,15 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
                 }
                 if (CHECK) sm.norig[w][l] = d.orig[j];
             }
+            if (lane == 0) wnear_slots += 32u * (unsigned)((nnear + 1) & ~1);
             __syncwarp();
-            // gravity for every pair; the SPH pairs are marked per lane (bit t of sbits) and
-            // evaluated afterwards, each lane taking its own pairs, so that a warp runs the SPH
-            // terms about as often as its busiest lane has SPH pairs
+            // Pass 1, every entry, two at a time and branch-free.  A gravity pair farther apart than
+            // 2 max(eps_i, eps_j) is Newtonian: both softened kernels equal their point-mass forms there
+            // (Eqs. softforce, softphi) and the correction term vanishes with dW/dr; it is summed here.
+            // Pairs inside that distance, and gas pairs inside 2 max(h_i, h_j), are marked per lane
+            // (bit t of sbits) and evaluated in pass 2, each lane taking its own marked pairs, so that
+            // the warp runs the softened and SPH terms about as often as its busiest lane has such pairs.
             unsigned long long sbits = 0ull;
-            // two entries per step, branch-free: lanes outside an entry's mask (and the lane of
-            // the particle itself) take it with zero mass, so both chains can be in flight
             for (int t = 0; t < nnear; t += 2) {
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
@@ -232,27 +244,19 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
                     const float dy = evol_wrap(pi.y - pj.y, plen1, pm & 2);
                     const float dz = evol_wrap(pi.z - pj.z, plen2, pm & 4);
                     const float r2 = dx * dx + dy * dy + dz * dz;
+                    bool mark = false;
                     if (GRAV) {
-                        const float mj = mine ? pj.w : 0.f;
-                        // r and 1/r from one reciprocal square root (coincident particles: both 0)
+                        const float iem = fminf(ie_i, gj.x);               // 1 / max(eps_i, eps_j)
+                        const bool soft = r2 * (iem * iem) < 4.f;
                         const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                        const float r = r2 * rinv;
-                        const float ui = r * ie_i, uj = r * gj.x;
-                        const float iui = rinv * eps_i, iuj = rinv * rcp_fast(gj.x);
-                        const float rinv3 = rinv * rinv * rinv;
-                        const float fi = ui < 2.f ? gsoft_over_r_u(ui, iui) * ie_i * ie_i * ie_i : rinv3;
-                        const float fj = uj < 2.f ? gsoft_over_r_u(uj, iuj) * gj.x * gj.x * gj.x : rinv3;
-                        float f = -0.5f * mj * (fi + fj);
-                        acc.pot += mj * (ui < 2.f ? phisoft_u(ui, iui) * ie_i : -rinv);
-                        if (kp.adaptive) {
-                            const float ie2 = ie_i * ie_i, je2 = gj.x * gj.x;
-                            const float ci = (mine && ui < 2.f) ? xu_i * dw_over_u_u(ui, iui) * ie2 * ie2 * ie_i : 0.f;
-                            const float cj = uj < 2.f ? gj.y * dw_over_u_u(uj, iuj) * je2 * je2 * gj.x : 0.f;
-                            f += -0.5f * inv_pi * (ci + mj * inv_mi * cj);
-                        }
-                        acc.ax += f * dx;
-                        acc.ay += f * dy;
-                        acc.az += f * dz;
+                        const float mr = (mine && !soft) ? pj.w * rinv : 0.f;      // m_j / r
+                        const float mr3 = mr * (rinv * rinv);
+                        acc.ax = fmaf(-mr3, dx, acc.ax);
+                        acc.ay = fmaf(-mr3, dy, acc.ay);
+                        acc.az = fmaf(-mr3, dz, acc.az);
+                        acc.pot -= mr;
+                        mark = mine && soft;
+                        wsoft += mark ? 1u : 0u;
                     }
                     if (SPH && mine && gas_i && gj.z > 0.f) {
                         const float two_h = fmaxf(two_h_i, 2.f * gj.z);
@@ -262,56 +266,90 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
                                 hsph += evol_mix64((unsigned long long)sm.norig[w][tt]);
                             }
                             ++wsph;
-                            if (r2 > 0.f) sbits |= 1ull << tt;
+                            if (r2 > 0.f) mark = true;
                         }
                     }
+                    if (mark) sbits |= 1ull << tt;
                 }
             }
-            if (SPH && __any_sync(0xffffffffu, sbits != 0ull)) {
-                // every lane of the warp runs this pass; lanes past the end read nothing
+            // Pass 2: the marked pairs of each lane.  Every lane of the warp runs this loop; lanes past
+            // the end of the particle array have no marks and read nothing.
+            if (__any_sync(0xffffffffu, sbits != 0ull)) {
                 const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 gi = valid ? d.grav[s] : z4;
-                const float4 hi = valid ? d.hydro[s] : z4;
-                const float4 si = valid ? d.snd[s] : z4;
+                const float4 gi = (SPH && valid) ? d.grav[s] : z4;
+                const float4 hi = (SPH && valid) ? d.hydro[s] : z4;
+                const float4 si = (SPH && valid) ? d.snd[s] : z4;
                 while (__any_sync(0xffffffffu, sbits != 0ull)) {
+                    if (lane == 0) wpass2_slots += 32u;
                     if (sbits) {
                         const int t = __ffsll((long long)sbits) - 1;
                         sbits &= sbits - 1ull;
                         const float4 pj = sm.np[w][t];
                         const float4 gj = sm.ng[w][t];
-                        const float4 hj = sm.nh[w][t];
-                        const float4 sj = sm.ns[w][t];
                         const float dx = evol_wrap(pi.x - pj.x, plen0, pm & 1);
                         const float dy = evol_wrap(pi.y - pj.y, plen1, pm & 2);
                         const float dz = evol_wrap(pi.z - pj.z, plen2, pm & 4);
                         const float r2 = dx * dx + dy * dy + dz * dz;
-                        const float rinv = rsqrtf(r2);
+                        // r and 1/r from one reciprocal square root (coincident particles: both 0)
+                        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
                         const float r = r2 * rinv;
-                        const float ihi = si.z, ihj = sj.z;
-                        const float uhi = r * ihi, uhj = r * ihj;
-                        const float iuhi = rinv * gi.z, iuhj = rinv * gj.z;     // h / r
-                        const float ihi2 = ihi * ihi, ihj2 = ihj * ihj;
-                        const float kgi = (kp.use_tc ? tc_over_u_u(uhi, iuhi) : dw_over_u_u(uhi, iuhi)) * ihi2 * ihi2 * ihi * inv_pi;
-                        const float kgj = (kp.use_tc ? tc_over_u_u(uhj, iuhj) : dw_over_u_u(uhj, iuhj)) * ihj2 * ihj2 * ihj * inv_pi;
-                        const float fi = 1.f + gi.w * rcp_fast(pj.w);     // 1 + zeta_i / (m_j Omega*_i)
-                        const float fj = 1.f + gj.w * inv_mi;             // 1 + zeta_j / (m_i Omega*_j)
-                        const float vx = hi.x - hj.x, vy = hi.y - hj.y, vz = hi.z - hj.z;
-                        const float vr = vx * dx + vy * dy + vz * dz;
-                        float visc = 0.f;
-                        if (vr < 0.f) {
-                            const float hb = 0.5f * (gi.z + gj.z);
-                            const float mu = hb * vr * rcp_fast(r2 + 0.01f * hb * hb);
-                            const float cb = 0.5f * (si.x + sj.x);
-                            const float rb = 0.5f * (si.y + sj.y);
-                            visc = (-kp.alpha * cb * mu + kp.beta * mu * mu) * rcp_fast(rb);
+                        if (GRAV) {
+                            const float iem = fminf(ie_i, gj.x);
+                            if (r2 * (iem * iem) < 4.f) {          // the same test as pass 1
+                                // symmetrised softened pair force and potential (App. B), each side
+                                // softened where u < 2 and Newtonian beyond
+                                const float mj = pj.w;
+                                const float ui = r * ie_i, uj = r * gj.x;
+                                const float iui = rinv * eps_i, iuj = rinv * rcp_fast(gj.x);
+                                const float rinv3 = rinv * rinv * rinv;
+                                const float fi = ui < 2.f ? gsoft_over_r_u(ui, iui) * ie_i * ie_i * ie_i : rinv3;
+                                const float fj = uj < 2.f ? gsoft_over_r_u(uj, iuj) * gj.x * gj.x * gj.x : rinv3;
+                                float f = -0.5f * mj * (fi + fj);
+                                acc.pot += mj * (ui < 2.f ? phisoft_u(ui, iui) * ie_i : -rinv);
+                                if (kp.adaptive) {
+                                    // adaptive-softening correction (Eq. dLgravdr, mass-weighted reading)
+                                    const float ie2 = ie_i * ie_i, je2 = gj.x * gj.x;
+                                    const float ci = ui < 2.f ? xu_i * dw_over_u_u(ui, iui) * ie2 * ie2 * ie_i : 0.f;
+                                    const float cj = uj < 2.f ? gj.y * dw_over_u_u(uj, iuj) * je2 * je2 * gj.x : 0.f;
+                                    f += -0.5f * inv_pi * (ci + mj * inv_mi * cj);
+                                }
+                                acc.ax += f * dx;
+                                acc.ay += f * dy;
+                                acc.az += f * dz;
+                            }
                         }
-                        const float gbar = 0.5f * (kgi * fi + kgj * fj);
-                        const float pterm_i = hi.w * fi * kgi;
-                        const float sc = -pj.w * (pterm_i + hj.w * fj * kgj + visc * gbar);
-                        acc.hx += sc * dx;
-                        acc.hy += sc * dy;
-                        acc.hz += sc * dz;
-                        acc.du += pj.w * (pterm_i + 0.5f * visc * gbar) * vr;
+                        if (SPH && gas_i && gj.z > 0.f && r2 > 0.f) {
+                            const float two_h = fmaxf(two_h_i, 2.f * gj.z);
+                            if (r2 < two_h * two_h) {                // the same test as pass 1
+                                const float4 hj = sm.nh[w][t];
+                                const float4 sj = sm.ns[w][t];
+                                const float ihi = si.z, ihj = sj.z;
+                                const float uhi = r * ihi, uhj = r * ihj;
+                                const float iuhi = rinv * gi.z, iuhj = rinv * gj.z;     // h / r
+                                const float ihi2 = ihi * ihi, ihj2 = ihj * ihj;
+                                const float kgi = (kp.use_tc ? tc_over_u_u(uhi, iuhi) : dw_over_u_u(uhi, iuhi)) * ihi2 * ihi2 * ihi * inv_pi;
+                                const float kgj = (kp.use_tc ? tc_over_u_u(uhj, iuhj) : dw_over_u_u(uhj, iuhj)) * ihj2 * ihj2 * ihj * inv_pi;
+                                const float fi = 1.f + gi.w * rcp_fast(pj.w);     // 1 + zeta_i / (m_j Omega*_i)
+                                const float fj = 1.f + gj.w * inv_mi;             // 1 + zeta_j / (m_i Omega*_j)
+                                const float vx = hi.x - hj.x, vy = hi.y - hj.y, vz = hi.z - hj.z;
+                                const float vr = vx * dx + vy * dy + vz * dz;
+                                float visc = 0.f;
+                                if (vr < 0.f) {
+                                    const float hb = 0.5f * (gi.z + gj.z);
+                                    const float mu = hb * vr * rcp_fast(r2 + 0.01f * hb * hb);
+                                    const float cb = 0.5f * (si.x + sj.x);
+                                    const float rb = 0.5f * (si.y + sj.y);
+                                    visc = (-kp.alpha * cb * mu + kp.beta * mu * mu) * rcp_fast(rb);
+                                }
+                                const float gbar = 0.5f * (kgi * fi + kgj * fj);
+                                const float pterm_i = hi.w * fi * kgi;
+                                const float sc = -pj.w * (pterm_i + hj.w * fj * kgj + visc * gbar);
+                                acc.hx += sc * dx;
+                                acc.hy += sc * dy;
+                                acc.hz += sc * dz;
+                                acc.du += pj.w * (pterm_i + 0.5f * visc * gbar) * vr;
+                            }
+                        }
                     }
                 }
             }
@@ -340,10 +378,16 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
             hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
             hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
         }
-        const float gcx = 0.5f * (gx0 + gx1), gcy = 0.5f * (gy0 + gy1), gcz = 0.5f * (gz0 + gz1);
-        const float gwx = 0.5f * (gx1 - gx0), gwy = 0.5f * (gy1 - gy0), gwz = 0.5f * (gz1 - gz0);
         const bool all_gas = SPH && __all_sync(0xffffffffu, !active || gas_i);
         if (!GRAV) emin = 0.f;
+        // the group bounds live in shared memory for the traversal (read as broadcasts), which keeps
+        // them out of the registers the pair loops need
+        if (lane == 0) {
+            sm.gbox[w][0] = make_float4(0.5f * (gx0 + gx1), 0.5f * (gy0 + gy1), 0.5f * (gz0 + gz1), 0.f);
+            sm.gbox[w][1] = make_float4(0.5f * (gx1 - gx0), 0.5f * (gy1 - gy0), 0.5f * (gz1 - gz0), 0.f);
+            sm.gbox[w][2] = make_float4(emax, emin, hmax, hmin);
+        }
+        __syncwarp();
 
         int2 *stk = d.wstack + (size_t)(blockIdx.x * WK_WARPS + w) * kp.stack_stride;
         // one stack entry per system present in the group: its root with the mask of its lanes
@@ -387,6 +431,9 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
                 const float4 B = d.nB[node];
                 const float4 C = d.nC[node];
                 const float4 A = GRAV ? d.nA[node] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 G0 = sm.gbox[w][0], G1 = sm.gbox[w][1], G2 = sm.gbox[w][2];
+                const float gcx = G0.x, gcy = G0.y, gcz = G0.z, gwx = G1.x, gwy = G1.y, gwz = G1.z;
+                const float emax = G2.x, emin = G2.y, hmax = G2.z, hmin = G2.w;
                 const float dx = fabsf(evol_wrap(B.x - gcx, plen0, pm & 1));
                 const float dy = fabsf(evol_wrap(B.y - gcy, plen1, pm & 2));
                 const float dz = fabsf(evol_wrap(B.z - gcz, plen2, pm & 4));
@@ -570,17 +617,22 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
             }
         }
         // interaction counters, per lane: summed over the warp
-        unsigned long long wf = wfar, wp = wpp, ws = wsph;
+        unsigned long long wf = wfar, wp = wpp, ws = wsph, wo = wsoft;   // warp sums in 64 bits
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             wf += __shfl_xor_sync(0xffffffffu, wf, o);
             wp += __shfl_xor_sync(0xffffffffu, wp, o);
             ws += __shfl_xor_sync(0xffffffffu, ws, o);
+            wo += __shfl_xor_sync(0xffffffffu, wo, o);
         }
         if (lane == 0) {
             atomicAdd(&d.counters[0], wf);
             atomicAdd(&d.counters[1], wp);
             atomicAdd(&d.counters[2], ws);
+            atomicAdd(&d.counters[8], wo);
+            atomicAdd(&d.counters[9], (unsigned long long)wfar_slots);
+            atomicAdd(&d.counters[10], (unsigned long long)wnear_slots);
+            atomicAdd(&d.counters[11], (unsigned long long)wpass2_slots);
         }
     }
 }

@@ -71,6 +71,7 @@ def lib():
         L.evol_sync.argtypes = [vp]
         L.evol_get_diagnostics.argtypes = [vp, pp(C.c_double)]
         L.evol_get_timings.argtypes = [vp, pp(C.c_float)]
+        L.evol_get_counters.argtypes = [vp, pp(C.c_uint64)]
         L.evol_get_debug.argtypes = [vp, C.c_int, vp, C.c_int64]
         L.evol_get_debug.restype = C.c_int64
         L.evol_set_check_mode.argtypes = [vp, C.c_int]
@@ -221,6 +222,12 @@ def evol_get_diagnostics(ctx):
 def evol_get_timings(ctx):
     out = (C.c_float * 5)()
     _check(lib().evol_get_timings(ctx, out), "evol_get_timings")
+    return list(out)
+
+
+def evol_get_counters(ctx):
+    out = (C.c_uint64 * 16)()
+    _check(lib().evol_get_counters(ctx, out), "evol_get_counters")
     return list(out)
 
 
