@@ -186,7 +186,8 @@ int evol_get_diagnostics(evol_ctx *ctx, double out[16]);
  *   [8] gravity pairs inside 2 max(eps_i, eps_j) (softened; the rest are Newtonian)
  *   [9] lane slots of the far-node loop, [10] of the pair loop's first pass, [11] of its second
  *       pass (32 per entry or trip: interactions / slots is the fraction of busy lanes)
- *   [12..15] zero */
+ *   [12] nodes popped by the force walk's groups, [13] of them tested lane by lane (neither
+ *        accepted nor opened for the whole group), [14] leaves opened, [15] internal nodes opened */
 int evol_get_counters(evol_ctx *ctx, uint64_t out[16]);
 
 /* Debug copies of internal state (valid after evol_sync), into host memory of cap bytes.
@@ -249,12 +250,13 @@ int evol_sort_keys_noalloc(int64_t n, const float *x, const float *y, const floa
                            int32_t *perm, double *cube, void *stream);
 
 /* Measurement helper (not part of the paper's method): the device's FP32 throughput, measured
- * by one kernel in which every thread runs eight independent chains of `iters` x 64 fused
- * multiply-adds (2 operations each) over 2048 resident threads per SM, on the current device.
- * Writes TFLOP/s to *tflops and the kernel's duration to *ms (may be NULL).  Synchronous;
- * allocates a few bytes of device memory for the duration of the call.  This is the peak the
- * force walk's FP32 roofline fraction is quoted against. */
-int evol_fp32_peak(int iters, double *tflops, float *ms);
+ * by kernels in which every thread runs eight independent chains of `iters` x 64 fused
+ * multiply-adds (2 operations each) over 2048 resident threads per SM, on the current device:
+ * once with scalar FP32 FMAs (*tflops) and once with packed two-wide FMAs (fma.rn.f32x2;
+ * *tflops_packed, may be NULL).  *ms (may be NULL) receives the scalar kernel's duration.
+ * Synchronous; allocates a few bytes of device memory for the duration of the call.  The larger
+ * rate is the peak the force walk's FP32 roofline fraction is quoted against. */
+int evol_fp32_peak(int iters, double *tflops, double *tflops_packed, float *ms);
 
 const char *evol_strerror(int code);
 

@@ -26,6 +26,12 @@
 namespace {
 
 constexpr int WK_THREADS = 128;
+#ifndef EVOL_WALK_MINB
+#define EVOL_WALK_MINB 5           // resident blocks per SM the production walk is compiled for
+#endif
+#ifndef EVOL_FAR_UNROLL
+#define EVOL_FAR_UNROLL 4          // entry pairs per trip of the far-node loop
+#endif
 constexpr int WK_WARPS = WK_THREADS / 32;
 constexpr int FARCAP = 64;
 constexpr int NEARCAP = 64;
@@ -38,17 +44,21 @@ struct WalkSmem {
     float4 bC[WK_WARPS][32];      // box half widths, 2 epsmax
     int far_id[WK_WARPS][FARCAP];
     unsigned far_mask[WK_WARPS][FARCAP];
-    float4 fA[WK_WARPS][FARCAP];
-    float4 fQ0[WK_WARPS][FARCAP];
-    float4 fQ1[WK_WARPS][FARCAP];
+    // far nodes in pairs for the packed two-wide evaluation: for the pair of entries (2p, 2p + 1),
+    // component c of entry 2p + k sits at fpair[p][2c + k], c = x, y, z, -M, Qxx, Qyy, Qzz, Qxy,
+    // Qxz, Qyz (centre of mass, mass and traceless quadrupole)
+    __align__(16) float fpair[WK_WARPS][FARCAP / 2][20];
     int near_j[WK_WARPS][NEARCAP];
-    unsigned near_mask[WK_WARPS][NEARCAP];
-    float4 np[WK_WARPS][NEARCAP];
+    unsigned near_mask[WK_WARPS][NEARCAP];       // lanes that opened the entry's leaf, less its own lane
+    // near entries in pairs for the two-wide first pass: component c of entry 2q + k sits at
+    // npair[q][2c + k], c = x, y, z, m, E = (2 eps)^2, H = (2 h)^2 (-1: not gas)
+    __align__(16) float npair[WK_WARPS][NEARCAP / 2][12];
     float4 ng[WK_WARPS][NEARCAP];
     float4 nh[WK_WARPS][NEARCAP];
     float4 ns[WK_WARPS][NEARCAP];
     int norig[WK_WARPS][NEARCAP];
     float4 gbox[WK_WARPS][3];     // group bounds: centre, 0 | half widths, 0 | emax, emin, hmax, hmin
+    unsigned wc[WK_WARPS][8];     // per-group work counts kept by lane 0 (see the end of k_walk)
 };
 
 // The kernel functions of the pair loop in a division-free form: each takes u and iu = 1/u (iu is
@@ -96,6 +106,56 @@ __device__ __forceinline__ float tc_over_u_u(float u, float iu)
 // 1/x from the hardware reciprocal (about 1 ulp), for operands of the pair loop
 __device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.f, x); }
 
+// Packed two-wide FP32 arithmetic (add/mul/fma .rn.f32x2): one instruction computes the same
+// operation, rounded the same way, on two independent FP32 values held in a 64-bit register.
+// The far-node loop evaluates two accepted nodes per lane with it, which halves the issue slots
+// its arithmetic needs.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo2(f32x2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    (void)b;
+    return a;
+}
+__device__ __forceinline__ float hi2(f32x2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    (void)a;
+    return b;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 template <bool MIXED>
 struct Acc {
     float ax = 0.f, ay = 0.f, az = 0.f, pot = 0.f;      // gravity (without G)
@@ -106,14 +166,15 @@ struct Acc {
 // (at most 102 registers) without spilling; every other variant carries a minimum of one block
 // per SM, so that the compiler keeps its state in registers instead of spilling to local memory.
 template <bool GRAV, bool SPH, bool MIXED, bool CHECK>
-__global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) ? 5 : 1) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) ? EVOL_WALK_MINB : 1) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int n = kp.n;
     const int ngroups = (n + 31) >> 5;
-    const int pm = SPH ? kp.periodic_mask : 0;
+    // periodic axes come only with SPH alone (periodic gravity is rejected by the entry points)
+    const int pm = (SPH && !GRAV) ? kp.periodic_mask : 0;
     const float plen0 = kp.plen[0], plen1 = kp.plen[1], plen2 = kp.plen[2];
     const float inv_pi = 1.f / EVOL_PI_F;
 
@@ -135,6 +196,10 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
         const float two_h_i = gas_i ? 2.f * g0.z : 0.f;
         const float inv_mi = valid ? 1.f / pi.w : 0.f;
         const float eps_i = GRAV && valid ? 1.f / ie_i : 0.f;
+        // squared near radii of the pair tests: softened gravity inside max(E_i, E_j), SPH inside
+        // max(H_i, H_j) when both are gas (H = -1 marks a particle that is not)
+        const float E_i = two_eps_i * two_eps_i;
+        const float H_i = gas_i ? two_h_i * two_h_i : -1.f;
 
         Acc<MIXED> acc;
         double tax = 0, tay = 0, taz = 0, tpot = 0, thx = 0, thy = 0, thz = 0, tdu = 0;
@@ -142,9 +207,12 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
         int cfar = 0, cpp = 0, csph = 0;
         // interaction counts of this lane (one group's counts fit 32 bits)
         unsigned wfar = 0, wpp = 0, wsph = 0, wsoft = 0;
-        // lane slots issued (32 per entry or per loop trip; kept by lane 0): fill of the far loop,
-        // of pass 1 and of pass 2 of the near loop
-        unsigned wfar_slots = 0, wnear_slots = 0, wpass2_slots = 0;
+        // per-group counts kept by lane 0 in shared memory: lane slots issued (32 per entry or per
+        // loop trip) by the far loop [0], pass 1 [1] and pass 2 [2] of the pair loop; nodes popped
+        // [3], tested lane by lane [4]; leaves [5] and internal nodes [6] opened
+        unsigned *wc = sm.wc[w];
+        if (lane < 8) wc[lane] = 0u;
+        __syncwarp();
 
         auto fold = [&]() {
             if (MIXED) {
@@ -158,8 +226,9 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
 
         auto flush_far = [&]() {
             __syncwarp();
-            // pad to a multiple of 4 with empty-mask entries (node 0 is always valid)
-            const int padded = (nfar + 3) & ~3;
+            // pad to a whole trip of the loop with empty-mask entries (node 0 is always valid)
+            constexpr int TRIP = 2 * EVOL_FAR_UNROLL;
+            const int padded = (nfar + TRIP - 1) / TRIP * TRIP;
             if (lane < padded - nfar) {
                 sm.far_id[w][nfar + lane] = 0;
                 sm.far_mask[w][nfar + lane] = 0u;
@@ -167,35 +236,52 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
             __syncwarp();
             for (int l = lane; l < padded; l += 32) {
                 const int id = sm.far_id[w][l];
-                sm.fA[w][l] = d.nA[id];
-                sm.fQ0[w][l] = d.nQ0[id];
-                sm.fQ1[w][l] = d.nQ1[id];
+                const float4 A = d.nA[id], Q0 = d.nQ0[id], Q1 = d.nQ1[id];
+                float *f = sm.fpair[w][l >> 1] + (l & 1);
+                f[0] = A.x; f[2] = A.y; f[4] = A.z; f[6] = -Q0.w;
+                f[8] = Q0.x; f[10] = Q0.y; f[12] = Q0.z; f[14] = Q1.x; f[16] = Q1.y; f[18] = Q1.z;
                 wfar += __popc(sm.far_mask[w][l]);     // interaction count (this lane's share)
             }
-            if (lane == 0) wfar_slots += 32u * (unsigned)padded;
+            if (lane == 0) wc[0] += 32u * (unsigned)padded;
             __syncwarp();
-            for (int e = 0; e < padded; e += 4) {
+            // monopole + traceless quadrupole about the centre of mass, d = r_i - com:
+            //   a += -M d/d^3 + Q d/d^5 - 5/2 (d.Q.d) d/d^7,  phi += -M/d - 1/2 (d.Q.d)/d^5
+            // two entries per packed operation; lanes outside an entry's mask take 1/d = 0 for it,
+            // so every term vanishes for them
+            const f32x2 PX = pk2(pi.x, pi.x), PY = pk2(pi.y, pi.y), PZ = pk2(pi.z, pi.z);
+            const f32x2 KM25 = pk2(-2.5f, -2.5f), KM05 = pk2(-0.5f, -0.5f);
+            f32x2 fax = 0ull, fay = 0ull, faz = 0ull, fpot = 0ull;      // +0.0f in both halves
+            for (int e = 0; e < padded; e += TRIP) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const unsigned msk = sm.far_mask[w][e + u];
-                    const float4 A = sm.fA[w][e + u], Q0 = sm.fQ0[w][e + u], Q1 = sm.fQ1[w][e + u];
-                    const float dx = pi.x - A.x, dy = pi.y - A.y, dz = pi.z - A.z;
-                    const float d2 = dx * dx + dy * dy + dz * dz;
-                    // lanes outside the mask get rinv = 0, so every term below vanishes for them
-                    const float rinv = ((msk >> lane) & 1u) ? rsqrtf(d2) : 0.f;
-                    const float rinv2 = rinv * rinv;
-                    const float r3 = rinv * rinv2, r5 = r3 * rinv2, r7 = r5 * rinv2;
-                    const float qx = Q0.x * dx + Q1.x * dy + Q1.y * dz;
-                    const float qy = Q1.x * dx + Q0.y * dy + Q1.z * dz;
-                    const float qz = Q1.y * dx + Q1.z * dy + Q0.z * dz;
-                    const float dqd = dx * qx + dy * qy + dz * qz;
-                    const float c1 = -Q0.w * r3 - 2.5f * dqd * r7;
-                    acc.ax += c1 * dx + r5 * qx;
-                    acc.ay += c1 * dy + r5 * qy;
-                    acc.az += c1 * dz + r5 * qz;
-                    acc.pot += -Q0.w * rinv - 0.5f * dqd * r5;
+                for (int u = 0; u < EVOL_FAR_UNROLL; ++u) {
+                    const int pp = (e >> 1) + u;
+                    const uint2 mk = *reinterpret_cast<const uint2 *>(&sm.far_mask[w][2 * pp]);
+                    const ulonglong2 *F = reinterpret_cast<const ulonglong2 *>(sm.fpair[w][pp]);
+                    const ulonglong2 v0 = F[0], v1 = F[1], v2 = F[2], v3 = F[3], v4 = F[4];
+                    // v0 = (x, y), v1 = (z, -M), v2 = (Qxx, Qyy), v3 = (Qzz, Qxy), v4 = (Qxz, Qyz)
+                    const f32x2 dx = sub2(PX, v0.x), dy = sub2(PY, v0.y), dz = sub2(PZ, v1.x);
+                    const f32x2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                    const float r0 = ((mk.x >> lane) & 1u) ? rsqrtf(lo2(d2)) : 0.f;
+                    const float r1 = ((mk.y >> lane) & 1u) ? rsqrtf(hi2(d2)) : 0.f;
+                    const f32x2 rinv = pk2(r0, r1);
+                    const f32x2 rinv2 = mul2(rinv, rinv);
+                    const f32x2 r3 = mul2(rinv, rinv2), r5 = mul2(r3, rinv2);
+                    const f32x2 qx = fma2(v4.x, dz, fma2(v3.y, dy, mul2(v2.x, dx)));
+                    const f32x2 qy = fma2(v4.y, dz, fma2(v2.y, dy, mul2(v3.y, dx)));
+                    const f32x2 qz = fma2(v3.x, dz, fma2(v4.y, dy, mul2(v4.x, dx)));
+                    const f32x2 dqd = fma2(dz, qz, fma2(dy, qy, mul2(dx, qx)));
+                    // c1 = -M/d^3 - 5/2 (d.Q.d)/d^7
+                    const f32x2 c1 = fma2(mul2(dqd, mul2(rinv2, KM25)), r5, mul2(v1.y, r3));
+                    fax = fma2(c1, dx, fma2(r5, qx, fax));
+                    fay = fma2(c1, dy, fma2(r5, qy, fay));
+                    faz = fma2(c1, dz, fma2(r5, qz, faz));
+                    fpot = fma2(v1.y, rinv, fma2(mul2(dqd, KM05), r5, fpot));
                 }
             }
+            acc.ax += lo2(fax) + hi2(fax);
+            acc.ay += lo2(fay) + hi2(fay);
+            acc.az += lo2(faz) + hi2(faz);
+            acc.pot += lo2(fpot) + hi2(fpot);
             fold();
             nfar = 0;
             __syncwarp();
@@ -203,73 +289,84 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
 
         auto flush_near = [&]() {
             __syncwarp();
+            // an odd list gets an empty partner entry (no lanes, finite zeros) for the two-wide pass
+            if ((nnear & 1) && lane == 0) {
+                sm.near_mask[w][nnear] = 0u;
+                float *f = sm.npair[w][nnear >> 1] + 1;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) f[2 * c] = 0.f;
+            }
             for (int l = lane; l < nnear; l += 32) {
                 const int j = sm.near_j[w][l];
-                {
-                    // interaction count (this lane's share): the entry's lanes, less the particle itself
-                    const unsigned msk = sm.near_mask[w][l];
-                    const int sl = j - g * 32;
-                    const unsigned self = (sl >= 0 && sl < 32) ? ((msk >> sl) & 1u) : 0u;
-                    wpp += __popc(msk) - self;
-                }
-                sm.np[w][l] = d.pos[j];
-                sm.ng[w][l] = d.grav[j];
+                wpp += __popc(sm.near_mask[w][l]);         // interaction count (this lane's share)
+                const float4 pj = d.pos[j];
+                const float4 gj = d.grav[j];
+                float *f = sm.npair[w][l >> 1] + (l & 1);
+                const float te = GRAV ? 2.f / gj.x : 0.f, th = 2.f * gj.z;
+                f[0] = pj.x; f[2] = pj.y; f[4] = pj.z; f[6] = pj.w;
+                f[8] = te * te;
+                f[10] = gj.z > 0.f ? th * th : -1.f;
+                sm.ng[w][l] = gj;
                 if (SPH) {
                     sm.nh[w][l] = d.hydro[j];
                     sm.ns[w][l] = d.snd[j];
                 }
                 if (CHECK) sm.norig[w][l] = d.orig[j];
             }
-            if (lane == 0) wnear_slots += 32u * (unsigned)((nnear + 1) & ~1);
+            if (lane == 0) wc[1] += 32u * (unsigned)((nnear + 1) & ~1);
             __syncwarp();
-            // Pass 1, every entry, two at a time and branch-free.  A gravity pair farther apart than
-            // 2 max(eps_i, eps_j) is Newtonian: both softened kernels equal their point-mass forms there
-            // (Eqs. softforce, softphi) and the correction term vanishes with dW/dr; it is summed here.
-            // Pairs inside that distance, and gas pairs inside 2 max(h_i, h_j), are marked per lane
-            // (bit t of sbits) and evaluated in pass 2, each lane taking its own marked pairs, so that
-            // the warp runs the softened and SPH terms about as often as its busiest lane has such pairs.
+            // Pass 1, every entry, two at a time in packed form.  A gravity pair farther apart than
+            // 2 max(eps_i, eps_j) is Newtonian: both softened kernels equal their point-mass forms
+            // there (Eqs. softforce, softphi) and the correction term vanishes with dW/dr; it is summed
+            // here (as +m/r^3 d and +m/r, subtracted at the end).  Pairs inside that distance, and gas
+            // pairs inside 2 max(h_i, h_j), are marked per lane (bit t of sbits) and evaluated in
+            // pass 2, each lane taking its own marked pairs, so that the warp runs the softened and
+            // SPH terms about as often as its busiest lane has such pairs.
             unsigned long long sbits = 0ull;
-            for (int t = 0; t < nnear; t += 2) {
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const bool ok = t + hh < nnear;
-                    const int tt = ok ? t + hh : t;
-                    const unsigned msk = ok ? sm.near_mask[w][tt] : 0u;
-                    const int j = sm.near_j[w][tt];
-                    const bool mine = ((msk >> lane) & 1u) && j != s;
-                    if (CHECK && mine) ++cpp;
-                    const float4 pj = sm.np[w][tt];
-                    const float4 gj = sm.ng[w][tt];
-                    const float dx = evol_wrap(pi.x - pj.x, plen0, pm & 1);
-                    const float dy = evol_wrap(pi.y - pj.y, plen1, pm & 2);
-                    const float dz = evol_wrap(pi.z - pj.z, plen2, pm & 4);
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    bool mark = false;
+            {
+                const f32x2 PX = pk2(pi.x, pi.x), PY = pk2(pi.y, pi.y), PZ = pk2(pi.z, pi.z);
+                f32x2 nax = 0ull, nay = 0ull, naz = 0ull, npot = 0ull;
+                for (int q = 0; q < (nnear + 1) >> 1; ++q) {
+                    const uint2 mk = *reinterpret_cast<const uint2 *>(&sm.near_mask[w][2 * q]);
+                    const ulonglong2 *F = reinterpret_cast<const ulonglong2 *>(sm.npair[w][q]);
+                    const ulonglong2 v0 = F[0], v1 = F[1], v2 = F[2];   // (x, y), (z, m), (E, H)
+                    f32x2 dx = sub2(PX, v0.x), dy = sub2(PY, v0.y), dz = sub2(PZ, v1.x);
+                    if (pm) {
+                        dx = pk2(evol_wrap(lo2(dx), plen0, pm & 1), evol_wrap(hi2(dx), plen0, pm & 1));
+                        dy = pk2(evol_wrap(lo2(dy), plen1, pm & 2), evol_wrap(hi2(dy), plen1, pm & 2));
+                        dz = pk2(evol_wrap(lo2(dz), plen2, pm & 4), evol_wrap(hi2(dz), plen2, pm & 4));
+                    }
+                    const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                    const float ra = lo2(r2), rb = hi2(r2);
+                    const bool mine_a = (mk.x >> lane) & 1u, mine_b = (mk.y >> lane) & 1u;
+                    if (CHECK) cpp += (mine_a ? 1 : 0) + (mine_b ? 1 : 0);
+                    bool mark_a = false, mark_b = false;
                     if (GRAV) {
-                        const float iem = fminf(ie_i, gj.x);               // 1 / max(eps_i, eps_j)
-                        const bool soft = r2 * (iem * iem) < 4.f;
-                        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                        const float mr = (mine && !soft) ? pj.w * rinv : 0.f;      // m_j / r
-                        const float mr3 = mr * (rinv * rinv);
-                        acc.ax = fmaf(-mr3, dx, acc.ax);
-                        acc.ay = fmaf(-mr3, dy, acc.ay);
-                        acc.az = fmaf(-mr3, dz, acc.az);
-                        acc.pot -= mr;
-                        mark = mine && soft;
-                        wsoft += mark ? 1u : 0u;
+                        const bool soft_a = ra < fmaxf(E_i, lo2(v2.x)), soft_b = rb < fmaxf(E_i, hi2(v2.x));
+                        const float ia = (mine_a && !soft_a) ? rsqrtf(ra) : 0.f;
+                        const float ib = (mine_b && !soft_b) ? rsqrtf(rb) : 0.f;
+                        const f32x2 rinv = pk2(ia, ib);
+                        const f32x2 mr = mul2(v1.y, rinv);                   // m_j / r
+                        const f32x2 mr3 = mul2(mr, mul2(rinv, rinv));
+                        nax = fma2(mr3, dx, nax);
+                        nay = fma2(mr3, dy, nay);
+                        naz = fma2(mr3, dz, naz);
+                        npot = add2(npot, mr);
+                        mark_a = mine_a && soft_a;
+                        mark_b = mine_b && soft_b;
                     }
-                    if (SPH && mine && gas_i && gj.z > 0.f) {
-                        const float two_h = fmaxf(two_h_i, 2.f * gj.z);
-                        if (r2 < two_h * two_h) {
-                            if (CHECK) {
-                                ++csph;
-                                hsph += evol_mix64((unsigned long long)sm.norig[w][tt]);
-                            }
-                            ++wsph;
-                            if (r2 > 0.f) mark = true;
-                        }
+                    if (SPH) {
+                        const float Ha = lo2(v2.y), Hb = hi2(v2.y);
+                        mark_a = mark_a || (mine_a && fminf(H_i, Ha) >= 0.f && ra < fmaxf(H_i, Ha));
+                        mark_b = mark_b || (mine_b && fminf(H_i, Hb) >= 0.f && rb < fmaxf(H_i, Hb));
                     }
-                    if (mark) sbits |= 1ull << tt;
+                    sbits |= ((unsigned long long)(mark_a ? 1u : 0u) | ((unsigned long long)(mark_b ? 1u : 0u) << 1)) << (2 * q);
+                }
+                if (GRAV) {
+                    acc.ax -= lo2(nax) + hi2(nax);
+                    acc.ay -= lo2(nay) + hi2(nay);
+                    acc.az -= lo2(naz) + hi2(naz);
+                    acc.pot -= lo2(npot) + hi2(npot);
                 }
             }
             // Pass 2: the marked pairs of each lane.  Every lane of the warp runs this loop; lanes past
@@ -280,47 +377,49 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
                 const float4 hi = (SPH && valid) ? d.hydro[s] : z4;
                 const float4 si = (SPH && valid) ? d.snd[s] : z4;
                 while (__any_sync(0xffffffffu, sbits != 0ull)) {
-                    if (lane == 0) wpass2_slots += 32u;
+                    if (lane == 0) wc[2] += 32u;
                     if (sbits) {
                         const int t = __ffsll((long long)sbits) - 1;
                         sbits &= sbits - 1ull;
-                        const float4 pj = sm.np[w][t];
-                        const float4 gj = sm.ng[w][t];
-                        const float dx = evol_wrap(pi.x - pj.x, plen0, pm & 1);
-                        const float dy = evol_wrap(pi.y - pj.y, plen1, pm & 2);
-                        const float dz = evol_wrap(pi.z - pj.z, plen2, pm & 4);
-                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const float *f = sm.npair[w][t >> 1] + (t & 1);
+                        const float mj = f[6], Ej = f[8], Hj = f[10];
+                        const float dx = evol_wrap(pi.x - f[0], plen0, pm & 1);
+                        const float dy = evol_wrap(pi.y - f[2], plen1, pm & 2);
+                        const float dz = evol_wrap(pi.z - f[4], plen2, pm & 4);
+                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));     // as in pass 1
                         // r and 1/r from one reciprocal square root (coincident particles: both 0)
                         const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
                         const float r = r2 * rinv;
-                        if (GRAV) {
-                            const float iem = fminf(ie_i, gj.x);
-                            if (r2 * (iem * iem) < 4.f) {          // the same test as pass 1
-                                // symmetrised softened pair force and potential (App. B), each side
-                                // softened where u < 2 and Newtonian beyond
-                                const float mj = pj.w;
-                                const float ui = r * ie_i, uj = r * gj.x;
-                                const float iui = rinv * eps_i, iuj = rinv * rcp_fast(gj.x);
-                                const float rinv3 = rinv * rinv * rinv;
-                                const float fi = ui < 2.f ? gsoft_over_r_u(ui, iui) * ie_i * ie_i * ie_i : rinv3;
-                                const float fj = uj < 2.f ? gsoft_over_r_u(uj, iuj) * gj.x * gj.x * gj.x : rinv3;
-                                float f = -0.5f * mj * (fi + fj);
-                                acc.pot += mj * (ui < 2.f ? phisoft_u(ui, iui) * ie_i : -rinv);
-                                if (kp.adaptive) {
-                                    // adaptive-softening correction (Eq. dLgravdr, mass-weighted reading)
-                                    const float ie2 = ie_i * ie_i, je2 = gj.x * gj.x;
-                                    const float ci = ui < 2.f ? xu_i * dw_over_u_u(ui, iui) * ie2 * ie2 * ie_i : 0.f;
-                                    const float cj = uj < 2.f ? gj.y * dw_over_u_u(uj, iuj) * je2 * je2 * gj.x : 0.f;
-                                    f += -0.5f * inv_pi * (ci + mj * inv_mi * cj);
-                                }
-                                acc.ax += f * dx;
-                                acc.ay += f * dy;
-                                acc.az += f * dz;
+                        const float4 gj = sm.ng[w][t];
+                        if (GRAV && r2 < fmaxf(E_i, Ej)) {              // the same test as pass 1
+                            ++wsoft;
+                            // symmetrised softened pair force and potential (App. B), each side
+                            // softened where u < 2 and Newtonian beyond
+                            const float ui = r * ie_i, uj = r * gj.x;
+                            const float iui = rinv * eps_i, iuj = rinv * rcp_fast(gj.x);
+                            const float rinv3 = rinv * rinv * rinv;
+                            const float fi = ui < 2.f ? gsoft_over_r_u(ui, iui) * ie_i * ie_i * ie_i : rinv3;
+                            const float fj = uj < 2.f ? gsoft_over_r_u(uj, iuj) * gj.x * gj.x * gj.x : rinv3;
+                            float fg = -0.5f * mj * (fi + fj);
+                            acc.pot += mj * (ui < 2.f ? phisoft_u(ui, iui) * ie_i : -rinv);
+                            if (kp.adaptive) {
+                                // adaptive-softening correction (Eq. dLgravdr, mass-weighted reading)
+                                const float ie2 = ie_i * ie_i, je2 = gj.x * gj.x;
+                                const float ci = ui < 2.f ? xu_i * dw_over_u_u(ui, iui) * ie2 * ie2 * ie_i : 0.f;
+                                const float cj = uj < 2.f ? gj.y * dw_over_u_u(uj, iuj) * je2 * je2 * gj.x : 0.f;
+                                fg += -0.5f * inv_pi * (ci + mj * inv_mi * cj);
                             }
+                            acc.ax += fg * dx;
+                            acc.ay += fg * dy;
+                            acc.az += fg * dz;
                         }
-                        if (SPH && gas_i && gj.z > 0.f && r2 > 0.f) {
-                            const float two_h = fmaxf(two_h_i, 2.f * gj.z);
-                            if (r2 < two_h * two_h) {                // the same test as pass 1
+                        if (SPH && fminf(H_i, Hj) >= 0.f && r2 < fmaxf(H_i, Hj)) {   // as in pass 1
+                            ++wsph;
+                            if (CHECK) {
+                                ++csph;
+                                hsph += evol_mix64((unsigned long long)sm.norig[w][t]);
+                            }
+                            if (r2 > 0.f) {
                                 const float4 hj = sm.nh[w][t];
                                 const float4 sj = sm.ns[w][t];
                                 const float ihi = si.z, ihj = sj.z;
@@ -329,7 +428,7 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
                                 const float ihi2 = ihi * ihi, ihj2 = ihj * ihj;
                                 const float kgi = (kp.use_tc ? tc_over_u_u(uhi, iuhi) : dw_over_u_u(uhi, iuhi)) * ihi2 * ihi2 * ihi * inv_pi;
                                 const float kgj = (kp.use_tc ? tc_over_u_u(uhj, iuhj) : dw_over_u_u(uhj, iuhj)) * ihj2 * ihj2 * ihj * inv_pi;
-                                const float fi = 1.f + gi.w * rcp_fast(pj.w);     // 1 + zeta_i / (m_j Omega*_i)
+                                const float fi = 1.f + gi.w * rcp_fast(mj);       // 1 + zeta_i / (m_j Omega*_i)
                                 const float fj = 1.f + gj.w * inv_mi;             // 1 + zeta_j / (m_i Omega*_j)
                                 const float vx = hi.x - hj.x, vy = hi.y - hj.y, vz = hi.z - hj.z;
                                 const float vr = vx * dx + vy * dy + vz * dz;
@@ -343,11 +442,11 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
                                 }
                                 const float gbar = 0.5f * (kgi * fi + kgj * fj);
                                 const float pterm_i = hi.w * fi * kgi;
-                                const float sc = -pj.w * (pterm_i + hj.w * fj * kgj + visc * gbar);
+                                const float sc = -mj * (pterm_i + hj.w * fj * kgj + visc * gbar);
                                 acc.hx += sc * dx;
                                 acc.hy += sc * dy;
                                 acc.hz += sc * dz;
-                                acc.du += pj.w * (pterm_i + 0.5f * visc * gbar) * vr;
+                                acc.du += mj * (pterm_i + 0.5f * visc * gbar) * vr;
                             }
                         }
                     }
@@ -474,6 +573,10 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
             __syncwarp();
             // mixed nodes: every lane in the mask applies its own test
             unsigned mm = __ballot_sync(0xffffffffu, cls == 3);
+            if (lane == 0) {
+                wc[3] += (unsigned)k;
+                wc[4] += (unsigned)__popc(mm);
+            }
             while (mm) {
                 const int kk = __ffs(mm) - 1;
                 mm &= mm - 1u;
@@ -519,7 +622,7 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
             }
             if (GRAV && fa) {
                 const int cnt = __popc(fa);
-                if (nfar + cnt > FARCAP - 3) flush_far();
+                if (nfar + cnt > FARCAP - 2 * EVOL_FAR_UNROLL + 1) flush_far();
                 if (Ak) {
                     const int pos = nfar + __popc(fa & ltmask);
                     sm.far_id[w][pos] = node;
@@ -530,6 +633,13 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
             // opened leaves: their particles go to the near list
             const bool isleaf = (I.x >> 8) & 1;
             unsigned lm = __ballot_sync(0xffffffffu, Ok != 0u && isleaf);
+            {
+                const unsigned im = __ballot_sync(0xffffffffu, Ok != 0u && !isleaf);
+                if (lane == 0) {
+                    wc[5] += (unsigned)__popc(lm);
+                    wc[6] += (unsigned)__popc(im);
+                }
+            }
             while (lm) {
                 const int kk = __ffs(lm) - 1;
                 lm &= lm - 1u;
@@ -544,8 +654,10 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
                     const int kc = min(32, e0 - b);
                     if (nnear + kc > NEARCAP) flush_near();
                     if (lane < kc) {
-                        sm.near_j[w][nnear + lane] = b + lane;
-                        sm.near_mask[w][nnear + lane] = ok;
+                        // the particle itself never pairs with itself: its lane leaves the entry's mask
+                        const int j = b + lane, sl = j - g * 32;
+                        sm.near_j[w][nnear + lane] = j;
+                        sm.near_mask[w][nnear + lane] = ok & ~((sl >= 0 && sl < 32) ? (1u << sl) : 0u);
                     }
                     nnear += kc;
                 }
@@ -630,9 +742,7 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
             atomicAdd(&d.counters[1], wp);
             atomicAdd(&d.counters[2], ws);
             atomicAdd(&d.counters[8], wo);
-            atomicAdd(&d.counters[9], (unsigned long long)wfar_slots);
-            atomicAdd(&d.counters[10], (unsigned long long)wnear_slots);
-            atomicAdd(&d.counters[11], (unsigned long long)wpass2_slots);
+            for (int q = 0; q < 7; ++q) atomicAdd(&d.counters[9 + q], (unsigned long long)wc[q]);
         }
     }
 }

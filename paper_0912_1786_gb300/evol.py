@@ -77,7 +77,7 @@ def lib():
         L.evol_set_check_mode.argtypes = [vp, C.c_int]
         L.evol_set_stack_limit.argtypes = [vp, C.c_int64]
         L.evol_sort_keys_noalloc.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, vp]
-        L.evol_fp32_peak.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_float)]
+        L.evol_fp32_peak.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_float)]
         L.evol_strerror.argtypes = [C.c_int]
         L.evol_strerror.restype = C.c_char_p
         _lib = L
@@ -236,10 +236,11 @@ def evol_set_check_mode(ctx, on: bool):
 
 
 def evol_fp32_peak(iters: int = 20000):
-    """Measured FP32 throughput of the current device: (TFLOP/s, kernel ms)."""
-    t, ms = C.c_double(), C.c_float()
-    _check(lib().evol_fp32_peak(int(iters), C.byref(t), C.byref(ms)), "evol_fp32_peak")
-    return t.value, ms.value
+    """Measured FP32 throughput of the current device: (scalar TFLOP/s, packed two-wide TFLOP/s,
+    scalar kernel ms)."""
+    t, t2, ms = C.c_double(), C.c_double(), C.c_float()
+    _check(lib().evol_fp32_peak(int(iters), C.byref(t), C.byref(t2), C.byref(ms)), "evol_fp32_peak")
+    return t.value, t2.value, ms.value
 
 
 def evol_set_stack_limit(ctx, entries: int):
