@@ -178,7 +178,7 @@ int evol_sync(evol_ctx *ctx);
  * [15] length-solve iterations (sum over particles). */
 int evol_get_diagnostics(evol_ctx *ctx, double out[16]);
 
-/* Work counters of the last step (valid after evol_sync), 16 values:
+/* Work counters of the last step (valid after evol_sync), 32 values:
  *   [0] far-node interactions   [1] particle pairs (all)   [2] SPH pairs
  *   [3] length-solve iterations (sum over particles)
  *   [4] [5] [6] work-queue positions of the walk, the h solve and the eps solve
@@ -187,8 +187,13 @@ int evol_get_diagnostics(evol_ctx *ctx, double out[16]);
  *   [9] lane slots of the far-node loop, [10] of the pair loop's first pass, [11] of its second
  *       pass (32 per entry or trip: interactions / slots is the fraction of busy lanes)
  *   [12] nodes popped by the force walk's groups, [13] of them tested lane by lane (neither
- *        accepted nor opened for the whole group), [14] leaves opened, [15] internal nodes opened */
-int evol_get_counters(evol_ctx *ctx, uint64_t out[16]);
+ *        accepted nor opened for the whole group), [14] leaves opened, [15] internal nodes opened
+ *   length solves, eps at [16..19] and h at [20..23]: [+0] neighbour gathers from a group's leaf
+ *        list, [+1] gathers by a particle's own tree walk, [+2] neighbour lists that overflowed,
+ *        [+3] group leaf lists that overflowed
+ *   [24] eps-solve and [25] h-solve Newton iterations (sum over particles)
+ *   [26..31] zero */
+int evol_get_counters(evol_ctx *ctx, uint64_t out[32]);
 
 /* Debug copies of internal state (valid after evol_sync), into host memory of cap bytes.
  * Returns the number of ELEMENTS available (whatever cap), or a negative status.

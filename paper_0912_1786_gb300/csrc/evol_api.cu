@@ -621,13 +621,13 @@ int evol_get_diagnostics(evol_ctx *c, double out[16])
                                                                                                  : EVOL_ECUDA;
 }
 
-int evol_get_counters(evol_ctx *c, uint64_t out[16])
+int evol_get_counters(evol_ctx *c, uint64_t out[32])
 {
     if (!c || !out) return EVOL_EINVAL;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return EVOL_ECUDA;
     unsigned long long v[EVOL_NCOUNTERS];
     if (cudaMemcpy(v, c->d.counters, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return EVOL_ECUDA;
-    for (int k = 0; k < 16; ++k) out[k] = k < EVOL_NCOUNTERS ? (uint64_t)v[k] : 0;
+    for (int k = 0; k < 32; ++k) out[k] = k < EVOL_NCOUNTERS ? (uint64_t)v[k] : 0;
     return EVOL_OK;
 }
 

@@ -9,7 +9,7 @@
 
 #define EVOL_MAXLEVEL 21          // 21 bits per axis, 63-bit Morton keys
 #define EVOL_WARP 32
-#define EVOL_NCOUNTERS 16
+#define EVOL_NCOUNTERS 32
 #define EVOL_PI_F 3.14159265358979f
 
 // ---- device error word: first error wins ------------------------------------------------

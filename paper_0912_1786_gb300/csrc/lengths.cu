@@ -48,6 +48,7 @@ struct LenSmem {
     int hb[LW_WARPS][HCAP + 1];       // listed leaves: exclusive prefix of their particle counts
     int hs[LW_WARPS][HCAP];           // and the first particle of each
     float2 nb[LW_WARPS][PCAP];        // (distance, mass) of the neighbours of the particle solved
+    unsigned lc[LW_WARPS][4];         // work counts of the warp's current item (kept by lane 0)
 };
 
 // Particles of the listed leaves against the particle at (px, py, pz), 32 at a time across
@@ -62,22 +63,28 @@ __device__ __forceinline__ int gather_listed(const evol_dev &d, const evol_kpara
     const float p0 = kp.plen[0], p1 = kp.plen[1], p2 = kp.plen[2];
     const int pm = kp.periodic_mask;
     const int total = hb[nh];
-    constexpr int U = 2;              // chunks whose loads are issued together (more costs occupancy)
+    constexpr int U = 1;              // chunks whose loads are issued together (more costs occupancy)
+    // the listed leaf holding the chunk's first flattened index; leaves are never empty, so the
+    // leaves starting inside a 32-index chunk are among the next 32, and each start offset is
+    // distinct: one bit per offset (a warp OR) gives every lane its leaf by a population count
+    int k0 = 0;
     for (int c0 = 0; c0 < total; c0 += 32 * U) {
         int jj[U];
 #pragma unroll
         for (int h = 0; h < U; ++h) {
-            const int x = c0 + 32 * h + lane;
+            const int x0 = c0 + 32 * h;
+            const int kb = k0 + 1 + lane;
+            const int p = kb < nh ? hb[kb] - x0 : 32;
+            const unsigned starts = __reduce_or_sync(0xffffffffu, (p > 0 && p < 32) ? (1u << p) : 0u);
+            const int x = x0 + lane;
             jj[h] = -1;
             if (x < total) {
-                // the listed leaf holding flattened index x: last k with hb[k] <= x
-                int lo = 0, hi = nh - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (hb[mid] <= x) lo = mid; else hi = mid - 1;
-                }
-                jj[h] = hs[lo] + (x - hb[lo]);
+                const int k = k0 + __popc(starts & ((2u << lane) - 1u));
+                jj[h] = hs[k] + (x - hb[k]);
             }
+            // the leaf holding x0 + 32
+            k0 += __popc(starts);
+            if (k0 + 1 < nh && hb[k0 + 1] == x0 + 32) ++k0;
         }
         float4 pj[U];
         bool gas[U];
@@ -407,6 +414,11 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
             if (!(L0 > 0.f) || !(L0 < 1e30f)) L0 = side / cbrtf((float)n);
         }
         int iters_total = 0;
+        // gathers from the group list [0], by the particle's own walk [1], list overflows [2],
+        // group-list overflows [3]
+        unsigned *lc = sm.lc[w];
+        if (lane < 4) lc[lane] = 0u;
+        __syncwarp();
         bool broken = false;
 
         do {                                           // one group walk for the SUB particles
@@ -435,6 +447,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
               break;
           }
           const bool glist = nleaf <= GCAP;
+          if (lane == 0 && !glist) ++lc[3];
           unsigned todo = subm;
           while (todo && !broken) {
             const int t = __ffs(todo) - 1;
@@ -485,12 +498,15 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                     const float R2 = Rc * Rc;
                     cnt = 0;
                     __syncwarp();
-                    if (glist && Rc <= Rg)
+                    if (glist && Rc <= Rg) {
+                        if (lane == 0) ++lc[0];
                         cnt = gather_from_list<MODE>(d, kp, sm.gc[w], sm.gh[w], sm.gr[w], nleaf, sm.hb[w], sm.hs[w], nb,
                                                      lane, px, py, pz, R2, sb, se);
-                    else
+                    } else {
+                        if (lane == 0) ++lc[1];
                         cnt = gather_ball<MODE>(d, kp, sm.hb[w], sm.hs[w], nb, lane, stk, stack_cap, pop_cap, rt, px,
                                                 py, pz, R2);
+                    }
                     if (cnt < 0) {
                         broken = true;
                         break;
@@ -499,6 +515,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                     stale = false;
                     if (cnt > PCAP) {
                         // more neighbours than the list holds: the radius is too large; shrink, gather again
+                        if (lane == 0) ++lc[2];
                         Rlim = fminf(Rlim, Rc);
                         hi = fminf(hi, 0.5f * Rlim * (1.f - 1e-6f));
                         float Ln = 0.75f * L;
@@ -513,34 +530,53 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                     }
                 }
                 // sums over the list: lane l takes entries l, l + 32, ...
-                float Sw = 0.f, Suw = 0.f, Smw = 0.f, Smuw = 0.f;
+                // Sums over the list (lane l takes entries l, l + 32, ...), combined across the warp.
+                // A Newton iteration needs Sw and Suw; the last evaluation also needs the
+                // mass-weighted sums of the outputs.
+                const bool last = status == ST_LAST;
+                float Sw = 0.f, Suw = 0.f, S3 = 0.f, S4 = 0.f;
                 const float Linv = 1.f / L;
-                for (int e = lane; e < cnt; e += 32) {
-                    const float2 rm = nb[e];
-                    const float u = rm.x * Linv;
-                    float wv, dw;
-                    evol_w_dw(u, wv, dw);      // zero for u >= 2
-                    Sw += wv;
-                    Suw += u * dw;
-                    if (MODE == 0) {
-                        Smw += rm.y * wv;
-                        Smuw += rm.y * u * dw;
-                    } else {
-                        Smw += rm.y * evol_dphideps(u);
+                if (!last) {
+                    for (int e = lane; e < cnt; e += 32) {
+                        const float u = nb[e].x * Linv;
+                        const float aa = fmaxf(2.f - u, 0.f), bb = fmaxf(1.f - u, 0.f);
+                        const float a2 = aa * aa, b2 = bb * bb;
+                        Sw += 0.25f * a2 * aa - b2 * bb;                    // w(u)
+                        Suw += u * (-0.75f * a2 + 3.f * b2);                // u w'(u)
+                    }
+                } else {
+                    for (int e = lane; e < cnt; e += 32) {
+                        const float2 rm = nb[e];
+                        const float u = rm.x * Linv;
+                        float wv, dw;
+                        evol_w_dw(u, wv, dw);      // zero for u >= 2
+                        Sw += wv;
+                        Suw += u * dw;
+                        if (MODE == 0) {
+                            S3 += rm.y * wv;                               // Smw
+                            S4 += rm.y * u * dw;                           // Smuw
+                        } else {
+                            S3 += rm.y * evol_dphideps(u);                 // sum m eps^2 dphi/deps
+                        }
                     }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     Sw += __shfl_xor_sync(0xffffffffu, Sw, o);
                     Suw += __shfl_xor_sync(0xffffffffu, Suw, o);
-                    Smw += __shfl_xor_sync(0xffffffffu, Smw, o);
-                    if (MODE == 0) Smuw += __shfl_xor_sync(0xffffffffu, Smuw, o);
+                    if (last) {
+                        S3 += __shfl_xor_sync(0xffffffffu, S3, o);
+                        if (MODE == 0) S4 += __shfl_xor_sync(0xffffffffu, S4, o);
+                    }
                 }
-                // identical on every lane already; broadcast lane 0's values to make it explicit
+                // identical on every lane up to the order of the additions; take lane 0's values
                 Sw = __shfl_sync(0xffffffffu, Sw, 0);
                 Suw = __shfl_sync(0xffffffffu, Suw, 0);
-                Smw = __shfl_sync(0xffffffffu, Smw, 0);
-                if (MODE == 0) Smuw = __shfl_sync(0xffffffffu, Smuw, 0);
+                if (last) {
+                    S3 = __shfl_sync(0xffffffffu, S3, 0);
+                    if (MODE == 0) S4 = __shfl_sync(0xffffffffu, S4, 0);
+                }
+                const float Smw = S3, Smuw = S4;
                 if (status == ST_LAST) {
                     if (lane == t) {
                         const int si = g * SUB + t;
@@ -562,13 +598,14 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                 } else {
                     ++iters;
                     const float F = Sw * inv_pi - eta3;
-                    const float Fp = -Suw * inv_pi * Linv;
                     if (F < 0.f) lo = L;
                     if (F > 0.f) hi = L;
                     float Ln;
                     if (F == 0.f) {
                         Ln = L;
                     } else {
+                        // Newton step, F' = -Suw/(pi L); bisection where it leaves the bracket
+                        const float Fp = -Suw * inv_pi * Linv;
                         Ln = Fp > 0.f ? L - F / Fp : (hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L);
                         if (!(Ln > lo && Ln < hi)) Ln = hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L;
                     }
@@ -589,7 +626,12 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
             iters_total += iters;
           }
         } while (0);
-        if (lane == 0) atomicAdd(&d.counters[3], (unsigned long long)iters_total);
+        if (lane == 0) {
+            atomicAdd(&d.counters[3], (unsigned long long)iters_total);
+            unsigned long long *c4 = d.counters + (MODE == 1 ? 16 : 20);
+            for (int q = 0; q < 4; ++q) atomicAdd(c4 + q, (unsigned long long)lc[q]);
+            atomicAdd(&d.counters[MODE == 1 ? 24 : 25], (unsigned long long)iters_total);
+        }
         if (broken) break;
     }
 }

@@ -226,7 +226,7 @@ def evol_get_timings(ctx):
 
 
 def evol_get_counters(ctx):
-    out = (C.c_uint64 * 16)()
+    out = (C.c_uint64 * 32)()
     _check(lib().evol_get_counters(ctx, out), "evol_get_counters")
     return list(out)
 
