@@ -607,6 +607,10 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         // Newton step, F' = -Suw/(pi L); bisection where it leaves the bracket
                         const float Fp = -Suw * inv_pi * Linv;
                         Ln = Fp > 0.f ? L - F / Fp : (hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L);
+                        // below the root with no upper bracket yet, F' counts only the few neighbours
+                        // inside the kernel and the step can overshoot by orders of magnitude: grow by
+                        // at most a factor 2 until the root is bracketed
+                        if (hi == INFINITY) Ln = fminf(Ln, 2.f * L);
                         if (!(Ln > lo && Ln < hi)) Ln = hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L;
                     }
                     const bool conv = fabsf(Ln - L) <= CONV_TOL * L || (hi < INFINITY && hi - lo <= 1e-7f * hi);

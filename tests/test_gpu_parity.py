@@ -306,3 +306,13 @@ def test_walk_stack_overflow_reports_eoverflow():
         assert E.evol_sync(ctx, raise_on_error=False) == 0
     finally:
         E.evol_destroy(ctx)
+
+
+@pytest.mark.parametrize("scale", [0.5, 2.0])
+def test_length_solve_from_poor_guesses(scale):
+    # the solution does not depend on the starting guesses (unique root): guesses off by a factor
+    # of two either way converge to the same lengths and forces
+    w = W.evrard_sphere(4096, seed=18, sigma_v=0.1)
+    w.h[:] = (w.h * scale).astype(np.float32)
+    w.eps[:] = (w.eps * scale).astype(np.float32)
+    _compare(w)
