@@ -74,10 +74,14 @@ def make_workload(name: str):
     if name == "c2":
         return W.plummer(1 << 20, seed=2, params=W.Params(theta=0.6, sph=0, n_nei_grav=32.0, leaf_size=8)), \
             "plummer_2^20_theta0.6_gravity_only"
+    # the mixed-species workloads default to leaf 24, the size the autotuner picks for them on GB300
+    # (the FP64 oracle of the reference arm uses the same value)
     if name == "c3":
-        return W.hernquist_gas(n_dm=1 << 21, n_gas=1 << 20, seed=3), "hernquist_2^21_dm+2^20_gas"
+        return W.hernquist_gas(n_dm=1 << 21, n_gas=1 << 20, seed=3, params=W.Params(leaf_size=24)), \
+            "hernquist_2^21_dm+2^20_gas"
     if name == "c3s":      # one eighth of c3, for profiler captures
-        return W.hernquist_gas(n_dm=1 << 18, n_gas=1 << 17, seed=3), "hernquist_2^18_dm+2^17_gas"
+        return W.hernquist_gas(n_dm=1 << 18, n_gas=1 << 17, seed=3, params=W.Params(leaf_size=24)), \
+            "hernquist_2^18_dm+2^17_gas"
     if name == "c4":
         return W.shock_tube(seed=4), "shock_tube_1046250_periodic_yz"
     if name == "c5":
@@ -154,22 +158,47 @@ def gpu_uuid(torch, dev):
         return None
 
 
-def oracle_sample(w, budget_s=25.0, seed=7):
+def oracle_state(w, leaf):
+    """The FP64 oracle's tree and lengths of every particle for workload w (eps of all particles,
+    h, rho, Omega*, zeta, P, c of the gas), as the force pass needs them."""
+    import oracle
+    p = w.params
+    lib = oracle.lib()
+    tree = oracle.OracleTree(w.x, w.y, w.z, w.m, w.n_gas, leaf)
+    n, ng = w.n, w.n_gas
+    st = {}
+    if p.gravity and p.adaptive_softening:
+        eps, _, ups, X, _ = tree.solve_lengths(1, p.n_nei_grav, guess=w.eps, params=p)
+        st.update(eps=eps, ups=ups, X=X)
+    elif p.gravity:
+        st.update(eps=w.eps.astype(np.float64), ups=np.ones(n), X=np.zeros(n))
+    if p.sph and ng:
+        h, _, rho, om, zeta = tree.solve_lengths(0, p.n_nei_sph, guess=w.h, idx=np.arange(ng), params=p)
+        P, c = np.zeros(n), np.zeros(n)
+        lib.orc_eos(n, float(p.gamma), np.ascontiguousarray(rho), np.ascontiguousarray(w.u, np.float64), P, c)
+        P[ng:] = 0
+        c[ng:] = 0
+        st.update(h=h, rho=rho, omega=om, zeta=zeta, P=P, c=c)
+    st.update(vx=w.vx.astype(np.float64), vy=w.vy.astype(np.float64), vz=w.vz.astype(np.float64))
+    return tree, st
+
+
+def oracle_sample(w, budget_s=25.0, seed=7, leaf=None, state=None):
     """Bounded timing of the FP64 oracle on workload w: a full tree build, the eps and h solves
     on seeded samples of particles and the force walk on a seeded sample, each scaled to its
     per-particle rate.  Returns (particles/s, cores, description)."""
     import oracle
-    from paper_0912_1786_gb300 import workloads as W
     p = w.params
+    leaf = leaf or p.leaf_size
     lib = oracle.lib()
     cores = int(lib.orc_num_threads())
     t0 = time.perf_counter()
-    tree = oracle.OracleTree(w.x, w.y, w.z, w.m, w.n_gas, p.leaf_size)
+    tree = oracle.OracleTree(w.x, w.y, w.z, w.m, w.n_gas, leaf)
     t_build = time.perf_counter() - t0
     n, ng = w.n, w.n_gas
     rng = np.random.default_rng(seed)
     per = 0.0
-    desc = [f"tree build of all {n} particles {t_build:.2f}s"]
+    desc = [f"leaf {leaf}: tree build of all {n} particles {t_build:.2f}s"]
     s_e = min(n, 60000)
     s_h = min(ng, 30000)
     if p.gravity and p.adaptive_softening:
@@ -187,21 +216,8 @@ def oracle_sample(w, budget_s=25.0, seed=7):
         per += th / s_h * ng
         desc.append(f"h solve {s_h} sampled ({th:.2f}s)")
     # neighbour lengths for the force sample come from the oracle's own solve of every particle
-    # (setup, not timed)
-    st = {}
-    if p.gravity and p.adaptive_softening:
-        eps, _, ups, X, _ = tree.solve_lengths(1, p.n_nei_grav, guess=w.eps, params=p)
-        st.update(eps=eps, ups=ups, X=X)
-    elif p.gravity:
-        st.update(eps=w.eps.astype(np.float64), ups=np.ones(n), X=np.zeros(n))
-    if p.sph and ng:
-        h, _, rho, om, zeta = tree.solve_lengths(0, p.n_nei_sph, guess=w.h, idx=np.arange(ng), params=p)
-        P, c = np.zeros(n), np.zeros(n)
-        lib.orc_eos(n, float(p.gamma), np.ascontiguousarray(rho), np.ascontiguousarray(w.u, np.float64), P, c)
-        P[ng:] = 0
-        c[ng:] = 0
-        st.update(h=h, rho=rho, omega=om, zeta=zeta, P=P, c=c)
-    st.update(vx=w.vx.astype(np.float64), vy=w.vy.astype(np.float64), vz=w.vz.astype(np.float64))
+    # (set-up, not timed)
+    st = (state or oracle_state(w, leaf))[1]
     s_f = min(n, 2000)
     idx = np.sort(rng.choice(n, s_f, replace=False))
     t0 = time.perf_counter()
@@ -219,6 +235,69 @@ def oracle_sample(w, budget_s=25.0, seed=7):
     desc.append(f"force walk {s_f} sampled ({tf:.2f}s)")
     total = t_build + per
     return n / total, cores, "; ".join(desc) + f"; scaled to {n} particles: {total:.1f}s per step"
+
+
+# Tolerances the force step is held to against the FP64 oracle (median / 99th percentile of the
+# relative error), and the explanation margin of an interaction-set mismatch (relative to the
+# threshold plus the particle's coordinate scale).
+TOL_MEDIAN, TOL_P99, EXPLAIN_MARGIN, CANCEL_FLOOR = 1e-5, 1e-4, 1e-6, 1e-2
+
+
+def _rel(got, ref, scale=None):
+    """Plain relative error statistics; with `scale`, results below CANCEL_FLOOR of their terms'
+    magnitude sum are counted apart and judged by |d| / scale."""
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    d = np.linalg.norm(got - ref, axis=1) if got.ndim == 2 else np.abs(got - ref)
+    r = np.linalg.norm(ref, axis=1) if ref.ndim == 2 else np.abs(ref)
+    fl = np.zeros(len(d), bool) if scale is None else r < CANCEL_FLOOR * np.asarray(scale)
+    e = d[~fl] / np.maximum(r[~fl], 1e-300)
+    out = {"median": float(np.median(e)) if e.size else 0.0, "p99": float(np.percentile(e, 99)) if e.size else 0.0,
+           "n": int(len(d))}
+    if fl.any():
+        fe = d[fl] / np.asarray(scale)[fl]
+        out.update(n_floor=int(fl.sum()), floor_p99=float(np.percentile(fe, 99)))
+    return out
+
+
+def form_errors(g, ref, idx, w):
+    """Errors of one GPU form (g: caller-order arrays incl. 'hashes') against the oracle on the
+    sampled particles idx (ref: the oracle's results)."""
+    gi = idx[idx < w.n_gas]
+    A = lambda x: np.stack([x["ax"], x["ay"], x["az"]], 1)
+    e = {"acc": _rel(A(g)[idx], A(ref)[idx], ref["aabs"][idx])}
+    if w.params.gravity:
+        e["pot"] = _rel(g["pot"][idx], ref["pot"][idx])
+        if w.params.adaptive_softening:
+            e["eps"] = _rel(g["eps"][idx], ref["eps"][idx])
+    if w.params.sph and len(gi):
+        e["h"] = _rel(g["h"][gi], ref["h"][gi])
+        e["rho"] = _rel(g["rho"][gi], ref["rho"][gi])
+        if np.any(w.vx != 0):
+            e["dudt"] = _rel(g["dudt"][gi], ref["dudt"][gi], ref["duabs"][gi])
+    if "hashes" in g:
+        oh = np.stack([ref["hfar"], ref["hnear"], ref["hsph"]], 1)[idx]
+        bad = np.any(g["hashes"][idx] != oh, axis=1)
+        mg = ref["margin"][idx][bad]
+        e["set_mismatches"] = int(bad.sum())
+        e["set_mismatches_explained"] = int((mg < EXPLAIN_MARGIN).sum())
+    ok = all(v["median"] <= TOL_MEDIAN and v["p99"] <= TOL_P99 for k, v in e.items() if isinstance(v, dict))
+    e["within_tolerance"] = bool(ok and e.get("set_mismatches", 0) == e.get("set_mismatches_explained", 0))
+    return e
+
+
+def gpu_check_step(E, ctx, ds, offsets=None):
+    """One more step with interaction-set hashes recorded; caller-order numpy results."""
+    E.evol_set_check_mode(ctx, True)
+    ds.reset_lengths()
+    if offsets is None:
+        E.evol_step(ctx, ds.particles, ds.params, ds.outputs)
+    else:
+        E.evol_step_batched(ctx, offsets, ds.particles, ds.params, ds.outputs)
+    E.evol_sync(ctx)
+    g = ds.numpy()
+    g["hashes"] = E.evol_get_debug(ctx, E.EVOL_DBG_HASHES, np.uint64).reshape(-1, 3)
+    E.evol_set_check_mode(ctx, False)
+    return g
 
 
 def run_reference(args):
@@ -239,7 +318,7 @@ def run_reference(args):
             "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wname, "n": w.n, "n_gas": w.n_gas, "theta": w.params.theta,
-                       "n_nei": w.params.n_nei_sph},
+                       "n_nei": w.params.n_nei_sph, "leaf_size": int(w.params.leaf_size)},
             "cpu_baseline": {"value": v, "unit": "particles/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "vs_baseline": None}
@@ -262,8 +341,9 @@ def time_steps(torch, dev, stream, fn, steps):
 
 def other_forms(torch, dev, stream, E, DeviceSet, w, steps, precision_used, leaf):
     """Throughput of the other precision form (same workload) and, for an ensemble, of one
-    launch per system; particles/s each."""
-    forms = {}
+    launch per system; particles/s each.  Also returns each form's results (caller order, with
+    interaction-set hashes for the precision form) for the accuracy comparison."""
+    forms, results = {}, {}
     other = E.EVOL_FP32_MIXED if precision_used == E.EVOL_FP32_PLAIN else E.EVOL_FP32_PLAIN
     ds = DeviceSet(w, device=str(dev), precision=other)
     ds.params.leaf_size = leaf
@@ -279,7 +359,9 @@ def other_forms(torch, dev, stream, E, DeviceSet, w, steps, precision_used, leaf
         E.evol_sync(ctx)
         ms = time_steps(torch, dev, stream, run, steps)
         E.evol_sync(ctx)
-        forms["mixed" if other == E.EVOL_FP32_MIXED else "plain"] = w.n * steps / (ms / 1e3)
+        name = "mixed" if other == E.EVOL_FP32_MIXED else "plain"
+        forms[name] = w.n * steps / (ms / 1e3)
+        results[name] = gpu_check_step(E, ctx, ds, [int(v) for v in w.sys_offsets] if w.sys_offsets is not None else None)
     finally:
         E.evol_destroy(ctx)
     if w.sys_offsets is not None:
@@ -304,10 +386,14 @@ def other_forms(torch, dev, stream, E, DeviceSet, w, steps, precision_used, leaf
             torch.cuda.synchronize(dev)
             ms = time_steps(torch, dev, stream, lambda: (ds.reset_lengths(), run()), steps)
             forms["per_system_launches"] = w.n * steps / (ms / 1e3)
+            ds.reset_lengths()
+            run()
+            torch.cuda.synchronize(dev)
+            results["per_system_launches"] = ds.numpy()
         finally:
             for c in ctxs:
                 E2.evol_destroy(c)
-    return forms
+    return forms, results
 
 
 def main():
@@ -358,7 +444,7 @@ def main():
     if args.leaf > 0:
         ds.params.leaf_size = args.leaf
     elif not args.no_autotune and w.sys_offsets is None:
-        best, ms = E.evol_autotune(ctx, ds.particles, ds.params, ds.outputs, candidates=[8, 12, 16, 24, 32], reps=2)
+        best, ms = E.evol_autotune(ctx, ds.particles, ds.params, ds.outputs, candidates=[12, 16, 24, 32, 48], reps=3)
         ds.params.leaf_size = best
         autotune = {"leaf_size": best, "median_ms_by_leaf": ms}
 
@@ -455,10 +541,33 @@ def main():
         e2e = {"value": n_total * ke / te, "unit": "particles/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ke}
 
-    forms = {args.precision if offsets is None else f"batched_{args.precision}": value}
+    main_form = args.precision if offsets is None else f"batched_{args.precision}"
+    forms = {main_form: value}
+    accuracy = None
+    ostate = None
     if not args.no_forms:
-        forms.update(other_forms(torch, dev, stream, E, DeviceSet, w, max(2, min(args.steps, 5)), prec,
-                                 int(ds.params.leaf_size)))
+        g_main = gpu_check_step(E, ctx, ds, offsets)
+        rates, results = other_forms(torch, dev, stream, E, DeviceSet, w, max(2, min(args.steps, 5)), prec,
+                                     int(ds.params.leaf_size))
+        forms.update(rates)
+        results[main_form] = g_main
+        accuracy = {}
+        if rank == 0 and world == 1 and offsets is None:
+            # every form against the FP64 oracle on a seeded sample of particles
+            ostate = oracle_state(w, int(ds.params.leaf_size))
+            sidx = np.sort(np.random.default_rng(11).choice(w.n, min(w.n, 2000), replace=False))
+            ref = ostate[0].forces(w.params, ostate[1], idx=sidx)
+            for k in ("eps", "h", "rho"):
+                if k in ostate[1]:
+                    ref[k] = ostate[1][k]
+            for name, g in results.items():
+                accuracy[name] = form_errors(g, ref, sidx, w)
+            accuracy["sample"] = f"{len(sidx)} particles (seed 11), oracle leaf {int(ds.params.leaf_size)}"
+        # the forms against each other
+        A = lambda x: np.stack([x["ax"], x["ay"], x["az"]], 1)
+        for name, g in results.items():
+            if name != main_form:
+                accuracy[f"{name}_vs_{main_form}"] = _rel(A(g), A(g_main))
 
     # ---- roofline of the dominant kernel (the force walk) ----
     far, pp, sph, soft = float(cnt[0]), float(cnt[1]), float(cnt[2]), float(cnt[8])
@@ -484,7 +593,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            v, cores, desc = oracle_sample(w)
+            v, cores, desc = oracle_sample(w, leaf=int(ds.params.leaf_size), state=ostate)
             cpu = {"value": v, "unit": "particles/s", "cores": cores, "kind": "oracle", "sample": desc}
         except Exception as ex:     # the baseline is reported, never required
             cpu = {"value": None, "unit": "particles/s", "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}
@@ -510,6 +619,7 @@ def main():
                 "status_last_step": rc,
                 "counters": cnt,
                 "forms_particles_per_s": forms,
+                "forms_accuracy": accuracy,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": None}
         line["gpu_launches"] = launches_per_step(w) * args.steps

@@ -161,9 +161,11 @@ int evol_step_host(evol_ctx *ctx, evol_particles *p_host, const evol_params *prm
 /* Autotuner for the cost parameters of the step (never theta or the neighbour numbers): times
  * evol_step on these particles for each candidate leaf size and returns the fastest in
  * *best_leaf.  candidates: host array of ncand leaf sizes in 1..64 (NULL: {4, 8, 12, 16, 24, 32});
- * reps >= 1 timed steps per candidate after one untimed step; ms_out (host, ncand floats, may be
- * NULL) receives each candidate's median step time.  The particles' h and eps are overwritten
- * by the solved lengths as in evol_step; out receives the last run's results.  Synchronous. */
+ * after one untimed step (clock ramp-up) each candidate gets one untimed step (graph recording)
+ * and reps >= 1 timed steps, each started from the caller's h and eps as passed in (restored
+ * before every step, outside the timed interval); ms_out (host, ncand floats, may be NULL)
+ * receives each candidate's median step time.  On return h and eps hold the caller's starting
+ * values again; out receives the last run's results.  Synchronous. */
 int evol_autotune(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outputs *out,
                   const int *candidates, int ncand, int reps, int *best_leaf, float *ms_out);
 

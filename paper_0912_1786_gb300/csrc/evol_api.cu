@@ -561,6 +561,17 @@ int evol_autotune(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_o
         *best_leaf = candidates[0];
         return EVOL_OK;
     }
+    // Every timed step starts from the caller's starting lengths, as a step of the caller's run
+    // does: they are kept in the host-step staging buffer and restored before each step (outside
+    // the timed interval).
+    const int64_t n = p->n, ng = p->n_gas;
+    float *save_h = c->stage, *save_e = c->stage + c->cap;
+    auto restore = [&]() {
+        if (p->h && ng > 0) cudaMemcpyAsync(p->h, save_h, ng * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+        if (p->eps) cudaMemcpyAsync(p->eps, save_e, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    };
+    if (p->h && ng > 0) cudaMemcpyAsync(save_h, p->h, ng * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    if (p->eps) cudaMemcpyAsync(save_e, p->eps, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return EVOL_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -570,12 +581,22 @@ int evol_autotune(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_o
     float best = 3.0e38f;
     int best_k = 0;
     std::vector<float> t(reps);
+    // one untimed step first, so that the first candidate does not pay the clocks' ramp-up
+    {
+        evol_params q = *prm;
+        q.leaf_size = candidates[0];
+        restore();
+        rc = evol_step(c, p, &q, out);
+        if (!rc) rc = evol_sync(c);
+    }
     for (int k = 0; k < ncand && !rc; ++k) {
         evol_params q = *prm;
         q.leaf_size = candidates[k];
+        restore();
         if ((rc = evol_step(c, p, &q, out))) break;           // records the graphs for this leaf size
         if ((rc = evol_sync(c))) break;
         for (int r = 0; r < reps && !rc; ++r) {
+            restore();
             cudaEventRecord(e0, c->stream);
             rc = evol_step(c, p, &q, out);
             cudaEventRecord(e1, c->stream);
@@ -585,13 +606,14 @@ int evol_autotune(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_o
         if (rc) break;
         std::vector<float> srt(t);
         std::sort(srt.begin(), srt.end());
-        const float med = srt[reps / 2];
+        const float med = (reps & 1) ? srt[reps / 2] : 0.5f * (srt[reps / 2 - 1] + srt[reps / 2]);
         if (ms_out) ms_out[k] = med;
         if (med < best) {
             best = med;
             best_k = k;
         }
     }
+    restore();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!rc) *best_leaf = candidates[best_k];

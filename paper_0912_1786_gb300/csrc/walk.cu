@@ -156,17 +156,53 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
     return r;
 }
 
-template <bool MIXED>
+// Per-particle sums of one flush (a block of at most FARCAP far nodes or NEARCAP near entries).
 struct Acc {
     float ax = 0.f, ay = 0.f, az = 0.f, pot = 0.f;      // gravity (without G)
     float hx = 0.f, hy = 0.f, hz = 0.f, du = 0.f;       // SPH
 };
 
-// Register budgets: the plain gravity + SPH walk (the production form) fits five blocks per SM
-// (at most 102 registers) without spilling; every other variant carries a minimum of one block
-// per SM, so that the compiler keeps its state in registers instead of spilling to local memory.
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bp = s - a, ap = s - bp;
+    e = (a - ap) + (b - bp);
+}
+
+// Mixed form: the per-particle totals over the flush blocks are compensated sums -- each block
+// sum is added with TwoSum and its rounding error kept in a separate compensation term -- so the
+// totals carry the blocks' own FP32 rounding only (a few ulps of at most 64 terms), not that of
+// thousands of successive additions.
+template <bool MIXED>
+struct Totals {
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    __device__ __forceinline__ void add(const Acc &a)
+    {
+        const float v[8] = {a.ax, a.ay, a.az, a.pot, a.hx, a.hy, a.hz, a.du};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float t, e;
+            two_sum(s[k], v[k], t, e);
+            s[k] = t;
+            c[k] += e;
+        }
+    }
+    __device__ __forceinline__ double get(int k) const { return (double)s[k] + (double)c[k]; }
+};
+template <>
+struct Totals<false> {
+    __device__ __forceinline__ void add(const Acc &) {}
+    __device__ __forceinline__ double get(int) const { return 0.0; }
+};
+
+// Register budgets, chosen so that no variant spills to local memory: the plain gravity + SPH walk
+// (the production form) and the SPH-only walk fit five blocks per SM (at most 102 registers), the
+// mixed gravity + SPH walk four (128 registers), the gravity-only walks three; the check-mode
+// variants one.
 template <bool GRAV, bool SPH, bool MIXED, bool CHECK>
-__global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) ? EVOL_WALK_MINB : 1) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (GRAV && MIXED) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
     const int lane = threadIdx.x & 31;
@@ -201,8 +237,8 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
         const float E_i = two_eps_i * two_eps_i;
         const float H_i = gas_i ? two_h_i * two_h_i : -1.f;
 
-        Acc<MIXED> acc;
-        double tax = 0, tay = 0, taz = 0, tpot = 0, thx = 0, thy = 0, thz = 0, tdu = 0;
+        Acc acc;
+        Totals<MIXED> tot;
         unsigned long long hfar = 0, hnear = 0, hsph = 0;
         int cfar = 0, cpp = 0, csph = 0;
         // interaction counts of this lane (one group's counts fit 32 bits)
@@ -216,9 +252,8 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
 
         auto fold = [&]() {
             if (MIXED) {
-                tax += acc.ax; tay += acc.ay; taz += acc.az; tpot += acc.pot;
-                thx += acc.hx; thy += acc.hy; thz += acc.hz; tdu += acc.du;
-                acc = Acc<MIXED>();
+                tot.add(acc);
+                acc = Acc();
             }
         };
 
@@ -696,7 +731,11 @@ __global__ void __launch_bounds__(WK_THREADS, (GRAV && SPH && !MIXED && !CHECK) 
         if (GRAV && nfar) flush_far();
         if (nnear) flush_near();
 
-        if (!MIXED) {
+        double tax, tay, taz, tpot, thx, thy, thz, tdu;
+        if (MIXED) {
+            tax = tot.get(0); tay = tot.get(1); taz = tot.get(2); tpot = tot.get(3);
+            thx = tot.get(4); thy = tot.get(5); thz = tot.get(6); tdu = tot.get(7);
+        } else {
             tax = acc.ax; tay = acc.ay; taz = acc.az; tpot = acc.pot;
             thx = acc.hx; thy = acc.hy; thz = acc.hz; tdu = acc.du;
         }
