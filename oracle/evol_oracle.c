@@ -599,6 +599,56 @@ int orc_solve_lengths(const orc_tree *t, int mode, double n_nei, const int64_t *
     return err;
 }
 
+/* Velocity divergence at every listed particle from the discretised continuity equation
+ * (Sect. 2.1, the equations below Eq. continuity): with n_i = sum_j W(r_ij, L_i),
+ *     div v_i = -1/(n_i C_i) sum_j (v_i - v_j) . grad_i W(r_ij, L_i),
+ * where L is the particle's solved length and C its correction factor: Upsilon for the softening
+ * (mode 1, all species) and Omega* for the smoothing length (mode 0, gas neighbours of gas).
+ * grad_i W = (r_i - r_j)/r dW/dr with the exact spline derivative.  L, nsum, corr: original order
+ * (as orc_solve_lengths returns them); idx: particles to evaluate (all of the mode's species if
+ * NULL).  Returns 0, or -3 on neighbour overflow. */
+int orc_divv(const orc_tree *t, int mode, const double *L, const double *nsum, const double *corr,
+             const double *vx, const double *vy, const double *vz, const int64_t *idx, int64_t nidx,
+             int periodic_mask, const double *plo, const double *phi_, double *divv)
+{
+    orc_period per = {periodic_mask, {0, 0, 0}, {1, 1, 1}};
+    for (int a = 0; a < 3; ++a)
+        if ((periodic_mask >> a) & 1) { per.lo[a] = plo[a]; per.len[a] = phi_[a] - plo[a]; }
+    int64_t count = idx ? nidx : (mode == 0 ? t->n_gas : t->n);
+    int err = 0;
+#pragma omp parallel
+    {
+        int64_t cap = 1 << 16;
+        int64_t *scr = malloc(cap * sizeof(int64_t));
+        double *rs = malloc(cap * sizeof(double));
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t q = 0; q < count; ++q) {
+            int64_t i = idx ? idx[q] : q;
+            double p[3] = {t->x[i], t->y[i], t->z[i]};
+            int64_t cnt = (scr && rs) ? orc_gather(t, &per, p, 2.0 * L[i], mode == 0, scr, rs, cap) : -1;
+            if (cnt < 0) {
+#pragma omp critical
+                if (!err) err = -3;
+                continue;
+            }
+            double s = 0.0;
+            for (int64_t k = 0; k < cnt; ++k) {
+                int64_t j = scr[k];
+                double r = rs[k];
+                if (j == i || r <= 0.0) continue;
+                double rv[3] = {orc_wrap(&per, 0, p[0] - t->x[j]), orc_wrap(&per, 1, p[1] - t->y[j]),
+                                orc_wrap(&per, 2, p[2] - t->z[j])};
+                double vr = (vx[i] - vx[j]) * rv[0] + (vy[i] - vy[j]) * rv[1] + (vz[i] - vz[j]) * rv[2];
+                s += vr / r * orc_dWdr(r, L[i]);
+            }
+            divv[i] = -s / (nsum[i] * corr[i]);
+        }
+        free(scr);
+        free(rs);
+    }
+    return err;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Forces: tree walk with the Dubinski opening criterion, far nodes by monopole +          */
 /* quadrupole, near particles by the softened symmetric pair force with the adaptive      */
@@ -643,6 +693,7 @@ typedef struct {
                            (threshold + coordinate scale of the particle) */
     double scale;       /* max |coordinate| of the particle: the scale of FP32 position rounding */
     double aabs, duabs; /* sums of the magnitudes of the individual contributions to a and du/dt */
+    double mumax;       /* largest |mu_ij| of the viscosity over the SPH neighbours */
 } orc_result;
 
 /* Distance of one decision (value v against threshold thr) from its threshold.  It is taken
@@ -701,6 +752,7 @@ static void orc_pair(const orc_tree *t, const orc_params *pr, const orc_state *s
                 if (vr < 0) {
                     double hb = 0.5 * (hi + hj);
                     double mu = hb * vr / (r2 + 0.01 * hb * hb);
+                    if (fabs(mu) > res->mumax) res->mumax = fabs(mu);
                     double cb = 0.5 * (st->c[i] + st->c[j]);
                     double rb = 0.5 * (st->rho[i] + st->rho[j]);
                     Pi_visc = (-pr->alpha * cb * mu + pr->beta * mu * mu) / rb;
@@ -825,7 +877,7 @@ void orc_forces(orc_tree *t, double theta, double G, double gamma, double alpha,
                 double *ax, double *ay, double *az, double *pot, double *dudt,
                 uint64_t *hfar, uint64_t *hnear, uint64_t *hsph,
                 int64_t *nfar, int64_t *npp, int64_t *nsph, double *margin,
-                double *aabs, double *duabs)
+                double *aabs, double *duabs, double *mumax)
 {
     orc_params pr = {theta, G, gamma, alpha, beta, gravity, sph, adaptive, use_tc};
     orc_state st = {vx, vy, vz, eps, ups, X, h, rho, P, c, om, zeta};
@@ -851,6 +903,7 @@ void orc_forces(orc_tree *t, double theta, double G, double gamma, double alpha,
         if (margin) margin[i] = res.margin;
         if (aabs) aabs[i] = res.aabs;
         if (duabs) duabs[i] = res.duabs;
+        if (mumax) mumax[i] = res.mumax;
     }
 }
 

@@ -11,6 +11,7 @@ import ctypes as C
 import os
 import subprocess
 import threading
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -66,7 +67,10 @@ def lib():
                                         _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, C.c_void_p]
         L.orc_forces.argtypes = ([C.c_void_p, d, d, d, d, d, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                   _f64p, _f64p] + [_f64p] * 3 + [_f64p] * 3 + [_f64p] * 6 +
-                                 [C.c_void_p, C.c_int64] + [_f64p] * 5 + [C.c_void_p] * 9)
+                                 [C.c_void_p, C.c_int64] + [_f64p] * 5 + [C.c_void_p] * 10)
+        L.orc_divv.restype = C.c_int
+        L.orc_divv.argtypes = [C.c_void_p, C.c_int, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, C.c_void_p,
+                               C.c_int64, C.c_int, _f64p, _f64p, _f64p]
         L.orc_eos.argtypes = [C.c_int64, d, _f64p, _f64p, _f64p, _f64p]
         L.orc_num_threads.restype = C.c_int
         _lib = L
@@ -190,7 +194,7 @@ class OracleTree:
         hashes = [np.zeros(n, np.uint64) for _ in range(3)]
         counts = [np.zeros(n, np.int64) for _ in range(3)]
         margin = np.full(n, np.inf)
-        aabs, duabs = np.zeros(n), np.zeros(n)
+        aabs, duabs, mumax = np.zeros(n), np.zeros(n), np.zeros(n)
         tc = params.use_tc_gradient if use_tc is None else use_tc
         lib().orc_forces(self.ptr, float(params.theta), float(params.G), float(params.gamma),
                          float(params.alpha), float(params.beta), int(params.gravity), int(params.sph),
@@ -199,14 +203,31 @@ class OracleTree:
                          g("h"), g("rho"), g("P"), g("c"), g("omega"), g("zeta"),
                          ix.ctypes.data if ix is not None else None, int(len(ix)) if ix is not None else 0,
                          *out, *[a.ctypes.data for a in hashes], *[a.ctypes.data for a in counts],
-                         margin.ctypes.data, aabs.ctypes.data, duabs.ctypes.data)
+                         margin.ctypes.data, aabs.ctypes.data, duabs.ctypes.data, mumax.ctypes.data)
         res = dict(zip(("ax", "ay", "az", "pot", "dudt"), out))
         res.update(zip(("hfar", "hnear", "hsph"), hashes))
         res.update(zip(("nfar", "npp", "nsph"), counts))
         res["margin"] = margin
         res["aabs"] = aabs
         res["duabs"] = duabs
+        res["mumax"] = mumax
         return res
+
+    def divv(self, mode: int, L, nsum, corr, vx, vy, vz, idx=None, params=None):
+        """Velocity divergence from the discretised continuity equation (Sect. 2.1): mode 1 with the
+        softening kernel over all species (corr = Upsilon), mode 0 with the smoothing kernel over
+        the gas (corr = Omega*).  Arrays in original order; returns div v (original order)."""
+        n = self.n
+        out = np.zeros(n)
+        pm, lo, hi = self._period(params)
+        ix = _c(idx, np.int64) if idx is not None else None
+        rc = lib().orc_divv(self.ptr, int(mode), _c(L, np.float64), _c(nsum, np.float64), _c(corr, np.float64),
+                            _c(vx, np.float64), _c(vy, np.float64), _c(vz, np.float64),
+                            ix.ctypes.data if ix is not None else None, int(len(ix)) if ix is not None else 0,
+                            pm, lo, hi, out)
+        if rc != 0:
+            raise RuntimeError(f"oracle divergence failed (code {rc})")
+        return out
 
 
 def force_step(w, params=None, idx=None, use_tc=None, tree=None, fixed_lengths=None):
@@ -237,6 +258,11 @@ def force_step(w, params=None, idx=None, use_tc=None, tree=None, fixed_lengths=N
             c[w.n_gas:] = 0
             st.update(h=h, rho=rho, omega=om, zeta=zeta, P=P, c=c)
             res.update(h=h, n_h=nh, rho=rho, omega=om, zeta=zeta, P=P, c=c)
+        # velocity divergence from the discretised continuity equation (Sect. 2.1), with each length
+        if p.gravity and p.adaptive_softening:
+            res["divv_eps"] = t.divv(1, eps, neps, ups, st["vx"], st["vy"], st["vz"], params=p)
+        if p.sph and w.n_gas > 0:
+            res["divv_h"] = t.divv(0, h, nh, om, st["vx"], st["vy"], st["vz"], idx=gidx, params=p)
     f = t.forces(p, st, idx=idx, use_tc=use_tc)
     res.update(f)
     res["tree"] = t
@@ -282,3 +308,112 @@ def kdk(w, dt: float, nsteps: int, params=None):
         U[:ng] += 0.5 * dt * DU[:ng]
     return {"x": X[:, 0], "y": X[:, 1], "z": X[:, 2], "vx": V[:, 0], "vy": V[:, 1], "vz": V[:, 2], "u": U,
             "last": r}
+
+
+@dataclass
+class TimeStep:
+    """Parameters of the global time step (Sect. 4.2): each eta scales one criterion (0 leaves it
+    out); the step is the smallest criterion over all particles, clamped to [dt_min, dt_max]."""
+    eta_acc: float = 0.1
+    eta_vel: float = 0.0
+    eta_av: float = 0.0
+    eta_courant: float = 0.1
+    eta_u: float = 0.1
+    dt_min: float = 0.0
+    dt_max: float = 1.0
+
+
+def timestep_criteria(w, res, vx, vy, vz, u, ts, params=None):
+    """Per-particle time-step criteria of Sect. 4.2 from the results of a force step.
+
+    L_i = min(eps_i, h_i) (eps alone for non-gas particles, h alone without gravity).
+      dt_acc = eta_acc sqrt(L / |a|)
+      dt_vel = eta_vel L / |v|                      (reading: the printed square root is not a time)
+      dt_av  = eta_av |v| / |a|                     (reading: the same)
+      dt_C   = eta_C h / (h |div v| + c + 1.2 (alpha c + beta max_j |mu_ij|))     (gas)
+      dt_u   = eta_u |u / (du/dt)|                                                 (gas)
+    div v is the smoothing-kernel estimate of the continuity equation.  Returns a dict of arrays
+    (inf where a criterion does not apply)."""
+    p = params or w.params
+    n, ng = w.n, w.n_gas
+    inf = np.full(n, np.inf)
+    a = np.sqrt(res["ax"] ** 2 + res["ay"] ** 2 + res["az"] ** 2)
+    v = np.sqrt(np.asarray(vx, np.float64) ** 2 + np.asarray(vy, np.float64) ** 2 + np.asarray(vz, np.float64) ** 2)
+    L = res["eps"].copy() if p.gravity else np.full(n, np.inf)
+    if p.sph and ng:
+        L[:ng] = np.minimum(L[:ng], res["h"][:ng])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        out = {"acc": ts.eta_acc * np.sqrt(L / a) if ts.eta_acc > 0 else inf,
+               "vel": ts.eta_vel * L / v if ts.eta_vel > 0 else inf,
+               "av": ts.eta_av * v / a if ts.eta_av > 0 else inf}
+        c_ = inf.copy()
+        uu = inf.copy()
+        if p.sph and ng:
+            h = res["h"][:ng]
+            c = res["c"][:ng]
+            den = h * np.abs(res["divv_h"][:ng]) + c + 1.2 * (p.alpha * c + p.beta * res["mumax"][:ng])
+            c_[:ng] = ts.eta_courant * h / den if ts.eta_courant > 0 else np.inf
+            uu[:ng] = ts.eta_u * np.abs(np.asarray(u[:ng], np.float64) / res["dudt"][:ng]) if ts.eta_u > 0 else np.inf
+        out["courant"] = c_
+        out["u"] = uu
+    for k in out:
+        out[k] = np.where(np.isfinite(out[k]) & (out[k] > 0), out[k], np.inf)
+    return out
+
+
+def global_timestep(crit, ts):
+    """The smallest criterion over all particles, clamped to [dt_min, dt_max]."""
+    dt = min(float(np.min(c)) for c in crit.values())
+    return float(min(max(dt, ts.dt_min), ts.dt_max))
+
+
+def run(w, nsteps: int, ts: TimeStep, params=None, predicted=True):
+    """Global-time-step KDK leapfrog (Sect. 4.1-4.2) in FP64 on top of force_step.
+
+    Each step: dt from the criteria of the last force step; v += a dt/2, u += du/dt dt/2;
+    x += v dt; a force step at the new positions in which the SPH terms use the predicted
+    v_n + a_n dt and the equation of state the predicted u_n + (du/dt)_n dt (Sect. 4.1, when
+    `predicted`); v += a dt/2, u += du/dt dt/2.  The state is kept in FP64 and handed to each force
+    step rounded to float32.  Returns the final state, the list of time steps and the last
+    force-step result."""
+    import copy
+
+    p = params or w.params
+    n, ng = w.n, w.n_gas
+    X = np.stack([w.x, w.y, w.z], 1).astype(np.float64)
+    V = np.stack([w.vx, w.vy, w.vz], 1).astype(np.float64)
+    U = w.u.astype(np.float64).copy()
+    cur = copy.copy(w)
+
+    def forces(vel, uu):
+        cur.x, cur.y, cur.z = (np.ascontiguousarray(X[:, a], np.float32) for a in range(3))
+        cur.vx, cur.vy, cur.vz = (np.ascontiguousarray(vel[:, a], np.float32) for a in range(3))
+        cur.u = np.ascontiguousarray(uu, np.float32)
+        r = force_step(cur, params=p)
+        return np.stack([r["ax"], r["ay"], r["az"]], 1), r["dudt"], r
+
+    A, DU, r = forces(V, U)
+    lo = np.asarray(getattr(p, "periodic_lo", (0, 0, 0)), np.float64)
+    hi = np.asarray(getattr(p, "periodic_hi", (1, 1, 1)), np.float64)
+    dts = []
+    for _ in range(nsteps):
+        crit = timestep_criteria(cur, r, V[:, 0], V[:, 1], V[:, 2], U, ts, params=p)
+        dt = global_timestep(crit, ts)
+        dts.append(dt)
+        V += 0.5 * dt * A
+        U[:ng] += 0.5 * dt * DU[:ng]
+        X += dt * V
+        for a in range(3):
+            if (getattr(p, "periodic_mask", 0) >> a) & 1:
+                X[:, a] = lo[a] + np.mod(X[:, a] - lo[a], hi[a] - lo[a])
+        if predicted:
+            Vp = V + 0.5 * dt * A
+            Up = U.copy()
+            Up[:ng] += 0.5 * dt * DU[:ng]
+        else:
+            Vp, Up = V, U
+        A, DU, r = forces(Vp, Up)
+        V += 0.5 * dt * A
+        U[:ng] += 0.5 * dt * DU[:ng]
+    return {"x": X[:, 0], "y": X[:, 1], "z": X[:, 2], "vx": V[:, 0], "vy": V[:, 1], "vz": V[:, 2], "u": U,
+            "dts": dts, "last": r}

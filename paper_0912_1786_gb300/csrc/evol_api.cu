@@ -36,7 +36,7 @@ int dalloc(T **p, size_t count)
 void free_all(evol_ctx *c)
 {
     evol_dev &d = c->d;
-    void *ptrs[] = {d.pos, d.vel, d.grav, d.hydro, d.snd, d.vah, d.orig, d.len_h, d.len_eps, d.nh, d.omega,
+    void *ptrs[] = {d.pos, d.vel, d.grav, d.hydro, d.snd, d.vah, d.orig, d.inv, d.len_h, d.len_eps, d.nh, d.omega,
                     d.zeta, d.rho, d.neps, d.ups, d.X, d.acc, d.dudt, d.keys_a, d.keys_b, d.vals_a, d.vals_b,
                     d.hist, d.lcp, d.cnt, d.base, d.scan_part, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
                     d.nnch, d.narrive, d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nM64, d.nC64, d.nQ64, d.nBmin,
@@ -199,7 +199,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     evol_dev &d = c->d;
     int rc = 0;
     rc |= dalloc(&d.pos, n); rc |= dalloc(&d.vel, n); rc |= dalloc(&d.grav, n); rc |= dalloc(&d.hydro, n);
-    rc |= dalloc(&d.snd, n); rc |= dalloc(&d.vah, n); rc |= dalloc(&d.orig, n);
+    rc |= dalloc(&d.snd, n); rc |= dalloc(&d.vah, n); rc |= dalloc(&d.orig, n); rc |= dalloc(&d.inv, n);
     rc |= dalloc(&d.len_h, n); rc |= dalloc(&d.len_eps, n); rc |= dalloc(&d.nh, n); rc |= dalloc(&d.omega, n);
     rc |= dalloc(&d.zeta, n); rc |= dalloc(&d.rho, n); rc |= dalloc(&d.neps, n); rc |= dalloc(&d.ups, n);
     rc |= dalloc(&d.X, n); rc |= dalloc(&d.acc, n); rc |= dalloc(&d.dudt, n);

@@ -28,6 +28,7 @@ struct evol_dev {
     float4 *pos, *vel, *grav, *hydro, *snd;
     float *vah;              // v . a_hyd per particle (energy balance diagnostic)
     int32_t *orig;           // sorted -> caller index
+    int32_t *inv;            // caller -> sorted index
     float *len_h, *len_eps;  // solved lengths, sorted
     float *nh, *omega, *zeta, *rho;     // gas outputs (sorted; n entries, non-gas unused)
     float *neps, *ups, *X;              // softening outputs (sorted)

@@ -40,16 +40,18 @@ __global__ void k_pack(int n, int n_gas, int do_grav, int adaptive, int do_sph, 
     d.snd[s] = sn;
 }
 
-// Results into the caller's order.  Every value written is checked: a non-finite one is flagged
-// as EVOL_ENAN (the first error recorded wins, so a length that had no root reports ENOCONV).
+// Results into the caller's order: thread j gathers caller index j's values from its sorted
+// position (so the writes, the larger share of the traffic, are coalesced).  Every value written
+// is checked: a non-finite one is flagged as EVOL_ENAN (the first error recorded wins, so a length
+// that had no root reports ENOCONV).
 __global__ void k_unpermute(int n, int n_gas, int what, int add_acc, evol_dev d, float *h, float *eps, float *ax,
                             float *ay, float *az, float *pot, float *rho, float *P, float *c, float *omega,
                             float *zeta, float *dudt, float *ups, float *X)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int j = d.orig[s];
-    bool gas = j < n_gas;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int s = d.inv[j];
+    const bool gas = j < n_gas;
     bool fin = true;
     auto put = [&](float *dst, float v) {
         fin = fin && isfinite(v);

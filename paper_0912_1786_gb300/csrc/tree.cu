@@ -110,12 +110,20 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v)
     return v;
 }
 
+// 2^21 / side for a power-of-two side (exact, without a double division)
+__device__ __forceinline__ double key_scale(double side)
+{
+    int e;
+    frexp(side, &e);                 // side = 2^(e-1)
+    return ldexp(1.0, EVOL_MAXLEVEL + 1 - e);
+}
+
 __global__ void k_keys(int n, const float *__restrict__ x, const float *__restrict__ y, const float *__restrict__ z,
                        const double *__restrict__ cube, uint64_t *__restrict__ keys, int32_t *__restrict__ vals)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double scale = ldexp(1.0, EVOL_MAXLEVEL) / cube[3];
+    const double scale = key_scale(cube[3]);
     float v[3] = {x[i], y[i], z[i]};
     uint64_t q[3];
 #pragma unroll
@@ -284,7 +292,7 @@ __global__ void k_permute(int n, int n_gas, const int32_t *__restrict__ perm, co
                           const float *__restrict__ vy, const float *__restrict__ vz, const float *__restrict__ m,
                           const float *__restrict__ u, const float *__restrict__ h, const float *__restrict__ eps,
                           float4 *__restrict__ pos, float4 *__restrict__ vel, float *__restrict__ lh,
-                          float *__restrict__ le, int32_t *__restrict__ orig)
+                          float *__restrict__ le, int32_t *__restrict__ orig, int32_t *__restrict__ inv)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -295,6 +303,7 @@ __global__ void k_permute(int n, int n_gas, const int32_t *__restrict__ perm, co
     lh[s] = (gas && h) ? h[j] : 0.f;
     le[s] = eps ? eps[j] : 0.f;
     orig[s] = j;
+    inv[j] = s;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -550,13 +559,14 @@ __device__ void leaf_moments(int b, int e, int n_gas, const float4 *__restrict__
     }
 }
 
-// child c's moments; FP32: its centre-of-mass offset re-expressed about the parent's centre
-// (cg_c - cg_p is a power of two per axis: exact in float)
+// child c's moments; FP32: its centre-of-mass offset re-expressed about the parent's centre.  A
+// child cell is one level below its parent (a cell with one non-empty octant still has that octant
+// as its child), so its centre is the parent's centre moved by a quarter of the parent's side
+// along each axis, in the direction the child's octal digit gives: a power of two, exact in float.
 template <typename T>
-__device__ void load_child(const NodeOut &o, int c, const double cgp[3], const double *__restrict__ cube,
-                           const uint64_t *__restrict__ keys, const int32_t *__restrict__ nbeg,
-                           const int32_t *__restrict__ nlev, Mom<T> &mm, float3 &lo, float3 &hi, int &hasgas,
-                           bool mixed)
+__device__ void load_child(const NodeOut &o, int c, float side_p, const uint64_t *__restrict__ keys,
+                           const int32_t *__restrict__ nbeg, const int32_t *__restrict__ nlev, Mom<T> &mm,
+                           float3 &lo, float3 &hi, int &hasgas, bool mixed)
 {
     constexpr bool rel = sizeof(T) == sizeof(float);
     float4 bl = __ldcg(&o.bmin[c]), bh = __ldcg(&o.bmax[c]);
@@ -576,12 +586,13 @@ __device__ void load_child(const NodeOut &o, int c, const double cgp[3], const d
     mm.q[3] = (T)Q1.x; mm.q[4] = (T)Q1.y; mm.q[5] = (T)Q1.z;
     if (rel) {
         const float4 co = __ldcg(&o.coff[c]);
-        double cgc[3];
-        node_centre(cube, __ldcg(&keys[__ldcg(&nbeg[c])]), __ldcg(&nlev[c]), cgc);
+        const int lc = __ldcg(&nlev[c]);
+        const unsigned dg = (unsigned)(__ldcg(&keys[__ldcg(&nbeg[c])]) >> (3 * (EVOL_MAXLEVEL - lc))) & 7u;
+        const float q = 0.25f * side_p;
         mm.M = (T)co.w;
-        mm.c[0] = (T)co.x + (T)(cgc[0] - cgp[0]);
-        mm.c[1] = (T)co.y + (T)(cgc[1] - cgp[1]);
-        mm.c[2] = (T)co.z + (T)(cgc[2] - cgp[2]);
+        mm.c[0] = (T)co.x + (T)((dg & 4u) ? q : -q);
+        mm.c[1] = (T)co.y + (T)((dg & 2u) ? q : -q);
+        mm.c[2] = (T)co.z + (T)((dg & 1u) ? q : -q);
     } else {
         const float4 A = __ldcg(&o.nA[c]);
         mm.M = (T)Q0.w;
@@ -591,9 +602,8 @@ __device__ void load_child(const NodeOut &o, int c, const double cgp[3], const d
 
 template <typename T>
 __device__ void combine(const NodeOut &o, int id, int nch, const int32_t *__restrict__ nnext, const double cgp[3],
-                        const double *__restrict__ cube, const uint64_t *__restrict__ keys,
-                        const int32_t *__restrict__ nbeg, const int32_t *__restrict__ nlev, Mom<T> &mm, float3 &lo,
-                        float3 &hi, int &hasgas, bool mixed)
+                        float side_p, const uint64_t *__restrict__ keys, const int32_t *__restrict__ nbeg,
+                        const int32_t *__restrict__ nlev, Mom<T> &mm, float3 &lo, float3 &hi, int &hasgas, bool mixed)
 {
     constexpr bool rel = sizeof(T) == sizeof(float);
     Mom<T> ch[8];
@@ -605,7 +615,7 @@ __device__ void combine(const NodeOut &o, int id, int nch, const int32_t *__rest
     for (int k = 0; k < nch; ++k) {
         float3 cl, chh;
         int cg;
-        load_child(o, c, cgp, cube, keys, nbeg, nlev, ch[k], cl, chh, cg, mixed);
+        load_child(o, c, side_p, keys, nbeg, nlev, ch[k], cl, chh, cg, mixed);
         lo.x = fminf(lo.x, cl.x); lo.y = fminf(lo.y, cl.y); lo.z = fminf(lo.z, cl.z);
         hi.x = fmaxf(hi.x, chh.x); hi.y = fmaxf(hi.y, chh.y); hi.z = fmaxf(hi.z, chh.z);
         hasgas |= cg;
@@ -662,7 +672,8 @@ __global__ void k_moments(const int32_t *__restrict__ nnodes, int n_gas, const i
             const double *cbp = cube + 4 * sys_sorted[nbeg[p]];
             double cgp[3];
             node_centre(cbp, keys[nbeg[p]], nlev[p], cgp);
-            combine<T>(o, p, nnch[p], nnext, cgp, cbp, keys, nbeg, nlev, mm, lo, hi, hg, mixed != 0);
+            combine<T>(o, p, nnch[p], nnext, cgp, (float)ldexp(cbp[3], -nlev[p]), keys, nbeg, nlev, mm, lo, hi, hg,
+                       mixed != 0);
             write_node<T>(o, p, mm, lo, hi, hg, nlev[p], cgp, ldexp(cbp[3], -nlev[p]), theta, mixed != 0);
             __threadfence();
             p = nparent[p];
@@ -788,7 +799,7 @@ __global__ void k_bbox_sys(const int32_t *__restrict__ sys_off, const float *__r
 
 __device__ __forceinline__ uint64_t key_of(float x, float y, float z, const double *__restrict__ cb)
 {
-    const double scale = ldexp(1.0, EVOL_MAXLEVEL) / cb[3];
+    const double scale = key_scale(cb[3]);
     const float v[3] = {x, y, z};
     uint64_t q[3];
 #pragma unroll
@@ -911,7 +922,7 @@ int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *p
                                          va == d.vals_a ? nullptr : d.vals_a);
     }
     k_permute<<<gb, tb, 0, st>>>(n, (int)p->n_gas, d.vals_a, p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->u,
-                                 p->h, p->eps, d.pos, d.vel, d.len_h, d.len_eps, d.orig);
+                                 p->h, p->eps, d.pos, d.vel, d.len_h, d.len_eps, d.orig, d.inv);
     k_lcp<<<gb, tb, 0, st>>>(n, d.keys_a, d.sys_off, nsys, d.lcp, d.sys_sorted);
     k_count<<<gb, tb, 0, st>>>(n, d.lcp, leaf, d.cnt);
     int rc = scan_i32(c, n, d.cnt, d.base, 1);
