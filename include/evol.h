@@ -152,6 +152,35 @@ int evol_step_batched(evol_ctx *ctx, const int64_t *sys_offsets, int nsys, evol_
  * nsteps times.  Returns EVOL_EINVAL for nsteps < 0 or dt not finite. */
 int evol_kdk(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outputs *out, float dt, int nsteps);
 
+/* Global time step of the integrator (Sect. 4.2).  Each eta scales one per-particle criterion;
+ * 0 leaves the criterion out.  With L = min(eps_i, h_i) (eps alone for non-gas particles):
+ *   eta_acc sqrt(L/|a|),  eta_vel L/|v|,  eta_av |v|/|a|,
+ *   eta_courant h / (h |div v| + c + 1.2 (alpha c + beta max_j |mu_ij|))     (gas),
+ *   eta_u |u / (du/dt)|                                                     (gas).
+ * (The paper prints the second and third criteria under square roots that do not give a time;
+ * they are taken as written here.)  dt is the smallest criterion over all particles, clamped to
+ * [dt_min, dt_max] (dt_max where no criterion applies). */
+typedef struct {
+    float eta_acc, eta_vel, eta_av, eta_courant, eta_u;
+    float dt_min, dt_max;           /* 0 <= dt_min <= dt_max, dt_max > 0 */
+    int predicted_velocity;         /* 1: SPH terms use v_n + a_n dt and u_n + (du/dt)_n dt (Sect. 4.1) */
+    int predict_lengths;            /* 1: each solve starts from L exp(div v dt / 3), the continuity
+                                       equation's prediction (Sect. 2.1); changes cost, not results */
+} evol_integrator;
+
+/* Kick-drift-kick leapfrog with the global time step (Sect. 4.1-4.2), entirely on the device:
+ * one force step at the start, then nsteps times: dt from the criteria of the last force step
+ * (a device minimum over all particles), v += a dt/2 (u += du/dt dt/2 for gas), x += v dt (periodic
+ * axes wrapped), the predicted starting lengths, a force step (velocity divergences and the
+ * largest |mu| per gas particle included), v += a dt/2, u += du/dt dt/2.  One step is recorded
+ * into a CUDA graph once and replayed nsteps times; dt never leaves the device.  x, y, z, vx, vy,
+ * vz, u, h and eps are updated IN PLACE (writable device memory despite the const qualifiers).
+ * *time (host, in/out, may be NULL) advances by the sum of the steps; *last_dt (may be NULL)
+ * receives the last step.  out receives the outputs of the last force step.  Synchronises the
+ * stream before returning.  EVOL_EINVAL for nsteps < 0, negative etas or a bad dt range. */
+int evol_run(evol_ctx *ctx, evol_particles *p, const evol_params *prm, const evol_integrator *ip,
+             evol_outputs *out, int nsteps, double *time, float *last_dt);
+
 /* evol_step on HOST buffers: copies the inputs host -> device into context-owned buffers,
  * runs the step and copies every non-NULL output (and h, eps) back, then synchronises.
  * The particle and output pointers of this call are host pointers (pinned memory is
@@ -208,7 +237,10 @@ int evol_get_counters(evol_ctx *ctx, uint64_t out[32]);
  *                              (l/theta + delta)^2
  *   EVOL_DBG_HASHES uint64[3*n] caller order: far-node set, near-leaf set, SPH neighbour set
  *   EVOL_DBG_COUNTS int32[3*n]  caller order: far nodes, particle pairs, SPH pairs
- * Hashes and per-particle counts are written only while check mode is on. */
+ *   EVOL_DBG_FLOW   float[3*n]  caller order: div v with the softening kernel, div v with the
+ *                               smoothing kernel (gas), largest |mu_ij| of the viscosity (gas)
+ * Hashes and per-particle counts are written only while check mode is on; the divergences only
+ * by evol_run's force steps. */
 #define EVOL_DBG_KEYS     1
 #define EVOL_DBG_PERM     2
 #define EVOL_DBG_NODES    3
@@ -216,6 +248,7 @@ int evol_get_counters(evol_ctx *ctx, uint64_t out[32]);
 #define EVOL_DBG_MOMENTS  5
 #define EVOL_DBG_HASHES   6
 #define EVOL_DBG_COUNTS   7
+#define EVOL_DBG_FLOW     8
 int64_t evol_get_debug(evol_ctx *ctx, int what, void *host_dst, int64_t cap_bytes);
 
 /* Check mode (0/1): the walks also record, per particle, order-independent 64-bit hashes

@@ -36,7 +36,7 @@ int dalloc(T **p, size_t count)
 void free_all(evol_ctx *c)
 {
     evol_dev &d = c->d;
-    void *ptrs[] = {d.pos, d.vel, d.grav, d.hydro, d.snd, d.vah, d.orig, d.inv, d.len_h, d.len_eps, d.nh, d.omega,
+    void *ptrs[] = {d.pos, d.vel, d.grav, d.hydro, d.snd, d.vah, d.orig, d.inv, d.divv_h, d.divv_e, d.mumax, d.dt, d.time, d.len_h, d.len_eps, d.nh, d.omega,
                     d.zeta, d.rho, d.neps, d.ups, d.X, d.acc, d.dudt, d.keys_a, d.keys_b, d.vals_a, d.vals_b,
                     d.hist, d.lcp, d.cnt, d.base, d.scan_part, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
                     d.nnch, d.narrive, d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nM64, d.nC64, d.nQ64, d.nBmin,
@@ -50,6 +50,7 @@ void free_all(evol_ctx *c)
     for (int k = 0; k < 8; ++k)
         if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
     if (c->kdk_exec) cudaGraphExecDestroy(c->kdk_exec);
+    if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
 }
 
 int check_args(evol_ctx *c, const evol_particles *p, const evol_params *prm)
@@ -203,6 +204,8 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.len_h, n); rc |= dalloc(&d.len_eps, n); rc |= dalloc(&d.nh, n); rc |= dalloc(&d.omega, n);
     rc |= dalloc(&d.zeta, n); rc |= dalloc(&d.rho, n); rc |= dalloc(&d.neps, n); rc |= dalloc(&d.ups, n);
     rc |= dalloc(&d.X, n); rc |= dalloc(&d.acc, n); rc |= dalloc(&d.dudt, n);
+    rc |= dalloc(&d.divv_h, n); rc |= dalloc(&d.divv_e, n); rc |= dalloc(&d.mumax, n);
+    rc |= dalloc(&d.dt, 4); rc |= dalloc(&d.time, 1);
     rc |= dalloc(&d.keys_a, n); rc |= dalloc(&d.keys_b, n); rc |= dalloc(&d.vals_a, n); rc |= dalloc(&d.vals_b, n);
     rc |= dalloc(&d.hist, 256 * c->sort_blocks + 1);
     rc |= dalloc(&d.lcp, n); rc |= dalloc(&d.cnt, n + 1); rc |= dalloc(&d.base, n + 1);
@@ -338,6 +341,8 @@ static int run_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol
     sig = fnv(sig, out, sizeof *out);
     sig = fnv(sig, &c->check_mode, sizeof c->check_mode);
     sig = fnv(sig, &c->wstack_lim, sizeof c->wstack_lim);
+    sig = fnv(sig, &c->want_divv, sizeof c->want_divv);
+    sig = fnv(sig, &c->pred_dt, sizeof c->pred_dt);
     sig = fnv(sig, &c->stream, sizeof c->stream);
     if (!c->graph_exec[0] || sig != c->graph_sig) {
         for (int k = 0; k < NPHASE; ++k)
@@ -499,6 +504,112 @@ int evol_kdk(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_output
     for (int k = 0; k < 4; ++k)
         if (dst[k] && len[k] > 0)
             cudaMemcpyAsync(dst[k], src[k], len[k] * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    return EVOL_OK;
+}
+
+int evol_run(evol_ctx *c, evol_particles *p, const evol_params *prm, const evol_integrator *ip, evol_outputs *out,
+             int nsteps, double *time, float *last_dt)
+{
+    int rc = check_args(c, p, prm);
+    if (rc || (p && p->n == 0)) return rc;
+    if (!ip || nsteps < 0) return EVOL_EINVAL;
+    const float et[5] = {ip->eta_acc, ip->eta_vel, ip->eta_av, ip->eta_courant, ip->eta_u};
+    for (float e : et)
+        if (!(e >= 0.f)) return EVOL_EINVAL;
+    if (!(ip->dt_min >= 0.f) || !(ip->dt_max > 0.f) || !(ip->dt_min <= ip->dt_max) || ip->dt_max > 3.0e38f)
+        return EVOL_EINVAL;
+    if (!p->vx || !p->vy || !p->vz) return EVOL_EINVAL;
+    const int64_t cap = c->cap;
+    evol_outputs o = out ? *out : evol_outputs{};
+    o.ax = c->kdk_acc;
+    o.ay = c->kdk_acc + cap;
+    o.az = c->kdk_acc + 2 * cap;
+    o.dudt = c->kdk_acc + 3 * cap;
+    const double t0 = time ? *time : 0.0;
+    if (cudaMemcpyAsync(c->d.time, &t0, sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return set_err(c, EVOL_ECUDA);
+    // forces, velocity divergences and the largest |mu| at the starting positions
+    c->want_divv = 1;
+    c->pred_dt = nullptr;
+    if ((rc = evol_step(c, p, prm, &o))) {
+        c->want_divv = 0;
+        return rc;
+    }
+    if (nsteps > 0) {
+        uint64_t sig = 6364136223846793005ull;
+        sig = fnv(sig, p, sizeof *p);
+        sig = fnv(sig, prm, sizeof *prm);
+        sig = fnv(sig, ip, sizeof *ip);
+        sig = fnv(sig, &o, sizeof o);
+        sig = fnv(sig, &c->check_mode, sizeof c->check_mode);
+        sig = fnv(sig, &c->wstack_lim, sizeof c->wstack_lim);
+        sig = fnv(sig, &c->stream, sizeof c->stream);
+        if (!c->run_exec || sig != c->run_sig) {
+            if (c->run_exec) {
+                cudaGraphExecDestroy(c->run_exec);
+                c->run_exec = nullptr;
+            }
+            cudaStream_t cap_stream = c->stream;
+            bool own = false;
+            if (!cap_stream) {
+                if (cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                    c->want_divv = 0;
+                    return set_err(c, EVOL_ECUDA);
+                }
+                own = true;
+            }
+            cudaStream_t saved = c->stream;
+            c->stream = cap_stream;
+            cudaGraph_t graph = nullptr;
+            int prc = EVOL_OK;
+            if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                prc = EVOL_ECUDA;
+            } else {
+                prc = evol_launch_integrator_step(c, p, prm, ip, 0);
+                c->pred_dt = ip->predicted_velocity ? c->d.dt : nullptr;
+                for (int k = 0; k < NPHASE && !prc; ++k) prc = record_phase(c, k, p, prm, &o);
+                c->pred_dt = nullptr;
+                if (!prc) prc = evol_launch_integrator_step(c, p, prm, ip, 1);
+                cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
+                if (!prc && (e != cudaSuccess || !graph)) prc = EVOL_ECUDA;
+                if (!prc && cudaGraphInstantiate(&c->run_exec, graph, 0) != cudaSuccess) {
+                    c->run_exec = nullptr;
+                    prc = EVOL_ECUDA;
+                }
+            }
+            if (graph) cudaGraphDestroy(graph);
+            c->stream = saved;
+            if (own) cudaStreamDestroy(cap_stream);
+            if (prc) {
+                cudaGetLastError();
+                c->want_divv = 0;
+                return set_err(c, prc);
+            }
+            c->run_sig = sig;
+        }
+        for (int k = 0; k < nsteps; ++k)
+            if (cudaGraphLaunch(c->run_exec, c->stream) != cudaSuccess) {
+                c->want_divv = 0;
+                return set_err(c, EVOL_ECUDA);
+            }
+    }
+    c->want_divv = 0;
+    // hand the last accelerations and du/dt to the caller
+    const int64_t n = p->n, ng = p->n_gas;
+    float *dst[4] = {out ? out->ax : nullptr, out ? out->ay : nullptr, out ? out->az : nullptr,
+                     out ? out->dudt : nullptr};
+    const float *src[4] = {o.ax, o.ay, o.az, o.dudt};
+    const int64_t len[4] = {n, n, n, ng};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k] && len[k] > 0)
+            cudaMemcpyAsync(dst[k], src[k], len[k] * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    double tt = t0;
+    float dt = 0.f;
+    cudaMemcpyAsync(&tt, c->d.time, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(&dt, c->d.dt, sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return set_err(c, EVOL_ECUDA);
+    if (time) *time = tt;
+    if (last_dt) *last_dt = nsteps > 0 ? dt : 0.f;
     return EVOL_OK;
 }
 
@@ -721,6 +832,23 @@ int64_t evol_get_debug(evol_ctx *c, int what, void *dst, int64_t cap)
             }
         }
         return (int64_t)nn * 20;
+    }
+    case EVOL_DBG_FLOW: {
+        if (dst && cap >= 3 * n * 4) {
+            std::vector<int32_t> orig(n);
+            std::vector<float> a(n), b(n), m(n);
+            cudaMemcpy(orig.data(), c->d.orig, n * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(a.data(), c->d.divv_e, n * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(b.data(), c->d.divv_h, n * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(m.data(), c->d.mumax, n * 4, cudaMemcpyDeviceToHost);
+            float *o = (float *)dst;
+            for (int64_t s = 0; s < n; ++s) {
+                o[orig[s]] = a[s];
+                o[n + orig[s]] = b[s];
+                o[2 * n + orig[s]] = m[s];
+            }
+        }
+        return 3 * n;
     }
     case EVOL_DBG_HASHES:
     case EVOL_DBG_COUNTS: {

@@ -33,6 +33,10 @@ struct evol_dev {
     float *nh, *omega, *zeta, *rho;     // gas outputs (sorted; n entries, non-gas unused)
     float *neps, *ups, *X;              // softening outputs (sorted)
     float4 *acc;             // ax, ay, az, pot (sorted)
+    float *divv_h, *divv_e;  // velocity divergence with the smoothing / softening kernel (sorted)
+    float *mumax;            // largest |mu_ij| of the viscosity per gas particle (sorted)
+    float *dt;               // integrator scalars: [0] time step, [1] criterion minimum (as bits)
+    double *time;            // integrator time
     float *dudt;             // sorted
     // sort
     uint64_t *keys_a, *keys_b;
@@ -89,6 +93,8 @@ struct evol_ctx {
     int64_t diag_blocks;
     int host_err;            // first error seen on the host side
     int check_mode;
+    int want_divv;           // the length solves also form div v (integrator)
+    const float *pred_dt;    // device time step of the predicted pack (integrator), or NULL
     // state of the last build / density
     int64_t built_n, built_ngas;
     int nsys;                // systems of the current particle set (1 unless batched)
@@ -107,6 +113,8 @@ struct evol_ctx {
     float *kdk_acc;
     cudaGraphExec_t kdk_exec;
     uint64_t kdk_sig;
+    cudaGraphExec_t run_exec;        // one global-step KDK step (evol_run)
+    uint64_t run_sig;
 };
 
 // ---- host-side launch helpers (defined in evol_api.cu / tree.cu / walks) ------------------
@@ -116,6 +124,8 @@ int evol_launch_walk(evol_ctx *c, const evol_particles *p, const evol_params *pr
 int evol_launch_node_lengths(evol_ctx *c, const evol_params *prm, int n_gas);
 int evol_launch_unpermute(evol_ctx *c, const evol_particles *p, const evol_outputs *o, int what);
 int evol_launch_diagnostics(evol_ctx *c, const evol_particles *p, const evol_params *prm);
+int evol_launch_integrator_step(evol_ctx *c, const evol_particles *p, const evol_params *prm, const evol_integrator *ip,
+                                int stage);
 
 #define EVOL_UNPERM_LENGTHS 1
 #define EVOL_UNPERM_DENSITY 2
@@ -202,4 +212,5 @@ struct evol_kparams {
     int stack_cap;           // traversal-stack entries a warp may use
     int stack_stride;        // entries allocated per warp (>= stack_cap)
     int nsys;
+    int want_divv;           // length solves also form div v
 };

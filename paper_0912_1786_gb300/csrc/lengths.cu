@@ -21,6 +21,8 @@
 //                           zeta = (3 Smw + Smuw)/(3 Sw)          (Sect. 3, Eq. drhodr)
 // Outputs (mode 1, eps):     Upsilon = -Suw/(3 Sw),
 //                           X = -(pi eps^2/(3 Sw)) sum_k m_k eps^2 dphi/deps   (Sect. 2.1)
+// On request, either mode:   div v = 3 sum_j ((v_i - v_j).(r_i - r_j)/r_ij) w'(u) / (L Suw)
+//                           (the discretised continuity equation of Sect. 2.1)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -47,7 +49,7 @@ struct LenSmem {
     int2 gr[LW_WARPS][GCAP];          // leaf particle range [begin, end)
     int hb[LW_WARPS][HCAP + 1];       // listed leaves: exclusive prefix of their particle counts
     int hs[LW_WARPS][HCAP];           // and the first particle of each
-    float2 nb[LW_WARPS][PCAP];        // (distance, mass) of the neighbours of the particle solved
+    float2 nb[LW_WARPS][PCAP];        // (distance, index bits) of the neighbours of the particle solved
     unsigned lc[LW_WARPS][4];         // work counts of the warp's current item (kept by lane 0)
 };
 
@@ -103,7 +105,7 @@ __device__ __forceinline__ int gather_listed(const evol_dev &d, const evol_kpara
             const unsigned bal = __ballot_sync(0xffffffffu, in);
             if (in) {
                 const int e = cnt + __popc(bal & ltmask);
-                if (e < PCAP) nb[e] = make_float2(sqrtf(r2), pj[h].w);
+                if (e < PCAP) nb[e] = make_float2(sqrtf(r2), __int_as_float(jj[h]));
             }
             cnt += __popc(bal);
         }
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                 // A Newton iteration needs Sw and Suw; the last evaluation also needs the
                 // mass-weighted sums of the outputs.
                 const bool last = status == ST_LAST;
-                float Sw = 0.f, Suw = 0.f, S3 = 0.f, S4 = 0.f;
+                float Sw = 0.f, Suw = 0.f, S3 = 0.f, S4 = 0.f, S5 = 0.f;
                 const float Linv = 1.f / L;
                 if (!last) {
                     for (int e = lane; e < cnt; e += 32) {
@@ -545,18 +547,31 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         Suw += u * (-0.75f * a2 + 3.f * b2);                // u w'(u)
                     }
                 } else {
+                    // the neighbours' masses (and, for the continuity equation, positions and
+                    // velocities) are read from the sorted particle state
+                    const float4 vi = kp.want_divv ? d.vel[g * SUB + t] : make_float4(0.f, 0.f, 0.f, 0.f);
                     for (int e = lane; e < cnt; e += 32) {
-                        const float2 rm = nb[e];
-                        const float u = rm.x * Linv;
+                        const float2 rj = nb[e];
+                        const int j = __float_as_int(rj.y);
+                        const float4 pj = d.pos[j];
+                        const float u = rj.x * Linv;
                         float wv, dw;
                         evol_w_dw(u, wv, dw);      // zero for u >= 2
                         Sw += wv;
                         Suw += u * dw;
                         if (MODE == 0) {
-                            S3 += rm.y * wv;                               // Smw
-                            S4 += rm.y * u * dw;                           // Smuw
+                            S3 += pj.w * wv;                               // Smw
+                            S4 += pj.w * u * dw;                           // Smuw
                         } else {
-                            S3 += rm.y * evol_dphideps(u);                 // sum m eps^2 dphi/deps
+                            S3 += pj.w * evol_dphideps(u);                 // sum m eps^2 dphi/deps
+                        }
+                        if (kp.want_divv && rj.x > 0.f) {
+                            // (v_i - v_j).(r_i - r_j) / r  w'(u)  (Sect. 2.1, continuity equation)
+                            const float4 vj = d.vel[j];
+                            const float dx = evol_wrap(px - pj.x, kp.plen[0], kp.periodic_mask & 1);
+                            const float dy = evol_wrap(py - pj.y, kp.plen[1], kp.periodic_mask & 2);
+                            const float dz = evol_wrap(pz - pj.z, kp.plen[2], kp.periodic_mask & 4);
+                            S5 += ((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz) / rj.x * dw;
                         }
                     }
                 }
@@ -567,6 +582,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                     if (last) {
                         S3 += __shfl_xor_sync(0xffffffffu, S3, o);
                         if (MODE == 0) S4 += __shfl_xor_sync(0xffffffffu, S4, o);
+                        if (kp.want_divv) S5 += __shfl_xor_sync(0xffffffffu, S5, o);
                     }
                 }
                 // identical on every lane up to the order of the additions; take lane 0's values
@@ -575,6 +591,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                 if (last) {
                     S3 = __shfl_sync(0xffffffffu, S3, 0);
                     if (MODE == 0) S4 = __shfl_sync(0xffffffffu, S4, 0);
+                    if (kp.want_divv) S5 = __shfl_sync(0xffffffffu, S5, 0);
                 }
                 const float Smw = S3, Smuw = S4;
                 if (status == ST_LAST) {
@@ -593,6 +610,9 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                             d.ups[si] = -Suw / (3.f * Sw);
                             d.X[si] = -EVOL_PI_F * L * L * Smw / (3.f * Sw);
                         }
+                        // div v = -1/(n C) sum_j (v_i - v_j).grad_i W = 3 S5 / (L Suw), C = Upsilon
+                        // or Omega* = -Suw/(3 Sw), n = Sw/(pi L^3), grad W = r_ij/r w'(u)/(pi L^4)
+                        if (kp.want_divv) (MODE == 0 ? d.divv_h : d.divv_e)[si] = 3.f * S5 / (L * Suw);
                     }
                     status = ST_DONE;
                 } else {
@@ -651,6 +671,7 @@ int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params 
     kp.eta_e = 0.5f * cbrtf(3.f * prm->n_nei_grav / (4.f * EVOL_PI_F));
     kp.periodic_mask = prm->periodic_mask;
     for (int a = 0; a < 3; ++a) kp.plen[a] = prm->periodic_hi[a] - prm->periodic_lo[a];
+    kp.want_divv = c->want_divv;
     kp.stack_cap = (int)c->wstack_lim;
     kp.stack_stride = (int)c->wstack_cap;
     unsigned long long *q = c->d.counters + (mode == 0 ? 5 : 6);

@@ -177,6 +177,111 @@ __global__ void k_drift(int n, float dt, float *x, float *y, float *z, const flo
     z[i] = p[2];
 }
 
+// ---- global time step (Sect. 4.2) ------------------------------------------------------
+// Per particle, in the caller's order, the smallest of the criteria
+//   eta_acc sqrt(L/|a|), eta_vel L/|v|, eta_av |v|/|a|          (L = min(eps, h), eps without gas)
+//   eta_C h / (h |div v| + c + 1.2 (alpha c + beta max |mu|)),  eta_u |u / (du/dt)|     (gas)
+// (a criterion with eta = 0, or without a finite positive value, is left out); the minimum over
+// all particles is folded into *dtbits (the bits of a non-negative float order like the float).
+// The sorted-order quantities (c, div v, max |mu|) are read through the inverse permutation.
+struct TsParams {
+    float eta_acc, eta_vel, eta_av, eta_c, eta_u, alpha, beta;
+    int gravity, sph;
+};
+
+__global__ void k_dt_criteria(int n, int n_gas, evol_dev d, TsParams tp, const float *vx, const float *vy,
+                              const float *vz, const float *u, const float *acc, int64_t stride, const float *h,
+                              const float *eps, unsigned *dtbits)
+{
+    float dt = INFINITY;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const float ax = acc[j], ay = acc[stride + j], az = acc[2 * stride + j];
+        const float a = sqrtf(ax * ax + ay * ay + az * az);
+        const float v = sqrtf(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]);
+        const bool gas = tp.sph && j < n_gas;
+        float L = tp.gravity ? eps[j] : INFINITY;
+        if (gas) L = fminf(L, h[j]);
+        float c[5] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY};
+        if (tp.eta_acc > 0.f) c[0] = tp.eta_acc * sqrtf(L / a);
+        if (tp.eta_vel > 0.f) c[1] = tp.eta_vel * L / v;
+        if (tp.eta_av > 0.f) c[2] = tp.eta_av * v / a;
+        if (gas) {
+            const int s = d.inv[j];
+            const float cs = d.snd[s].x, hj = h[j];
+            if (tp.eta_c > 0.f)
+                c[3] = tp.eta_c * hj / (hj * fabsf(d.divv_h[s]) + cs + 1.2f * (tp.alpha * cs + tp.beta * d.mumax[s]));
+            if (tp.eta_u > 0.f) c[4] = tp.eta_u * fabsf(u[j] / acc[3 * stride + j]);
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            if (c[k] > 0.f && c[k] < INFINITY) dt = fminf(dt, c[k]);      // NaN and 0 are left out
+    }
+    for (int o = 16; o > 0; o >>= 1) dt = fminf(dt, __shfl_xor_sync(0xffffffffu, dt, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(dtbits, __float_as_uint(dt));
+}
+
+// dt = the criteria's minimum clamped to [dt_min, dt_max] (dt_max where no criterion applies);
+// the integrator time advances by dt.
+__global__ void k_dt_final(float *dt, const unsigned *dtbits, double *time, float dt_min, float dt_max)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float v = __uint_as_float(*dtbits);
+    v = fminf(v, dt_max);
+    v = fmaxf(v, dt_min);
+    dt[0] = v;
+    *time += (double)v;
+}
+
+// Kick with the device time step: v += f dt a (u += f dt du/dt for gas), caller order.
+__global__ void k_kick_dev(int n, int n_gas, const float *dtp, float f, float *vx, float *vy, float *vz, float *u,
+                           const float *acc, int64_t stride)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float hdt = f * *dtp;
+    vx[i] += hdt * acc[i];
+    vy[i] += hdt * acc[stride + i];
+    vz[i] += hdt * acc[2 * stride + i];
+    if (u && i < n_gas) u[i] += hdt * acc[3 * stride + i];
+}
+
+__global__ void k_drift_dev(int n, const float *dtp, float *x, float *y, float *z, const float *vx, const float *vy,
+                            const float *vz, int pmask, float lo0, float lo1, float lo2, float len0, float len1,
+                            float len2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float dt = *dtp;
+    float p[3] = {x[i] + dt * vx[i], y[i] + dt * vy[i], z[i] + dt * vz[i]};
+    const float lo[3] = {lo0, lo1, lo2}, len[3] = {len0, len1, len2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if ((pmask >> a) & 1) {
+            float t = p[a] - lo[a];
+            t -= len[a] * floorf(t / len[a]);
+            if (t >= len[a]) t -= len[a];
+            if (t < 0.f) t = 0.f;
+            p[a] = lo[a] + t;
+        }
+    x[i] = p[0];
+    y[i] = p[1];
+    z[i] = p[2];
+}
+
+// Starting lengths of the next solve from the continuity equation (Sect. 2.1): dn/dt = -n div v
+// and L ~ n^(-1/3) give L(t + dt) = L exp(div v dt / 3), applied to the solved lengths the caller's
+// arrays hold; div v comes from the last solve (sorted order, through the inverse permutation).
+__global__ void k_predict_lengths(int n, int n_gas, evol_dev d, const float *dtp, float *h, float *eps, int do_h,
+                                  int do_eps)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float k = *dtp * (1.f / 3.f);
+    const int s = d.inv[j];
+    if (do_eps) eps[j] *= __expf(d.divv_e[s] * k);
+    if (do_h && j < n_gas) h[j] *= __expf(d.divv_h[s] * k);
+}
+
 }  // namespace
 
 int evol_launch_kick(evol_ctx *c, const evol_particles *p, float half_dt, const float *ax, const float *ay,
@@ -227,5 +332,40 @@ int evol_launch_diagnostics(evol_ctx *c, const evol_particles *p, const evol_par
     int nb = (int)c->diag_blocks;
     k_diag_partial<<<nb, DG_THREADS, 0, c->stream>>>((int)p->n, (int)p->n_gas, prm->sph, c->d, c->d.diag_part);
     k_diag_final<<<1, 32, 0, c->stream>>>(nb, c->d.diag_part, c->d.nnodes, c->d.counters, c->d.diag);
+    return evol_cuda_ok(cudaGetLastError());
+}
+
+// One global-step KDK step around a force step: stage 0 = time step, first half kick, drift and
+// the predicted starting lengths; stage 1 = the second half kick.  The accelerations and du/dt of
+// the last force step are c->kdk_acc (caller order: ax | ay | az | du/dt, c->cap apart).
+int evol_launch_integrator_step(evol_ctx *c, const evol_particles *p, const evol_params *prm, const evol_integrator *ip,
+                                int stage)
+{
+    const int n = (int)p->n, ng = (int)p->n_gas;
+    const int tb = 256, gb = (n + tb - 1) / tb;
+    const int64_t cap = c->cap;
+    unsigned *dtbits = reinterpret_cast<unsigned *>(c->d.dt + 1);
+    if (stage == 0) {
+        TsParams tp{ip->eta_acc, ip->eta_vel, ip->eta_av, ip->eta_courant, ip->eta_u, prm->alpha, prm->beta,
+                    prm->gravity, prm->sph && p->n_gas > 0};
+        // all bits set: above every non-negative float's bits, so the first criterion replaces it
+        cudaMemsetAsync(dtbits, 0xff, sizeof(unsigned), c->stream);
+        k_dt_criteria<<<c->num_sms * 4, 256, 0, c->stream>>>(n, ng, c->d, tp, p->vx, p->vy, p->vz, p->u, c->kdk_acc,
+                                                              cap, p->h, p->eps, dtbits);
+        k_dt_final<<<1, 32, 0, c->stream>>>(c->d.dt, dtbits, c->d.time, ip->dt_min, ip->dt_max);
+        k_kick_dev<<<gb, tb, 0, c->stream>>>(n, ng, c->d.dt, 0.5f, (float *)p->vx, (float *)p->vy, (float *)p->vz,
+                                             (float *)p->u, c->kdk_acc, cap);
+        k_drift_dev<<<gb, tb, 0, c->stream>>>(
+            n, c->d.dt, (float *)p->x, (float *)p->y, (float *)p->z, p->vx, p->vy, p->vz, prm->periodic_mask,
+            prm->periodic_lo[0], prm->periodic_lo[1], prm->periodic_lo[2], prm->periodic_hi[0] - prm->periodic_lo[0],
+            prm->periodic_hi[1] - prm->periodic_lo[1], prm->periodic_hi[2] - prm->periodic_lo[2]);
+        if (ip->predict_lengths)
+            k_predict_lengths<<<gb, tb, 0, c->stream>>>(n, ng, c->d, c->d.dt, p->h, p->eps,
+                                                        prm->sph && ng > 0 && p->h != nullptr,
+                                                        prm->gravity && prm->adaptive_softening);
+    } else {
+        k_kick_dev<<<gb, tb, 0, c->stream>>>(n, ng, c->d.dt, 0.5f, (float *)p->vx, (float *)p->vy, (float *)p->vz,
+                                             (float *)p->u, c->kdk_acc, cap);
+    }
     return evol_cuda_ok(cudaGetLastError());
 }

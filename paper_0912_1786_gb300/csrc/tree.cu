@@ -292,14 +292,27 @@ __global__ void k_permute(int n, int n_gas, const int32_t *__restrict__ perm, co
                           const float *__restrict__ vy, const float *__restrict__ vz, const float *__restrict__ m,
                           const float *__restrict__ u, const float *__restrict__ h, const float *__restrict__ eps,
                           float4 *__restrict__ pos, float4 *__restrict__ vel, float *__restrict__ lh,
-                          float *__restrict__ le, int32_t *__restrict__ orig, int32_t *__restrict__ inv)
+                          float *__restrict__ le, int32_t *__restrict__ orig, int32_t *__restrict__ inv,
+                          const float *__restrict__ pred_dt, const float *__restrict__ pred_acc, int64_t stride)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int j = perm[s];
     bool gas = j < n_gas;
     pos[s] = make_float4(x[j], y[j], z[j], m[j]);
-    vel[s] = make_float4(vx ? vx[j] : 0.f, vy ? vy[j] : 0.f, vz ? vz[j] : 0.f, (gas && u) ? u[j] : 0.f);
+    float4 v = make_float4(vx ? vx[j] : 0.f, vy ? vy[j] : 0.f, vz ? vz[j] : 0.f, (gas && u) ? u[j] : 0.f);
+    if (pred_dt) {
+        // integrator: the force step sees the velocity and internal energy predicted to the end of
+        // the step, v_n + a_n dt and u_n + (du/dt)_n dt (Sect. 4.1); the caller's arrays hold the
+        // half-kicked values, so half a step of the previous accelerations (pred_acc: ax | ay | az |
+        // du/dt in the caller's order, `stride` apart) is added
+        const float hdt = 0.5f * *pred_dt;
+        v.x += hdt * pred_acc[j];
+        v.y += hdt * pred_acc[stride + j];
+        v.z += hdt * pred_acc[2 * stride + j];
+        if (gas && u) v.w += hdt * pred_acc[3 * stride + j];
+    }
+    vel[s] = v;
     lh[s] = (gas && h) ? h[j] : 0.f;
     le[s] = eps ? eps[j] : 0.f;
     orig[s] = j;
@@ -922,7 +935,8 @@ int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *p
                                          va == d.vals_a ? nullptr : d.vals_a);
     }
     k_permute<<<gb, tb, 0, st>>>(n, (int)p->n_gas, d.vals_a, p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->u,
-                                 p->h, p->eps, d.pos, d.vel, d.len_h, d.len_eps, d.orig, d.inv);
+                                 p->h, p->eps, d.pos, d.vel, d.len_h, d.len_eps, d.orig, d.inv,
+                                 c->pred_dt, c->kdk_acc, c->cap);
     k_lcp<<<gb, tb, 0, st>>>(n, d.keys_a, d.sys_off, nsys, d.lcp, d.sys_sorted);
     k_count<<<gb, tb, 0, st>>>(n, d.lcp, leaf, d.cnt);
     int rc = scan_i32(c, n, d.cnt, d.base, 1);

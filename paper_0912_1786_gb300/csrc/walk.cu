@@ -59,6 +59,7 @@ struct WalkSmem {
     int norig[WK_WARPS][NEARCAP];
     float4 gbox[WK_WARPS][3];     // group bounds: centre, 0 | half widths, 0 | emax, emin, hmax, hmin
     unsigned wc[WK_WARPS][8];     // per-group work counts kept by lane 0 (see the end of k_walk)
+    float mum[WK_WARPS][32];      // largest |mu_ij| of each lane's particle (viscosity)
 };
 
 // The kernel functions of the pair loop in a division-free form: each takes u and iu = 1/u (iu is
@@ -248,6 +249,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
         // [3], tested lane by lane [4]; leaves [5] and internal nodes [6] opened
         unsigned *wc = sm.wc[w];
         if (lane < 8) wc[lane] = 0u;
+        if (SPH) sm.mum[w][lane] = 0.f;
         __syncwarp();
 
         auto fold = [&]() {
@@ -471,6 +473,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                                 if (vr < 0.f) {
                                     const float hb = 0.5f * (gi.z + gj.z);
                                     const float mu = hb * vr * rcp_fast(r2 + 0.01f * hb * hb);
+                                    sm.mum[w][lane] = fmaxf(sm.mum[w][lane], -mu);    // |mu| (vr < 0)
                                     const float cb = 0.5f * (si.x + sj.x);
                                     const float rb = 0.5f * (si.y + sj.y);
                                     visc = (-kp.alpha * cb * mu + kp.beta * mu * mu) * rcp_fast(rb);
@@ -755,6 +758,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
             d.acc[s] = make_float4(ax, ay, az, pot);
             if (SPH) {
                 d.dudt[s] = gas_i ? (float)tdu : 0.f;
+                d.mumax[s] = gas_i ? sm.mum[w][lane] : 0.f;
                 const float4 hv = d.hydro[s];
                 d.vah[s] = gas_i ? (float)(hv.x * thx + hv.y * thy + hv.z * thz) : 0.f;
             }

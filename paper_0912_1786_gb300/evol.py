@@ -17,7 +17,7 @@ EVOL_OK, EVOL_EINVAL, EVOL_ENOMEM, EVOL_ECUDA = 0, -1, -2, -3
 EVOL_EOVERFLOW, EVOL_ENOCONV, EVOL_ETIMEOUT, EVOL_ENAN, EVOL_ESTATE = -4, -5, -6, -7, -8
 EVOL_FP32_PLAIN, EVOL_FP32_MIXED = 0, 1
 EVOL_DBG_KEYS, EVOL_DBG_PERM, EVOL_DBG_NODES, EVOL_DBG_CUBE = 1, 2, 3, 4
-EVOL_DBG_MOMENTS, EVOL_DBG_HASHES, EVOL_DBG_COUNTS = 5, 6, 7
+EVOL_DBG_MOMENTS, EVOL_DBG_HASHES, EVOL_DBG_COUNTS, EVOL_DBG_FLOW = 5, 6, 7, 8
 
 _fp = C.POINTER(C.c_float)
 
@@ -36,6 +36,12 @@ class EvolParams(C.Structure):
                 ("use_tc_gradient", C.c_int), ("periodic_mask", C.c_int),
                 ("periodic_lo", C.c_float * 3), ("periodic_hi", C.c_float * 3),
                 ("precision", C.c_int), ("leaf_size", C.c_int), ("group_size", C.c_int)]
+
+
+class EvolIntegrator(C.Structure):
+    _fields_ = [("eta_acc", C.c_float), ("eta_vel", C.c_float), ("eta_av", C.c_float), ("eta_courant", C.c_float),
+                ("eta_u", C.c_float), ("dt_min", C.c_float), ("dt_max", C.c_float),
+                ("predicted_velocity", C.c_int), ("predict_lengths", C.c_int)]
 
 
 class EvolOutputs(C.Structure):
@@ -68,6 +74,8 @@ def lib():
         L.evol_autotune.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs), C.POINTER(C.c_int),
                                      C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
         L.evol_kdk.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs), C.c_float, C.c_int]
+        L.evol_run.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolIntegrator), pp(EvolOutputs), C.c_int,
+                               pp(C.c_double), pp(C.c_float)]
         L.evol_sync.argtypes = [vp]
         L.evol_get_diagnostics.argtypes = [vp, pp(C.c_double)]
         L.evol_get_timings.argtypes = [vp, pp(C.c_float)]
@@ -204,6 +212,26 @@ def evol_kdk(ctx, particles, params, outputs, dt: float, nsteps: int):
     """Fixed-step kick-drift-kick; updates the particle arrays in place (device tensors)."""
     return _check(lib().evol_kdk(ctx, C.byref(particles), C.byref(params), C.byref(outputs), float(dt), int(nsteps)),
                   "evol_kdk")
+
+
+def make_integrator(eta_acc=0.1, eta_vel=0.0, eta_av=0.0, eta_courant=0.1, eta_u=0.1, dt_min=0.0, dt_max=1.0,
+                    predicted_velocity=1, predict_lengths=1) -> EvolIntegrator:
+    e = EvolIntegrator()
+    e.eta_acc, e.eta_vel, e.eta_av, e.eta_courant, e.eta_u = (float(eta_acc), float(eta_vel), float(eta_av),
+                                                              float(eta_courant), float(eta_u))
+    e.dt_min, e.dt_max = float(dt_min), float(dt_max)
+    e.predicted_velocity, e.predict_lengths = int(predicted_velocity), int(predict_lengths)
+    return e
+
+
+def evol_run(ctx, particles, params, integrator, outputs, nsteps: int, time: float = 0.0):
+    """Global-time-step KDK on the device; updates the particle arrays in place.  Returns
+    (time after the steps, last time step)."""
+    t = C.c_double(float(time))
+    dt = C.c_float()
+    _check(lib().evol_run(ctx, C.byref(particles), C.byref(params), C.byref(integrator), C.byref(outputs),
+                          int(nsteps), C.byref(t), C.byref(dt)), "evol_run")
+    return t.value, dt.value
 
 
 def evol_sync(ctx, raise_on_error=True):
