@@ -285,6 +285,34 @@ def form_errors(g, ref, idx, w):
     return e
 
 
+def plummer_checks(w, g, ostate, dist_seed=12, nsample=1024):
+    """Context for the Plummer sphere (G = M = a = 1): shell averages of the radial acceleration
+    against the closed form -r (1 + r^2)^(-3/2) with their Poisson noise, and the tree's error
+    against the oracle's direct sum (theta = 0) on a seeded sample."""
+    import copy
+    P = np.stack([w.x, w.y, w.z], 1).astype(np.float64)
+    a = np.stack([g["ax"], g["ay"], g["az"]], 1)
+    r = np.linalg.norm(P, axis=1)
+    ar = (a * P).sum(1) / r
+    shells = []
+    edges = np.array([0.2, 0.4, 0.7, 1.0, 1.5, 2.5, 4.0])
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = (r >= lo) & (r < hi)
+        rs = r[sel]
+        cf = np.mean(-rs * (1 + rs ** 2) ** -1.5)
+        shells.append({"r": [float(lo), float(hi)], "count": int(sel.sum()),
+                       "rel_diff": float(abs(ar[sel].mean() - cf) / abs(cf)), "poisson": float(1 / np.sqrt(sel.sum()))})
+    p0 = copy.copy(w.params)
+    p0.theta = 0.0
+    idx = np.sort(np.random.default_rng(dist_seed).choice(w.n, min(w.n, nsample), replace=False))
+    ref = ostate[0].forces(p0, ostate[1], idx=idx)
+    ad = np.stack([ref["ax"], ref["ay"], ref["az"]], 1)[idx]
+    e = np.linalg.norm(a[idx] - ad, axis=1) / np.linalg.norm(ad, axis=1)
+    return {"closed_form_shells": shells,
+            "tree_vs_direct_sum": {"median": float(np.median(e)), "p99": float(np.percentile(e, 99)),
+                                   "n": int(len(idx)), "theta": float(w.params.theta)}}
+
+
 def gpu_check_step(E, ctx, ds, offsets=None):
     """One more step with interaction-set hashes recorded; caller-order numpy results."""
     E.evol_set_check_mode(ctx, True)
@@ -410,6 +438,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--leaf", type=int, default=0, help="fixed leaf size (skips the autotune)")
     ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--theta", type=float, default=None, help="opening angle (overrides the workload's)")
+    ap.add_argument("--kdk-steps", type=int, default=0,
+                    help="time this many fixed-step KDK steps (one captured graph) per bench step")
+    ap.add_argument("--kdk-dt", type=float, default=1e-4)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -436,6 +468,9 @@ def main():
     build.build()
 
     w, wname = make_workload(args.workload)
+    if args.theta is not None:
+        w.params.theta = float(args.theta)
+        wname = f"{wname.split('_theta')[0]}_theta{args.theta:g}" if "theta" in wname else f"{wname}_theta{args.theta:g}"
     prec = E.EVOL_FP32_MIXED if args.precision == "mixed" else E.EVOL_FP32_PLAIN
     ds = DeviceSet(w, device=str(dev), precision=prec)
     stream = torch.cuda.current_stream(dev)
@@ -450,7 +485,16 @@ def main():
 
     offsets = [int(v) for v in w.sys_offsets] if w.sys_offsets is not None else None
 
+    kdk_initial = {k: t.clone() for k, t in ds.inp.items()} if args.kdk_steps > 0 else None
+
     def one_step():
+        if args.kdk_steps > 0:
+            # a leapfrog run of kdk_steps steps from the initial state (restored on the device: the
+            # state evolves in place and lengths carry over from step to step within the run)
+            for k, t in kdk_initial.items():
+                ds.inp[k].copy_(t, non_blocking=True)
+            E.evol_kdk(ctx, ds.particles, ds.params, ds.outputs, args.kdk_dt, args.kdk_steps)
+            return
         ds.reset_lengths()
         if offsets is not None:
             E.evol_step_batched(ctx, offsets, ds.particles, ds.params, ds.outputs)
@@ -487,14 +531,15 @@ def main():
         dist.barrier()
     ms = t_start.elapsed_time(t_end)
     clocks = sampler.stop()
-    value, ms_max = replica_rate(dist, dev, ms, w.n, args.steps, world)
+    units = w.n * max(args.kdk_steps, 1)          # particles (x KDK steps) per bench step
+    value, ms_max = replica_rate(dist, dev, ms, units, args.steps, world)
     diag = E.evol_get_diagnostics(ctx)
     cnt = E.evol_get_counters(ctx)               # work counters of the last timed step
     n_total = w.n * world
 
     # ---- e2e through the host-buffer entry point (pinned host memory) ----
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.kdk_steps == 0:
         host_in = {}
         for k, a in w.arrays().items():
             t = torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
@@ -563,6 +608,8 @@ def main():
             for name, g in results.items():
                 accuracy[name] = form_errors(g, ref, sidx, w)
             accuracy["sample"] = f"{len(sidx)} particles (seed 11), oracle leaf {int(ds.params.leaf_size)}"
+            if args.workload == "c2":
+                accuracy["plummer"] = plummer_checks(w, g_main, ostate, dist_seed=12)
         # the forms against each other
         A = lambda x: np.stack([x["ax"], x["ay"], x["az"]], 1)
         for name, g in results.items():
@@ -600,12 +647,15 @@ def main():
 
     E.evol_destroy(ctx)
     if rank == 0:
-        line = {"metric": "force-step particles/s (tree gravity+SPH)", "value": value, "unit": "particles/s",
+        metric = ("KDK particle-steps/s (fixed step, one captured graph)" if args.kdk_steps > 0
+                  else "force-step particles/s (tree gravity+SPH)")
+        line = {"metric": metric, "value": value, "unit": "particle-steps/s" if args.kdk_steps > 0 else "particles/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "precision": args.precision, "data": "synthetic",
                 "config": {"workload": wname, "n": w.n, "n_gas": w.n_gas, "theta": w.params.theta,
                            "n_nei": w.params.n_nei_sph, "leaf_size": int(ds.params.leaf_size),
+                           "kdk_steps_per_bench_step": args.kdk_steps or None,
                 "autotune": autotune,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "working set > L2 (inputs 40 B/particle x 3.1M + tree), no flush"},
@@ -622,7 +672,8 @@ def main():
                 "forms_accuracy": accuracy,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": None}
-        line["gpu_launches"] = launches_per_step(w) * args.steps
+        lps = launches_per_step(w)
+        line["gpu_launches"] = (lps + args.kdk_steps * (lps + 3)) * args.steps if args.kdk_steps else lps * args.steps
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
