@@ -16,7 +16,9 @@
  * its softening derivative (Eq. dphidh), n the number density (Eq. rho0 / Eq. nsum),
  * eps = eta n^{-1/3} (Eq. etan), h = eta n^{-1/3} (Eq. hn), Upsilon/xi the adaptive
  * softening correction terms (Sect. 2.1), Omega* and zeta the variable-mass grad-h terms
- * (Sect. 3, Eq. drhodr), Pi the Monaghan artificial viscosity (Eq. mu_visc).
+ * (Sect. 3, Eq. drhodr), Pi the Monaghan artificial viscosity (Eq. mu_visc) or its signal-velocity
+ * form (Eqs. pvsig, vsig) with the Balsara limiter and per-particle alpha, Pi^u the artificial
+ * conductivity (Sect. 3.3.3).
  */
 #include <math.h>
 #include <stdint.h>
@@ -602,6 +604,11 @@ int orc_solve_lengths(const orc_tree *t, int mode, double n_nei, const int64_t *
 /* Velocity divergence at every listed particle from the discretised continuity equation
  * (Sect. 2.1, the equations below Eq. continuity): with n_i = sum_j W(r_ij, L_i),
  *     div v_i = -1/(n_i C_i) sum_j (v_i - v_j) . grad_i W(r_ij, L_i),
+ * and, when curl != NULL, the magnitude of the curl from the same neighbour sum (the rotational
+ * part of the velocity field that the Balsara limiter of Sect. 3.3.3 needs):
+ *     curl v_i = +1/(n_i C_i) sum_j (v_i - v_j) x grad_i W(r_ij, L_i)
+ * (for v = w x r the sum gives 2 w, for v = k r it gives -3 k in div v; the signs follow from
+ * the kernel's second moment, sum_j (1/n) x_a x_b dW/dr / r = -delta_ab),
  * where L is the particle's solved length and C its correction factor: Upsilon for the softening
  * (mode 1, all species) and Omega* for the smoothing length (mode 0, gas neighbours of gas).
  * grad_i W = (r_i - r_j)/r dW/dr with the exact spline derivative.  L, nsum, corr: original order
@@ -609,7 +616,7 @@ int orc_solve_lengths(const orc_tree *t, int mode, double n_nei, const int64_t *
  * NULL).  Returns 0, or -3 on neighbour overflow. */
 int orc_divv(const orc_tree *t, int mode, const double *L, const double *nsum, const double *corr,
              const double *vx, const double *vy, const double *vz, const int64_t *idx, int64_t nidx,
-             int periodic_mask, const double *plo, const double *phi_, double *divv)
+             int periodic_mask, const double *plo, const double *phi_, double *divv, double *curl)
 {
     orc_period per = {periodic_mask, {0, 0, 0}, {1, 1, 1}};
     for (int a = 0; a < 3; ++a)
@@ -631,17 +638,22 @@ int orc_divv(const orc_tree *t, int mode, const double *L, const double *nsum, c
                 if (!err) err = -3;
                 continue;
             }
-            double s = 0.0;
+            double s = 0.0, cv[3] = {0.0, 0.0, 0.0};
             for (int64_t k = 0; k < cnt; ++k) {
                 int64_t j = scr[k];
                 double r = rs[k];
                 if (j == i || r <= 0.0) continue;
                 double rv[3] = {orc_wrap(&per, 0, p[0] - t->x[j]), orc_wrap(&per, 1, p[1] - t->y[j]),
                                 orc_wrap(&per, 2, p[2] - t->z[j])};
-                double vr = (vx[i] - vx[j]) * rv[0] + (vy[i] - vy[j]) * rv[1] + (vz[i] - vz[j]) * rv[2];
-                s += vr / r * orc_dWdr(r, L[i]);
+                double dv[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
+                double g = orc_dWdr(r, L[i]) / r;           /* grad_i W = r_vec g */
+                s += (dv[0] * rv[0] + dv[1] * rv[1] + dv[2] * rv[2]) * g;
+                cv[0] += (dv[1] * rv[2] - dv[2] * rv[1]) * g;
+                cv[1] += (dv[2] * rv[0] - dv[0] * rv[2]) * g;
+                cv[2] += (dv[0] * rv[1] - dv[1] * rv[0]) * g;
             }
             divv[i] = -s / (nsum[i] * corr[i]);
+            if (curl) curl[i] = sqrt(cv[0] * cv[0] + cv[1] * cv[1] + cv[2] * cv[2]) / (nsum[i] * corr[i]);
         }
         free(scr);
         free(rs);
@@ -655,9 +667,24 @@ int orc_divv(const orc_tree *t, int mode, const double *L, const double *nsum, c
 /* softening correction, and SPH pressure + viscosity + du/dt on the same near list.       */
 /* ------------------------------------------------------------------------------------ */
 
+/* Dissipation variants of Sect. 3.3.3 (all off: the standard Monaghan viscosity with constant
+ * alpha and beta).  Per-particle inputs in original order. */
+typedef struct {
+    int form;             /* 0: Monaghan (Eq. mu_visc); 1: signal velocity (Eqs. pvsig, vsig) */
+    int balsara;          /* 1: Pi_ij multiplied by (f_i + f_j)/2, the Balsara limiter */
+    int var_alpha;        /* 1: alpha_ij = (alpha_i + alpha_j)/2 (Eq. alphaswitch) */
+    int conduction;       /* 1: the artificial conductivity Pi^u_ij */
+    int cond_vsig;        /* signal speed of Pi^u: 0 as Eq. vsig, 1 sqrt(|P_i - P_j| / rho_ij) */
+    const double *f;      /* Balsara factor f_i (balsara) */
+    const double *alpha;  /* alpha_i (var_alpha) */
+    const double *alpha_u;/* alpha^u_i (conduction) */
+    const double *u;      /* specific internal energy u_i (conduction) */
+} orc_diss;
+
 typedef struct {
     double theta, G, gamma, alpha, beta;
     int gravity, sph, adaptive, use_tc;
+    orc_diss ds;
 } orc_params;
 
 /* Per-particle state needed by the force pass (original order, length n).  Fields of species
@@ -694,6 +721,8 @@ typedef struct {
     double scale;       /* max |coordinate| of the particle: the scale of FP32 position rounding */
     double aabs, duabs; /* sums of the magnitudes of the individual contributions to a and du/dt */
     double mumax;       /* largest |mu_ij| of the viscosity over the SPH neighbours */
+    double vsig;        /* largest signal velocity v^sig_ij over the SPH neighbours */
+    double lapu;        /* Brookshaw estimate of the Laplacian of u (conduction only) */
 } orc_result;
 
 /* Distance of one decision (value v against threshold thr) from its threshold.  It is taken
@@ -747,15 +776,28 @@ static void orc_pair(const orc_tree *t, const orc_params *pr, const orc_state *s
                 double Pj_ = st->P[j] / (st->rho[j] * st->rho[j]);
                 double v[3] = {st->vx[i] - st->vx[j], st->vy[i] - st->vy[j], st->vz[i] - st->vz[j]};
                 double vr = v[0] * rv[0] + v[1] * rv[1] + v[2] * rv[2];
-                /* Monaghan viscosity (Eq. mu_visc): mu = hbar v.r / (r^2 + 0.01 hbar^2). */
+                const orc_diss *ds = &pr->ds;
+                double w = vr / r;                                  /* w_ij = v_ij . r_ij / |r_ij| */
+                double cb = 0.5 * (st->c[i] + st->c[j]);
+                double rb = 0.5 * (st->rho[i] + st->rho[j]);
+                /* Eq. vsig, v^sig = 2 cbar - w.  Reading: w enters only where the pair approaches
+                 * (w < 0), so that v^sig >= c_i + c_j for every pair; for approaching pairs, the only
+                 * ones the viscosity acts on, this is the printed form. */
+                double vsig = 2.0 * cb - (w < 0 ? w : 0.0);
+                if (vsig > res->vsig) res->vsig = vsig;
+                double al = ds->var_alpha ? 0.5 * (ds->alpha[i] + ds->alpha[j]) : pr->alpha;
+                /* Monaghan viscosity (Eq. mu_visc): mu = hbar v.r / (r^2 + 0.01 hbar^2); mu is formed
+                 * in both forms, its largest |mu| enters the Courant criterion. */
                 double Pi_visc = 0;
                 if (vr < 0) {
                     double hb = 0.5 * (hi + hj);
                     double mu = hb * vr / (r2 + 0.01 * hb * hb);
                     if (fabs(mu) > res->mumax) res->mumax = fabs(mu);
-                    double cb = 0.5 * (st->c[i] + st->c[j]);
-                    double rb = 0.5 * (st->rho[i] + st->rho[j]);
-                    Pi_visc = (-pr->alpha * cb * mu + pr->beta * mu * mu) / rb;
+                    if (ds->form == 0)
+                        Pi_visc = (-al * cb * mu + pr->beta * mu * mu) / rb;
+                    else
+                        Pi_visc = -al * vsig * w / rb;              /* Eq. pvsig */
+                    if (ds->balsara) Pi_visc *= 0.5 * (ds->f[i] + ds->f[j]);
                 }
                 /* grad_i W_ij(h) = dW/dr * r_vec / r; mean gradient with grad-h factors. */
                 double gbar = 0.5 * (gi * fi + gj * fj);
@@ -771,6 +813,23 @@ static void orc_pair(const orc_tree *t, const orc_params *pr, const orc_state *s
                  * viscous heating 1/2 Pi v_ij . gradbar W >= 0. */
                 res->dudt += mj * (Pi_ * fi * gi + 0.5 * Pi_visc * gbar) * vr / r;
                 res->duabs += fabs(mj * (Pi_ * fi * gi + 0.5 * Pi_visc * gbar) * vr / r);
+                if (ds->conduction) {
+                    /* Artificial conductivity (Sect. 3.3.3):
+                     *   Pi^u_ij = -alphabar^u_ij v^u_sig (u_i - u_j) / rhobar_ij,
+                     * added to du_i/dt as m_j Pi^u_ij |gradbar W_ij|.  Reading: the printed factor
+                     * w_ij on Pi^u is left out; with it the term would not have the units of du/dt
+                     * (Pi^u carries a velocity cubed over a density), and heat would flow from cold to
+                     * hot for approaching pairs.  Without it the term moves heat from the hotter
+                     * particle of a pair to the colder one and conserves sum_i m_i u_i. */
+                    double du_ = ds->u[i] - ds->u[j];
+                    double vu = ds->cond_vsig == 0 ? vsig : sqrt(fabs(st->P[i] - st->P[j]) / rb);
+                    double au = 0.5 * (ds->alpha_u[i] + ds->alpha_u[j]);
+                    double Piu = -au * vu * du_ / rb;
+                    res->dudt += mj * Piu * fabs(gbar);
+                    res->duabs += fabs(mj * Piu * gbar);
+                    /* Brookshaw's Laplacian, as printed: sum_j 2 m_j (u_i - u_j)/rho_j |gradbar W_ij| / r */
+                    res->lapu += 2.0 * mj * du_ / st->rho[j] * fabs(gbar) / r;
+                }
             }
         }
     }
@@ -877,9 +936,11 @@ void orc_forces(orc_tree *t, double theta, double G, double gamma, double alpha,
                 double *ax, double *ay, double *az, double *pot, double *dudt,
                 uint64_t *hfar, uint64_t *hnear, uint64_t *hsph,
                 int64_t *nfar, int64_t *npp, int64_t *nsph, double *margin,
-                double *aabs, double *duabs, double *mumax)
+                double *aabs, double *duabs, double *mumax,
+                const orc_diss *diss, double *vsig, double *lapu)
 {
-    orc_params pr = {theta, G, gamma, alpha, beta, gravity, sph, adaptive, use_tc};
+    orc_params pr = {theta, G, gamma, alpha, beta, gravity, sph, adaptive, use_tc, {0}};
+    if (diss) pr.ds = *diss;
     orc_state st = {vx, vy, vz, eps, ups, X, h, rho, P, c, om, zeta};
     orc_period per = {periodic_mask, {0, 0, 0}, {1, 1, 1}};
     for (int a = 0; a < 3; ++a)
@@ -904,6 +965,10 @@ void orc_forces(orc_tree *t, double theta, double G, double gamma, double alpha,
         if (aabs) aabs[i] = res.aabs;
         if (duabs) duabs[i] = res.duabs;
         if (mumax) mumax[i] = res.mumax;
+        /* the self pair (w = 0) bounds v^sig_i from below by 2 c_i, also for a particle without
+         * neighbours */
+        if (vsig) vsig[i] = (sph && i < t->n_gas && c) ? fmax(res.vsig, 2.0 * c[i]) : 0.0;
+        if (lapu) lapu[i] = res.lapu;
     }
 }
 

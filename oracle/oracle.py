@@ -67,10 +67,11 @@ def lib():
                                         _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, C.c_void_p]
         L.orc_forces.argtypes = ([C.c_void_p, d, d, d, d, d, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                   _f64p, _f64p] + [_f64p] * 3 + [_f64p] * 3 + [_f64p] * 6 +
-                                 [C.c_void_p, C.c_int64] + [_f64p] * 5 + [C.c_void_p] * 10)
+                                 [C.c_void_p, C.c_int64] + [_f64p] * 5 + [C.c_void_p] * 10 +
+                                 [C.c_void_p] * 3)
         L.orc_divv.restype = C.c_int
         L.orc_divv.argtypes = [C.c_void_p, C.c_int, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, C.c_void_p,
-                               C.c_int64, C.c_int, _f64p, _f64p, _f64p]
+                               C.c_int64, C.c_int, _f64p, _f64p, _f64p, C.c_void_p]
         L.orc_eos.argtypes = [C.c_int64, d, _f64p, _f64p, _f64p, _f64p]
         L.orc_num_threads.restype = C.c_int
         _lib = L
@@ -107,6 +108,13 @@ def eta_from_nnei(n_nei: float) -> float:
 
 def hash_id(i: int) -> int:
     return int(lib().orc_hash_id(int(i)))
+
+
+class _Diss(C.Structure):
+    # the dissipation-variant block of the force pass (orc_diss in evol_oracle.c)
+    _fields_ = [("form", C.c_int), ("balsara", C.c_int), ("var_alpha", C.c_int), ("conduction", C.c_int),
+                ("cond_vsig", C.c_int), ("f", C.c_void_p), ("alpha", C.c_void_p), ("alpha_u", C.c_void_p),
+                ("u", C.c_void_p)]
 
 
 def _c(a, dt):
@@ -185,9 +193,21 @@ class OracleTree:
         return outs
 
     def forces(self, params, state: dict, idx=None, use_tc=None):
+        """Force pass.  The dissipation variants of Sect. 3.3.3 are taken from params (visc_form,
+        balsara, variable_alpha, conduction, cond_vsig; all 0 by default) with the per-particle
+        arrays state["f"] (Balsara factor), state["alpha"], state["alpha_u"] and state["u"]."""
         n = self.n
         z = np.zeros(n)
         g = lambda k: _c(state.get(k, z), np.float64)
+        ds = _Diss()
+        ds.form = int(getattr(params, "visc_form", 0))
+        ds.balsara = int(getattr(params, "balsara", 0))
+        ds.var_alpha = int(getattr(params, "variable_alpha", 0))
+        ds.conduction = int(getattr(params, "conduction", 0))
+        ds.cond_vsig = int(getattr(params, "cond_vsig", 0))
+        keep = {k: g(k) for k in ("f", "alpha", "alpha_u", "u")}
+        ds.f, ds.alpha, ds.alpha_u, ds.u = (keep[k].ctypes.data for k in ("f", "alpha", "alpha_u", "u"))
+        vsig, lapu = np.zeros(n), np.zeros(n)
         pm, lo, hi = self._period(params)
         ix = _c(idx, np.int64) if idx is not None else None
         out = [np.zeros(n) for _ in range(5)]
@@ -203,7 +223,8 @@ class OracleTree:
                          g("h"), g("rho"), g("P"), g("c"), g("omega"), g("zeta"),
                          ix.ctypes.data if ix is not None else None, int(len(ix)) if ix is not None else 0,
                          *out, *[a.ctypes.data for a in hashes], *[a.ctypes.data for a in counts],
-                         margin.ctypes.data, aabs.ctypes.data, duabs.ctypes.data, mumax.ctypes.data)
+                         margin.ctypes.data, aabs.ctypes.data, duabs.ctypes.data, mumax.ctypes.data,
+                         C.addressof(ds), vsig.ctypes.data, lapu.ctypes.data)
         res = dict(zip(("ax", "ay", "az", "pot", "dudt"), out))
         res.update(zip(("hfar", "hnear", "hsph"), hashes))
         res.update(zip(("nfar", "npp", "nsph"), counts))
@@ -211,23 +232,27 @@ class OracleTree:
         res["aabs"] = aabs
         res["duabs"] = duabs
         res["mumax"] = mumax
+        res["vsig"] = vsig
+        res["lapu"] = lapu
         return res
 
-    def divv(self, mode: int, L, nsum, corr, vx, vy, vz, idx=None, params=None):
+    def divv(self, mode: int, L, nsum, corr, vx, vy, vz, idx=None, params=None, curl=False):
         """Velocity divergence from the discretised continuity equation (Sect. 2.1): mode 1 with the
         softening kernel over all species (corr = Upsilon), mode 0 with the smoothing kernel over
-        the gas (corr = Omega*).  Arrays in original order; returns div v (original order)."""
+        the gas (corr = Omega*).  Arrays in original order; returns div v (original order), and with
+        curl=True also |curl v| from the same neighbour sum."""
         n = self.n
         out = np.zeros(n)
+        cv = np.zeros(n) if curl else None
         pm, lo, hi = self._period(params)
         ix = _c(idx, np.int64) if idx is not None else None
         rc = lib().orc_divv(self.ptr, int(mode), _c(L, np.float64), _c(nsum, np.float64), _c(corr, np.float64),
                             _c(vx, np.float64), _c(vy, np.float64), _c(vz, np.float64),
                             ix.ctypes.data if ix is not None else None, int(len(ix)) if ix is not None else 0,
-                            pm, lo, hi, out)
+                            pm, lo, hi, out, cv.ctypes.data if curl else None)
         if rc != 0:
             raise RuntimeError(f"oracle divergence failed (code {rc})")
-        return out
+        return (out, cv) if curl else out
 
 
 def force_step(w, params=None, idx=None, use_tc=None, tree=None, fixed_lengths=None):
@@ -262,12 +287,89 @@ def force_step(w, params=None, idx=None, use_tc=None, tree=None, fixed_lengths=N
         if p.gravity and p.adaptive_softening:
             res["divv_eps"] = t.divv(1, eps, neps, ups, st["vx"], st["vy"], st["vz"], params=p)
         if p.sph and w.n_gas > 0:
-            res["divv_h"] = t.divv(0, h, nh, om, st["vx"], st["vy"], st["vz"], idx=gidx, params=p)
+            res["divv_h"], res["curlv_h"] = t.divv(0, h, nh, om, st["vx"], st["vy"], st["vz"], idx=gidx,
+                                                   params=p, curl=True)
+    diss = p.sph and w.n_gas > 0 and _dissipation_on(p)
+    if diss:
+        st.update(_dissipation_state(w, p, res, st))
+        res["balsara_f"] = st["f"]
     f = t.forces(p, st, idx=idx, use_tc=use_tc)
     res.update(f)
+    if diss:
+        res.update(_dissipation_rates(w, p, res, st))
     res["tree"] = t
     res["state"] = st
     return res
+
+
+def _dissipation_on(p) -> bool:
+    return bool(getattr(p, "visc_form", 0) or getattr(p, "balsara", 0) or getattr(p, "variable_alpha", 0)
+                or getattr(p, "conduction", 0))
+
+
+def _dissipation_state(w, p, res, st):
+    """Per-particle inputs of the dissipation variants (Sect. 3.3.3), original order, gas only.
+
+    Balsara limiter: f_i = |div v_i| / (|div v_i| + |curl v_i| + eta_B c_i / h_i), div v and curl v
+    from the smoothing-kernel neighbour sums.  Reading: f_i = 0 where the denominator vanishes (a
+    particle at rest relative to its neighbours with u_i = 0).  alpha_i and alpha^u_i come with the
+    particles; without them the constant alpha (and alpha^u = 0) is used."""
+    n, ng = w.n, w.n_gas
+    f = np.zeros(n)
+    zero = np.zeros(n)
+    dv = np.abs(res.get("divv_h", st.get("divv_h", zero))[:ng])
+    cv = res.get("curlv_h", st.get("curlv_h", zero))[:ng]
+    den = dv + cv + float(getattr(p, "balsara_eta", 1e-4)) * st["c"][:ng] / st["h"][:ng]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        f[:ng] = np.where(den > 0, dv / den, 0.0)
+    alpha = np.full(n, float(p.alpha))
+    a_in = getattr(w, "alpha", None)
+    if a_in is not None:
+        alpha[:ng] = np.asarray(a_in, np.float64)[:ng]
+    alpha_u = np.zeros(n)
+    au_in = getattr(w, "alpha_u", None)
+    if au_in is not None:
+        alpha_u[:ng] = np.asarray(au_in, np.float64)[:ng]
+    u = np.zeros(n)
+    u[:ng] = np.asarray(w.u, np.float64)[:ng]
+    out = {"f": f, "alpha": alpha, "alpha_u": alpha_u, "u": u}
+    if "f" in st:                      # a given limiter (fixed-lengths runs) is kept
+        out["f"] = np.asarray(st["f"], np.float64)
+    return out
+
+
+def _dissipation_rates(w, p, res, st):
+    """Time derivatives of alpha_i (Eq. alphaswitch) and alpha^u_i (Sect. 3.3.3), gas only:
+
+      tau_i        = alpha_tau h_i / v^sig_i,   v^sig_i = max_j v^sig_ij (Eq. vsig; self pair 2 c_i)
+      dalpha/dt    = -(alpha_i - alpha_min) / tau_i + alpha_source f_i max(0, -div v_i)
+      dalpha^u/dt  = -(alpha^u_i - alpha^u_min) / tau_i + S^u_i,
+      S^u_i        = h_i |lap u_i| / sqrt(u_i)      (cond_source 0, Price 2008)
+                   = 0.1 h_i |lap u_i|               (cond_source 1, Price 2005)
+
+    Reading: the source term is printed as 0.75 f_i max[0, -|div v_i|], which is zero for every
+    flow; the intended switch is on in compression, max(0, -div v_i).  alpha_tau = 0.1 is the
+    printed e-folding constant."""
+    n, ng = w.n, w.n_gas
+    h, vs = st["h"][:ng], res["vsig"][:ng]
+    tau = float(getattr(p, "alpha_tau", 0.1)) * h / vs
+    out = {}
+    if getattr(p, "variable_alpha", 0):
+        da = np.zeros(n)
+        da[:ng] = (-(st["alpha"][:ng] - float(getattr(p, "alpha_min", 0.01))) / tau +
+                   float(getattr(p, "alpha_source", 0.75)) * st["f"][:ng] *
+                   np.maximum(0.0, -res.get("divv_h", st.get("divv_h", np.zeros(n)))[:ng]))
+        out["dalpha"] = da
+    if getattr(p, "conduction", 0):
+        lap = np.abs(res["lapu"][:ng])
+        if int(getattr(p, "cond_source", 0)) == 0:
+            S = h * lap / np.sqrt(st["u"][:ng])
+        else:
+            S = 0.1 * h * lap
+        dau = np.zeros(n)
+        dau[:ng] = -(st["alpha_u"][:ng] - float(getattr(p, "alpha_u_min", 0.0))) / tau + S
+        out["dalpha_u"] = dau
+    return out
 
 
 def kdk(w, dt: float, nsteps: int, params=None):

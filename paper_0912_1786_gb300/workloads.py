@@ -46,6 +46,18 @@ class Params:
     leaf_size: int = 8
     group_size: int = 32
     use_tc_gradient: int = 1
+    # dissipation variants (Sect. 3.3.3); all off is the standard Monaghan viscosity
+    visc_form: int = 0             # 0: Monaghan alpha/beta form; 1: signal-velocity form
+    balsara: int = 0               # 1: Balsara limiter on the viscosity
+    balsara_eta: float = 1e-4
+    variable_alpha: int = 0        # 1: per-particle alpha with its time derivative
+    alpha_min: float = 0.01
+    alpha_tau: float = 0.1
+    alpha_source: float = 0.75
+    conduction: int = 0            # 1: artificial conductivity with per-particle alpha^u
+    cond_vsig: int = 0             # 0: sound-speed signal velocity; 1: pressure-jump signal velocity
+    cond_source: int = 0           # 0: h |lap u| / sqrt(u); 1: 0.1 h |lap u|
+    alpha_u_min: float = 0.0
 
 
 @dataclass
@@ -64,6 +76,8 @@ class Workload:
     n_gas: int
     params: Params = field(default_factory=Params)
     sys_offsets: np.ndarray | None = None     # batched ensembles: CSR offsets of the systems
+    alpha: np.ndarray | None = None           # per-particle viscosity alpha_i (gas), variable alpha
+    alpha_u: np.ndarray | None = None         # per-particle conductivity alpha^u_i (gas)
 
     @property
     def n(self) -> int:
@@ -223,6 +237,32 @@ def ensemble(nsys: int = 64, seed: int = 5, log2_min: float = 10.0, log2_max: fl
     p = params or parts[0].params
     w = Workload("ensemble", **cat, n_gas=int(offs[-1]), params=p, sys_offsets=offs)
     return w
+
+
+def with_dissipation(w: Workload, seed: int = 7, alpha=(0.05, 1.5), alpha_u=(0.0, 1.0), u_spread: float = 0.5,
+                     sigma_v: float = 0.0, **params) -> Workload:
+    """A copy of `w` with the per-particle inputs of the dissipation variants: alpha_i and alpha^u_i
+    uniform in the given ranges, u_i multiplied by a log-uniform factor in [1/(1+s), 1+s] (so that
+    neighbouring particles differ in u and the conductivity has work to do), optionally isotropic
+    Gaussian velocities of dispersion sigma_v added, and the keyword arguments set on a copy of
+    its Params (e.g. visc_form=1, balsara=1, variable_alpha=1, conduction=1)."""
+    import copy
+    import dataclasses
+
+    rng = np.random.default_rng(seed)
+    ng = w.n_gas
+    out = copy.copy(w)
+    out.params = dataclasses.replace(w.params, **params)
+    out.alpha = np.ascontiguousarray(rng.uniform(alpha[0], alpha[1], ng), F32)
+    out.alpha_u = np.ascontiguousarray(rng.uniform(alpha_u[0], alpha_u[1], ng), F32)
+    if u_spread > 0 and ng:
+        k = np.log1p(u_spread)
+        uu = w.u.astype(np.float64) * np.exp(rng.uniform(-k, k, ng))
+        out.u = np.ascontiguousarray(uu, F32)
+    if sigma_v > 0:
+        out.vx, out.vy, out.vz = (np.ascontiguousarray(a + rng.normal(0.0, sigma_v, w.n), F32)
+                                  for a in (w.vx, w.vy, w.vz))
+    return out
 
 
 def sample_indices(n: int, k: int, seed: int = 12345) -> np.ndarray:
