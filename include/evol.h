@@ -14,7 +14,10 @@
  *     softening correction (Eq. dLgravdr; App. B),
  *   - the SPH pressure + artificial-viscosity acceleration and du/dt (Eqs. motionvarmass1,
  *     thermalvarmass1, mu_visc; App. B), with the Thomas-Couchman kernel gradient (Sect. 3
- *     footnote) and nearest-image periodic axes (Sect. 4.3).
+ *     footnote) and nearest-image periodic axes (Sect. 4.3),
+ *   - optionally the other dissipation terms of Sect. 3.3.3: the signal-velocity viscosity
+ *     (Eqs. pvsig, vsig), the Balsara limiter, per-particle alpha with its time derivative
+ *     (Eq. alphaswitch) and the artificial conductivity with per-particle alpha^u.
  *
  * Conventions common to every entry point:
  *   - All particle and output pointers are DEVICE pointers (cudaMalloc'd or torch tensors),
@@ -47,6 +50,14 @@ extern "C" {
 #define EVOL_ENAN       -7   /* a non-finite value was produced */
 #define EVOL_ESTATE     -8   /* call order violated (e.g. forces before density) */
 
+/* ---- dissipation variants (Sect. 3.3.3) ------------------------------------------------ */
+#define EVOL_VISC_MONAGHAN        0  /* Pi = (-alpha cbar mu + beta mu^2) / rhobar (Eq. mu_visc) */
+#define EVOL_VISC_SIGNAL          1  /* Pi = -alpha v^sig w / rhobar (Eqs. pvsig, vsig) */
+#define EVOL_COND_VSIG_SOUND      0  /* conductivity signal speed: v^sig of Eq. vsig */
+#define EVOL_COND_VSIG_PRESSURE   1  /* sqrt(|P_i - P_j| / rhobar) */
+#define EVOL_COND_SRC_SQRTU       0  /* conductivity switch source h |lap u| / sqrt(u) */
+#define EVOL_COND_SRC_LINEAR      1  /* 0.1 h |lap u| */
+
 /* ---- precision forms -------------------------------------------------------------- */
 #define EVOL_FP32_PLAIN  0   /* FP32 moments and FP32 accumulation of per-particle sums */
 #define EVOL_FP32_MIXED  1   /* FP64 multipole/centre-of-mass accumulation and FP64 totals of
@@ -65,6 +76,10 @@ typedef struct {
     const float *u;        /* specific internal energy of gas particles (length n_gas) */
     float *h;              /* in: starting guess (> 0) for gas; out: solved smoothing length */
     float *eps;            /* in: softening (fixed) or starting guess (adaptive); out: solved */
+    const float *alpha;    /* per-particle viscosity alpha_i (length n_gas); read only with
+                              variable_alpha, required then */
+    const float *alpha_u;  /* per-particle conductivity alpha^u_i (length n_gas); read only with
+                              conduction, required then */
 } evol_particles;
 
 /* Parameters (Sect. 5 lists the paper's choices: eta, alpha, beta, gamma, theta). */
@@ -85,6 +100,25 @@ typedef struct {
     int leaf_size;             /* a cube is split while it holds more than leaf_size particles
                                   (1..64; 0 = default 8).  Changes cost, not the definition. */
     int group_size;            /* particles per warp group in the walks: 0 or 32 */
+    /* Dissipation variants (Sect. 3.3.3).  A zeroed block is the Monaghan viscosity with the
+     * constant alpha and beta above.  Every variant uses, per pair, w_ij = v_ij.r_ij/|r_ij| and
+     * the signal velocity v^sig_ij = c_i + c_j - min(w_ij, 0) (Eq. vsig; the min keeps it >= c_i + c_j
+     * for receding pairs), and per particle v^sig_i = max(2 c_i, max_j v^sig_ij). */
+    int visc_form;             /* EVOL_VISC_MONAGHAN or EVOL_VISC_SIGNAL */
+    int balsara;               /* 1: Pi_ij times (f_i + f_j)/2, f_i = |div v| / (|div v| + |curl v|
+                                  + balsara_eta c_i/h_i) (0 where that denominator is 0) */
+    float balsara_eta;         /* >= 0; the paper's value is about 1e-4 */
+    int variable_alpha;        /* 1: alpha_ij = (alpha_i + alpha_j)/2 from p->alpha (either form),
+                                  and out->dalpha = -(alpha_i - alpha_min)/tau_i
+                                  + alpha_source f_i max(0, -div v_i), tau_i = alpha_tau h_i/v^sig_i */
+    float alpha_min, alpha_tau, alpha_source;   /* paper: 0.01, 0.1, 0.75; alpha_tau > 0 */
+    int conduction;            /* 1: du_i/dt += sum_j m_j Pi^u_ij |gradbar W_ij| with
+                                  Pi^u_ij = -(alpha^u_i + alpha^u_j)/2 v^u (u_i - u_j) / rhobar_ij,
+                                  and out->dalpha_u = -(alpha^u_i - alpha_u_min)/tau_i + S^u_i */
+    int cond_vsig;             /* v^u: EVOL_COND_VSIG_SOUND or EVOL_COND_VSIG_PRESSURE */
+    int cond_source;           /* S^u from Brookshaw's lap u_i = sum_j 2 m_j (u_i - u_j)/rho_j
+                                  |gradbar W_ij|/r_ij: EVOL_COND_SRC_SQRTU or EVOL_COND_SRC_LINEAR */
+    float alpha_u_min;         /* paper: 0 */
 } evol_params;
 
 /* Outputs, caller order.  Any pointer may be NULL (not written). */
@@ -96,6 +130,8 @@ typedef struct {
     float *omega, *zeta;       /* length n_gas: Omega*_i and zeta_i (Eq. drhodr) */
     float *dudt;               /* length n_gas: du/dt (Eq. thermalvarmass1) */
     float *ups, *X;            /* length n: Upsilon_i and X_i (adaptive softening) */
+    float *dalpha;             /* length n_gas: d alpha_i / dt (variable_alpha; else not written) */
+    float *dalpha_u;           /* length n_gas: d alpha^u_i / dt (conduction; else not written) */
 } evol_outputs;
 
 /* Create a context for up to max_n particles on the current CUDA device; every device
@@ -146,7 +182,8 @@ int evol_step_batched(evol_ctx *ctx, const int64_t *sys_offsets, int nsys, evol_
  * nsteps times: v += a dt/2 (and u += du/dt dt/2 for gas); x += v dt (periodic axes wrapped
  * into [periodic_lo, periodic_hi)); force step; v += a dt/2, u += du/dt dt/2.  The particle
  * arrays x, y, z, vx, vy, vz and u are updated IN PLACE, so they must be writable device
- * memory despite their const qualifiers; h and eps carry over as the next step's starting
+ * memory despite their const qualifiers (so are alpha and alpha_u, kicked with their time
+ * derivatives like u, when variable_alpha / conduction is on); h and eps carry over as the next step's starting
  * guesses.  out receives the outputs of the last force step (any field may be NULL).  One KDK
  * step (kicks, drift and the force phases) is recorded into CUDA graphs once and replayed
  * nsteps times.  Returns EVOL_EINVAL for nsteps < 0 or dt not finite. */
@@ -155,7 +192,8 @@ int evol_kdk(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outp
 /* Global time step of the integrator (Sect. 4.2).  Each eta scales one per-particle criterion;
  * 0 leaves the criterion out.  With L = min(eps_i, h_i) (eps alone for non-gas particles):
  *   eta_acc sqrt(L/|a|),  eta_vel L/|v|,  eta_av |v|/|a|,
- *   eta_courant h / (h |div v| + c + 1.2 (alpha c + beta max_j |mu_ij|))     (gas),
+ *   eta_courant h / (h |div v| + c + 1.2 (alpha c + beta max_j |mu_ij|))     (gas; alpha_i
+ *                                                        with variable_alpha, in both forms),
  *   eta_u |u / (du/dt)|                                                     (gas).
  * (The paper prints the second and third criteria under square roots that do not give a time;
  * they are taken as written here.)  dt is the smallest criterion over all particles, clamped to
@@ -239,8 +277,12 @@ int evol_get_counters(evol_ctx *ctx, uint64_t out[32]);
  *   EVOL_DBG_COUNTS int32[3*n]  caller order: far nodes, particle pairs, SPH pairs
  *   EVOL_DBG_FLOW   float[3*n]  caller order: div v with the softening kernel, div v with the
  *                               smoothing kernel (gas), largest |mu_ij| of the viscosity (gas)
+ *   EVOL_DBG_DISS   float[5*n]  caller order, gas: div v and |curl v| with the smoothing kernel,
+ *                               Balsara f_i, v^sig_i, Brookshaw lap u_i (as printed, with
+ *                               |gradbar W|; conduction only)
  * Hashes and per-particle counts are written only while check mode is on; the divergences only
- * by evol_run's force steps. */
+ * by evol_run's force steps or when a dissipation variant needs them (Balsara, variable alpha);
+ * EVOL_DBG_DISS only by steps with a dissipation variant on. */
 #define EVOL_DBG_KEYS     1
 #define EVOL_DBG_PERM     2
 #define EVOL_DBG_NODES    3
@@ -249,6 +291,7 @@ int evol_get_counters(evol_ctx *ctx, uint64_t out[32]);
 #define EVOL_DBG_HASHES   6
 #define EVOL_DBG_COUNTS   7
 #define EVOL_DBG_FLOW     8
+#define EVOL_DBG_DISS     9
 int64_t evol_get_debug(evol_ctx *ctx, int what, void *host_dst, int64_t cap_bytes);
 
 /* Check mode (0/1): the walks also record, per particle, order-independent 64-bit hashes

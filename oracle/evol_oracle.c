@@ -723,6 +723,7 @@ typedef struct {
     double mumax;       /* largest |mu_ij| of the viscosity over the SPH neighbours */
     double vsig;        /* largest signal velocity v^sig_ij over the SPH neighbours */
     double lapu;        /* Brookshaw estimate of the Laplacian of u (conduction only) */
+    double lapabs;      /* sum of the magnitudes of its terms */
 } orc_result;
 
 /* Distance of one decision (value v against threshold thr) from its threshold.  It is taken
@@ -829,6 +830,7 @@ static void orc_pair(const orc_tree *t, const orc_params *pr, const orc_state *s
                     res->duabs += fabs(mj * Piu * gbar);
                     /* Brookshaw's Laplacian, as printed: sum_j 2 m_j (u_i - u_j)/rho_j |gradbar W_ij| / r */
                     res->lapu += 2.0 * mj * du_ / st->rho[j] * fabs(gbar) / r;
+                    res->lapabs += fabs(2.0 * mj * du_ / st->rho[j] * gbar / r);
                 }
             }
         }
@@ -937,7 +939,7 @@ void orc_forces(orc_tree *t, double theta, double G, double gamma, double alpha,
                 uint64_t *hfar, uint64_t *hnear, uint64_t *hsph,
                 int64_t *nfar, int64_t *npp, int64_t *nsph, double *margin,
                 double *aabs, double *duabs, double *mumax,
-                const orc_diss *diss, double *vsig, double *lapu)
+                const orc_diss *diss, double *vsig, double *lapu, double *lapabs)
 {
     orc_params pr = {theta, G, gamma, alpha, beta, gravity, sph, adaptive, use_tc, {0}};
     if (diss) pr.ds = *diss;
@@ -969,6 +971,7 @@ void orc_forces(orc_tree *t, double theta, double G, double gamma, double alpha,
          * neighbours */
         if (vsig) vsig[i] = (sph && i < t->n_gas && c) ? fmax(res.vsig, 2.0 * c[i]) : 0.0;
         if (lapu) lapu[i] = res.lapu;
+        if (lapabs) lapabs[i] = res.lapabs;
     }
 }
 

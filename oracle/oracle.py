@@ -68,7 +68,7 @@ def lib():
         L.orc_forces.argtypes = ([C.c_void_p, d, d, d, d, d, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                   _f64p, _f64p] + [_f64p] * 3 + [_f64p] * 3 + [_f64p] * 6 +
                                  [C.c_void_p, C.c_int64] + [_f64p] * 5 + [C.c_void_p] * 10 +
-                                 [C.c_void_p] * 3)
+                                 [C.c_void_p] * 4)
         L.orc_divv.restype = C.c_int
         L.orc_divv.argtypes = [C.c_void_p, C.c_int, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, C.c_void_p,
                                C.c_int64, C.c_int, _f64p, _f64p, _f64p, C.c_void_p]
@@ -207,7 +207,7 @@ class OracleTree:
         ds.cond_vsig = int(getattr(params, "cond_vsig", 0))
         keep = {k: g(k) for k in ("f", "alpha", "alpha_u", "u")}
         ds.f, ds.alpha, ds.alpha_u, ds.u = (keep[k].ctypes.data for k in ("f", "alpha", "alpha_u", "u"))
-        vsig, lapu = np.zeros(n), np.zeros(n)
+        vsig, lapu, lapabs = np.zeros(n), np.zeros(n), np.zeros(n)
         pm, lo, hi = self._period(params)
         ix = _c(idx, np.int64) if idx is not None else None
         out = [np.zeros(n) for _ in range(5)]
@@ -224,7 +224,7 @@ class OracleTree:
                          ix.ctypes.data if ix is not None else None, int(len(ix)) if ix is not None else 0,
                          *out, *[a.ctypes.data for a in hashes], *[a.ctypes.data for a in counts],
                          margin.ctypes.data, aabs.ctypes.data, duabs.ctypes.data, mumax.ctypes.data,
-                         C.addressof(ds), vsig.ctypes.data, lapu.ctypes.data)
+                         C.addressof(ds), vsig.ctypes.data, lapu.ctypes.data, lapabs.ctypes.data)
         res = dict(zip(("ax", "ay", "az", "pot", "dudt"), out))
         res.update(zip(("hfar", "hnear", "hsph"), hashes))
         res.update(zip(("nfar", "npp", "nsph"), counts))
@@ -234,6 +234,7 @@ class OracleTree:
         res["mumax"] = mumax
         res["vsig"] = vsig
         res["lapu"] = lapu
+        res["lapabs"] = lapabs
         return res
 
     def divv(self, mode: int, L, nsum, corr, vx, vy, vz, idx=None, params=None, curl=False):

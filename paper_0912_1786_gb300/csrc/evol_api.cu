@@ -37,6 +37,7 @@ void free_all(evol_ctx *c)
 {
     evol_dev &d = c->d;
     void *ptrs[] = {d.pos, d.vel, d.grav, d.hydro, d.snd, d.vah, d.orig, d.inv, d.divv_h, d.divv_e, d.mumax, d.dt, d.time, d.len_h, d.len_eps, d.nh, d.omega,
+                    d.diss, d.curlv_h, d.vsig, d.lapu, d.dalpha, d.dalpha_u,
                     d.zeta, d.rho, d.neps, d.ups, d.X, d.acc, d.dudt, d.keys_a, d.keys_b, d.vals_a, d.vals_b,
                     d.hist, d.lcp, d.cnt, d.base, d.scan_part, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
                     d.nnch, d.narrive, d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nM64, d.nC64, d.nQ64, d.nBmin,
@@ -76,6 +77,16 @@ int check_args(evol_ctx *c, const evol_particles *p, const evol_params *prm)
     if (prm->periodic_mask & ~7) return EVOL_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (((prm->periodic_mask >> a) & 1) && !(prm->periodic_hi[a] > prm->periodic_lo[a])) return EVOL_EINVAL;
+    // dissipation variants (Sect. 3.3.3)
+    if (prm->visc_form != EVOL_VISC_MONAGHAN && prm->visc_form != EVOL_VISC_SIGNAL) return EVOL_EINVAL;
+    if (prm->cond_vsig != EVOL_COND_VSIG_SOUND && prm->cond_vsig != EVOL_COND_VSIG_PRESSURE) return EVOL_EINVAL;
+    if (prm->cond_source != EVOL_COND_SRC_SQRTU && prm->cond_source != EVOL_COND_SRC_LINEAR) return EVOL_EINVAL;
+    if (prm->balsara && !(prm->balsara_eta >= 0.f)) return EVOL_EINVAL;
+    if ((prm->variable_alpha || prm->conduction) && !(prm->alpha_tau > 0.f)) return EVOL_EINVAL;
+    if (prm->sph && p->n_gas > 0) {
+        if (prm->variable_alpha && !p->alpha) return EVOL_EINVAL;
+        if (prm->conduction && !p->alpha_u) return EVOL_EINVAL;
+    }
     return EVOL_OK;
 }
 
@@ -142,7 +153,8 @@ int record_phase(evol_ctx *c, int k, evol_particles *p, const evol_params *prm, 
         break;
     case 4: {
         int what = EVOL_UNPERM_ACC | (grav ? EVOL_UNPERM_EPSOUT : 0) |
-                   (sph ? (EVOL_UNPERM_LENGTHS | EVOL_UNPERM_DENSITY | EVOL_UNPERM_DUDT) : 0);
+                   (sph ? (EVOL_UNPERM_LENGTHS | EVOL_UNPERM_DENSITY | EVOL_UNPERM_DUDT) : 0) |
+                   (sph && evol_diss_on(prm) ? EVOL_UNPERM_DISS : 0);
         rc = evol_launch_unpermute(c, p, out, what);
         if (!rc) rc = evol_launch_diagnostics(c, p, prm);
         break;
@@ -205,6 +217,8 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.zeta, n); rc |= dalloc(&d.rho, n); rc |= dalloc(&d.neps, n); rc |= dalloc(&d.ups, n);
     rc |= dalloc(&d.X, n); rc |= dalloc(&d.acc, n); rc |= dalloc(&d.dudt, n);
     rc |= dalloc(&d.divv_h, n); rc |= dalloc(&d.divv_e, n); rc |= dalloc(&d.mumax, n);
+    rc |= dalloc(&d.diss, n); rc |= dalloc(&d.curlv_h, n); rc |= dalloc(&d.vsig, n); rc |= dalloc(&d.lapu, n);
+    rc |= dalloc(&d.dalpha, n); rc |= dalloc(&d.dalpha_u, n);
     rc |= dalloc(&d.dt, 4); rc |= dalloc(&d.time, 1);
     rc |= dalloc(&d.keys_a, n); rc |= dalloc(&d.keys_b, n); rc |= dalloc(&d.vals_a, n); rc |= dalloc(&d.vals_b, n);
     rc |= dalloc(&d.hist, 256 * c->sort_blocks + 1);
@@ -227,7 +241,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.sys_off, NSYS_CAP + 1); rc |= dalloc(&d.sys_root, NSYS_CAP); rc |= dalloc(&d.sys_sorted, n);
     if (!rc && cudaMallocHost((void **)&c->h_sys_off, (NSYS_CAP + 1) * sizeof(int32_t)) != cudaSuccess) rc = EVOL_ENOMEM;
     rc |= dalloc(&d.hash3, 3 * n); rc |= dalloc(&d.cnt3, 3 * n);
-    rc |= dalloc(&c->stage, 24 * n);
+    rc |= dalloc(&c->stage, 26 * n);
     rc |= dalloc(&c->kdk_acc, 4 * n);
     for (int k = 0; k < 6 && !rc; ++k)
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) rc = EVOL_ECUDA;
@@ -326,7 +340,10 @@ int evol_sph_forces(evol_ctx *c, const evol_particles *p, const evol_params *prm
     if (p->n_gas == 0) return EVOL_OK;
     if ((rc = evol_launch_node_lengths(c, prm, (int)p->n_gas))) return set_err(c, rc);
     if ((rc = evol_launch_walk(c, p, prm, 0, 1))) return set_err(c, rc);
-    if ((rc = evol_launch_unpermute_ex(c, p, out, EVOL_UNPERM_ACC | EVOL_UNPERM_DUDT, 1))) return set_err(c, rc);
+    if ((rc = evol_launch_unpermute_ex(c, p, out,
+                                       EVOL_UNPERM_ACC | EVOL_UNPERM_DUDT | (evol_diss_on(prm) ? EVOL_UNPERM_DISS : 0),
+                                       1)))
+        return set_err(c, rc);
     return EVOL_OK;
 }
 
@@ -619,11 +636,13 @@ int evol_step_host(evol_ctx *c, evol_particles *ph, const evol_params *prm, evol
     if (rc || ph->n == 0) return rc;
     int64_t n = ph->n, ng = ph->n_gas;
     float *st = c->stage;
-    float *in[10];
-    for (int k = 0; k < 10; ++k) in[k] = st + (int64_t)k * c->cap;
-    const float *src[10] = {ph->x, ph->y, ph->z, ph->vx, ph->vy, ph->vz, ph->m, ph->u, ph->h, ph->eps};
-    int64_t len[10] = {n, n, n, n, n, n, n, ng, ng, n};
-    for (int k = 0; k < 10; ++k)
+    constexpr int NIN = 12, NOUT = 14;
+    float *in[NIN];
+    for (int k = 0; k < NIN; ++k) in[k] = st + (int64_t)k * c->cap;
+    const float *src[NIN] = {ph->x, ph->y, ph->z, ph->vx, ph->vy, ph->vz, ph->m, ph->u, ph->h, ph->eps,
+                             ph->alpha, ph->alpha_u};
+    int64_t len[NIN] = {n, n, n, n, n, n, n, ng, ng, n, ng, ng};
+    for (int k = 0; k < NIN; ++k)
         if (src[k] && len[k] > 0)
             if (cudaMemcpyAsync(in[k], src[k], len[k] * sizeof(float), cudaMemcpyHostToDevice, c->stream) !=
                 cudaSuccess)
@@ -635,19 +654,21 @@ int evol_step_host(evol_ctx *c, evol_particles *ph, const evol_params *prm, evol
     pd.u = ph->u ? in[7] : nullptr;
     pd.h = ph->h ? in[8] : nullptr;
     pd.eps = ph->eps ? in[9] : nullptr;
+    pd.alpha = ph->alpha ? in[10] : nullptr;
+    pd.alpha_u = ph->alpha_u ? in[11] : nullptr;
     evol_outputs zero{};
     if (!oh) oh = &zero;
-    float *outp[12];
-    for (int k = 0; k < 12; ++k) outp[k] = st + (int64_t)(10 + k) * c->cap;
-    float *hdst[12] = {oh->ax, oh->ay, oh->az, oh->pot, oh->rho, oh->P, oh->c, oh->omega, oh->zeta, oh->dudt,
-                       oh->ups, oh->X};
-    int64_t olen[12] = {n, n, n, n, ng, ng, ng, ng, ng, ng, n, n};
+    float *outp[NOUT];
+    for (int k = 0; k < NOUT; ++k) outp[k] = st + (int64_t)(NIN + k) * c->cap;
+    float *hdst[NOUT] = {oh->ax, oh->ay, oh->az, oh->pot, oh->rho, oh->P, oh->c, oh->omega, oh->zeta, oh->dudt,
+                         oh->ups, oh->X, oh->dalpha, oh->dalpha_u};
+    int64_t olen[NOUT] = {n, n, n, n, ng, ng, ng, ng, ng, ng, n, n, ng, ng};
     evol_outputs od{};
-    float **odp[12] = {&od.ax, &od.ay, &od.az, &od.pot, &od.rho, &od.P, &od.c, &od.omega, &od.zeta, &od.dudt,
-                       &od.ups, &od.X};
-    for (int k = 0; k < 12; ++k) *odp[k] = hdst[k] ? outp[k] : nullptr;
+    float **odp[NOUT] = {&od.ax, &od.ay, &od.az, &od.pot, &od.rho, &od.P, &od.c, &od.omega, &od.zeta, &od.dudt,
+                         &od.ups, &od.X, &od.dalpha, &od.dalpha_u};
+    for (int k = 0; k < NOUT; ++k) *odp[k] = hdst[k] ? outp[k] : nullptr;
     if ((rc = evol_step(c, &pd, prm, &od))) return rc;
-    for (int k = 0; k < 12; ++k)
+    for (int k = 0; k < NOUT; ++k)
         if (hdst[k] && olen[k] > 0)
             cudaMemcpyAsync(hdst[k], outp[k], olen[k] * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
     if (ph->h && ng > 0) cudaMemcpyAsync(ph->h, in[8], ng * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
@@ -849,6 +870,22 @@ int64_t evol_get_debug(evol_ctx *c, int what, void *dst, int64_t cap)
             }
         }
         return 3 * n;
+    }
+    case EVOL_DBG_DISS: {
+        if (dst && cap >= 5 * n * 4) {
+            std::vector<int32_t> orig(n);
+            cudaMemcpy(orig.data(), c->d.orig, n * 4, cudaMemcpyDeviceToHost);
+            const float *src[5] = {c->d.divv_h, c->d.curlv_h, nullptr, c->d.vsig, c->d.lapu};
+            std::vector<float> a(n);
+            std::vector<float4> ds(n);
+            cudaMemcpy(ds.data(), c->d.diss, n * 16, cudaMemcpyDeviceToHost);
+            float *o = (float *)dst;
+            for (int k = 0; k < 5; ++k) {
+                if (src[k]) cudaMemcpy(a.data(), src[k], n * 4, cudaMemcpyDeviceToHost);
+                for (int64_t s = 0; s < n; ++s) o[k * n + orig[s]] = src[k] ? a[s] : ds[s].y;
+            }
+        }
+        return 5 * n;
     }
     case EVOL_DBG_HASHES:
     case EVOL_DBG_COUNTS: {

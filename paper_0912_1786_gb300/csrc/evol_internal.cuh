@@ -22,7 +22,8 @@ __device__ __forceinline__ void evol_flag(int *err, int code)
 // pos  : x, y, z, m
 // grav : 1/eps, X/Upsilon, h (0 for non-gas), zeta/Omega* (0 for non-gas)
 // hydro: vx, vy, vz, P/rho^2
-// snd  : c, rho, 1/h (0 for non-gas), unused
+// snd  : c, rho, 1/h (0 for non-gas), P
+// diss : alpha, Balsara f, u, alpha^u (gas, only with a dissipation variant on)
 struct evol_dev {
     // particles, sorted order
     float4 *pos, *vel, *grav, *hydro, *snd;
@@ -35,6 +36,10 @@ struct evol_dev {
     float4 *acc;             // ax, ay, az, pot (sorted)
     float *divv_h, *divv_e;  // velocity divergence with the smoothing / softening kernel (sorted)
     float *mumax;            // largest |mu_ij| of the viscosity per gas particle (sorted)
+    float4 *diss;            // dissipation operands: alpha_i, Balsara f_i, u_i, alpha^u_i (sorted, gas)
+    float *curlv_h;          // |curl v| with the smoothing kernel (sorted)
+    float *vsig, *lapu;      // v^sig_i and Brookshaw lap u_i of the last walk (sorted)
+    float *dalpha, *dalpha_u;    // d alpha/dt and d alpha^u/dt (sorted)
     float *dt;               // integrator scalars: [0] time step, [1] criterion minimum (as bits)
     double *time;            // integrator time
     float *dudt;             // sorted
@@ -108,7 +113,7 @@ struct evol_ctx {
     // events for phase timings
     cudaEvent_t ev[6];
     // host staging for evol_step_host (device buffers)
-    float *stage;            // 10 * cap floats (inputs) + 14 * cap floats (outputs)
+    float *stage;            // 12 * cap floats (inputs) + 14 * cap floats (outputs)
     // leapfrog: accelerations and du/dt in caller order, and the recorded KDK step
     float *kdk_acc;
     cudaGraphExec_t kdk_exec;
@@ -132,6 +137,16 @@ int evol_launch_integrator_step(evol_ctx *c, const evol_particles *p, const evol
 #define EVOL_UNPERM_ACC     4
 #define EVOL_UNPERM_DUDT    8
 #define EVOL_UNPERM_EPSOUT  16
+#define EVOL_UNPERM_DISS    32
+
+// Any dissipation variant of Sect. 3.3.3 on (they act on SPH pairs only).
+static inline bool evol_diss_on(const evol_params *prm)
+{
+    return prm->sph &&
+           (prm->visc_form != EVOL_VISC_MONAGHAN || prm->balsara || prm->variable_alpha || prm->conduction);
+}
+// The Balsara factor (limiter, alpha source) needs div v and |curl v| from the h solve.
+static inline bool evol_needs_curl(const evol_params *prm) { return prm->sph && (prm->balsara || prm->variable_alpha); }
 
 static inline int evol_cuda_ok(cudaError_t e) { return e == cudaSuccess ? EVOL_OK : EVOL_ECUDA; }
 
@@ -213,4 +228,8 @@ struct evol_kparams {
     int stack_stride;        // entries allocated per warp (>= stack_cap)
     int nsys;
     int want_divv;           // length solves also form div v
+    int want_curl;           // the h solve also forms |curl v| (Balsara limiter, alpha switch)
+    // dissipation variants (Sect. 3.3.3); diss = any of them on
+    int diss, visc_form, balsara, var_alpha, conduction, cond_vsig, cond_source;
+    float alpha_min, alpha_tau, alpha_source, alpha_u_min;
 };

@@ -537,6 +537,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                 // mass-weighted sums of the outputs.
                 const bool last = status == ST_LAST;
                 float Sw = 0.f, Suw = 0.f, S3 = 0.f, S4 = 0.f, S5 = 0.f;
+                float S6x = 0.f, S6y = 0.f, S6z = 0.f;       // curl sums (h solve, on request)
                 const float Linv = 1.f / L;
                 if (!last) {
                     for (int e = lane; e < cnt; e += 32) {
@@ -572,6 +573,14 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                             const float dy = evol_wrap(py - pj.y, kp.plen[1], kp.periodic_mask & 2);
                             const float dz = evol_wrap(pz - pj.z, kp.plen[2], kp.periodic_mask & 4);
                             S5 += ((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz) / rj.x * dw;
+                            if (MODE == 0 && kp.want_curl) {
+                                // (v_i - v_j) x (r_i - r_j) / r  w'(u)
+                                const float ux = vi.x - vj.x, uy = vi.y - vj.y, uz = vi.z - vj.z;
+                                const float q = dw / rj.x;
+                                S6x += (uy * dz - uz * dy) * q;
+                                S6y += (uz * dx - ux * dz) * q;
+                                S6z += (ux * dy - uy * dx) * q;
+                            }
                         }
                     }
                 }
@@ -583,6 +592,11 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         S3 += __shfl_xor_sync(0xffffffffu, S3, o);
                         if (MODE == 0) S4 += __shfl_xor_sync(0xffffffffu, S4, o);
                         if (kp.want_divv) S5 += __shfl_xor_sync(0xffffffffu, S5, o);
+                        if (MODE == 0 && kp.want_curl) {
+                            S6x += __shfl_xor_sync(0xffffffffu, S6x, o);
+                            S6y += __shfl_xor_sync(0xffffffffu, S6y, o);
+                            S6z += __shfl_xor_sync(0xffffffffu, S6z, o);
+                        }
                     }
                 }
                 // identical on every lane up to the order of the additions; take lane 0's values
@@ -592,6 +606,11 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                     S3 = __shfl_sync(0xffffffffu, S3, 0);
                     if (MODE == 0) S4 = __shfl_sync(0xffffffffu, S4, 0);
                     if (kp.want_divv) S5 = __shfl_sync(0xffffffffu, S5, 0);
+                    if (MODE == 0 && kp.want_curl) {
+                        S6x = __shfl_sync(0xffffffffu, S6x, 0);
+                        S6y = __shfl_sync(0xffffffffu, S6y, 0);
+                        S6z = __shfl_sync(0xffffffffu, S6z, 0);
+                    }
                 }
                 const float Smw = S3, Smuw = S4;
                 if (status == ST_LAST) {
@@ -613,6 +632,9 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         // div v = -1/(n C) sum_j (v_i - v_j).grad_i W = 3 S5 / (L Suw), C = Upsilon
                         // or Omega* = -Suw/(3 Sw), n = Sw/(pi L^3), grad W = r_ij/r w'(u)/(pi L^4)
                         if (kp.want_divv) (MODE == 0 ? d.divv_h : d.divv_e)[si] = 3.f * S5 / (L * Suw);
+                        // |curl v| = |1/(n C) sum_j (v_i - v_j) x grad_i W| = 3 |S6| / (L |Suw|)
+                        if (MODE == 0 && kp.want_curl)
+                            d.curlv_h[si] = 3.f * sqrtf(S6x * S6x + S6y * S6y + S6z * S6z) / (L * fabsf(Suw));
                     }
                     status = ST_DONE;
                 } else {
@@ -671,7 +693,8 @@ int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params 
     kp.eta_e = 0.5f * cbrtf(3.f * prm->n_nei_grav / (4.f * EVOL_PI_F));
     kp.periodic_mask = prm->periodic_mask;
     for (int a = 0; a < 3; ++a) kp.plen[a] = prm->periodic_hi[a] - prm->periodic_lo[a];
-    kp.want_divv = c->want_divv;
+    kp.want_curl = mode == 0 && evol_needs_curl(prm);
+    kp.want_divv = c->want_divv || kp.want_curl;
     kp.stack_cap = (int)c->wstack_lim;
     kp.stack_stride = (int)c->wstack_cap;
     unsigned long long *q = c->d.counters + (mode == 0 ? 5 : 6);

@@ -7,9 +7,19 @@
 
 namespace {
 
+// Dissipation operands of the pack (Sect. 3.3.3): per-particle alpha and alpha^u in the caller's
+// order (NULL: the constant alpha, alpha^u = 0) and the Balsara limiter's constant.
+struct DissPack {
+    const float *alpha, *alpha_u;
+    float alpha_const, balsara_eta;
+    int on, need_f;
+};
+
 // Walk operands.  grav = (1/eps, X/Upsilon, h, zeta/Omega*), hydro = (v, P/rho^2),
 // snd = (c, rho, 1/h, P).  Ideal gas (App. B): P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u).
-__global__ void k_pack(int n, int n_gas, int do_grav, int adaptive, int do_sph, float gamma, evol_dev d)
+// With a dissipation variant on, diss = (alpha_i, f_i, u_i, alpha^u_i) with the Balsara factor
+// f_i = |div v| / (|div v| + |curl v| + eta_B c/h), 0 where that denominator is 0.
+__global__ void k_pack(int n, int n_gas, int do_grav, int adaptive, int do_sph, float gamma, evol_dev d, DissPack dp)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -34,6 +44,16 @@ __global__ void k_pack(int n, int n_gas, int do_grav, int adaptive, int do_sph, 
         g.w = d.zeta[s] / d.omega[s];
         hy.w = P / (rho * rho);
         sn = make_float4(sqrtf(gamma * (gamma - 1.f) * u), rho, 1.f / h, P);
+        if (dp.on) {
+            const int j = d.orig[s];
+            float f = 0.f;
+            if (dp.need_f) {
+                const float dv = fabsf(d.divv_h[s]);
+                const float den = dv + d.curlv_h[s] + dp.balsara_eta * sn.x * sn.z;
+                f = den > 0.f ? dv / den : 0.f;
+            }
+            d.diss[s] = make_float4(dp.alpha ? dp.alpha[j] : dp.alpha_const, f, u, dp.alpha_u ? dp.alpha_u[j] : 0.f);
+        }
     }
     d.grav[s] = g;
     d.hydro[s] = hy;
@@ -46,7 +66,7 @@ __global__ void k_pack(int n, int n_gas, int do_grav, int adaptive, int do_sph, 
 // that had no root reports ENOCONV).
 __global__ void k_unpermute(int n, int n_gas, int what, int add_acc, evol_dev d, float *h, float *eps, float *ax,
                             float *ay, float *az, float *pot, float *rho, float *P, float *c, float *omega,
-                            float *zeta, float *dudt, float *ups, float *X)
+                            float *zeta, float *dudt, float *ups, float *X, float *dalpha, float *dalpha_u)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -88,6 +108,10 @@ __global__ void k_unpermute(int n, int n_gas, int what, int add_acc, evol_dev d,
         }
     }
     if ((what & EVOL_UNPERM_DUDT) && gas) put(dudt, d.dudt[s]);
+    if ((what & EVOL_UNPERM_DISS) && gas) {
+        if (dalpha) put(dalpha, d.dalpha[s]);
+        if (dalpha_u) put(dalpha_u, d.dalpha_u[s]);
+    }
     if (!fin) evol_flag(d.err, EVOL_ENAN);
 }
 
@@ -306,8 +330,15 @@ int evol_launch_drift(evol_ctx *c, const evol_particles *p, const evol_params *p
 int evol_launch_pack(evol_ctx *c, const evol_particles *p, const evol_params *prm, int do_grav, int do_sph)
 {
     int n = (int)p->n;
+    DissPack dp{};
+    dp.on = do_sph && evol_diss_on(prm);
+    dp.need_f = evol_needs_curl(prm);
+    dp.alpha = prm->variable_alpha ? p->alpha : nullptr;
+    dp.alpha_u = prm->conduction ? p->alpha_u : nullptr;
+    dp.alpha_const = prm->alpha;
+    dp.balsara_eta = prm->balsara_eta;
     k_pack<<<(n + 255) / 256, 256, 0, c->stream>>>(n, (int)p->n_gas, do_grav, prm->adaptive_softening, do_sph,
-                                                   prm->gamma, c->d);
+                                                   prm->gamma, c->d, dp);
     return evol_cuda_ok(cudaGetLastError());
 }
 
@@ -318,7 +349,7 @@ int evol_launch_unpermute_ex(evol_ctx *c, const evol_particles *p, const evol_ou
     const evol_outputs *q = o ? o : &z;
     k_unpermute<<<(n + 255) / 256, 256, 0, c->stream>>>(n, (int)p->n_gas, what, add_acc, c->d, p->h, p->eps, q->ax,
                                                         q->ay, q->az, q->pot, q->rho, q->P, q->c, q->omega, q->zeta,
-                                                        q->dudt, q->ups, q->X);
+                                                        q->dudt, q->ups, q->X, q->dalpha, q->dalpha_u);
     return evol_cuda_ok(cudaGetLastError());
 }
 

@@ -198,14 +198,27 @@ struct Totals<false> {
     __device__ __forceinline__ double get(int) const { return 0.0; }
 };
 
+// Dissipation operands staged per near entry (alpha, Balsara f, u, alpha^u of the neighbour) and
+// each lane's running v^sig maximum and Brookshaw sum: only the DISS variants hold them.
+template <bool DISS>
+struct DissSmem {
+    float4 nd[WK_WARPS][NEARCAP];
+    float vs[WK_WARPS][32];
+    float lap[WK_WARPS][32];
+};
+template <>
+struct DissSmem<false> {
+};
+
 // Register budgets, chosen so that no variant spills to local memory: the plain gravity + SPH walk
 // (the production form) and the SPH-only walk fit five blocks per SM (at most 102 registers), the
-// mixed gravity + SPH walk four (128 registers), the gravity-only walks three; the check-mode
-// variants one.
-template <bool GRAV, bool SPH, bool MIXED, bool CHECK>
-__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (GRAV && MIXED) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+// mixed gravity + SPH walk and the walks with the dissipation variants (DISS) four (128
+// registers), the gravity-only walks and the mixed DISS walks three; the check-mode variants one.
+template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS>
+__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (MIXED && DISS) ? 3 : ((GRAV && MIXED) || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
+    __shared__ DissSmem<DISS> ds;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int n = kp.n;
@@ -250,6 +263,10 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
         unsigned *wc = sm.wc[w];
         if (lane < 8) wc[lane] = 0u;
         if (SPH) sm.mum[w][lane] = 0.f;
+        if constexpr (DISS) {
+            ds.vs[w][lane] = 0.f;
+            ds.lap[w][lane] = 0.f;
+        }
         __syncwarp();
 
         auto fold = [&]() {
@@ -348,6 +365,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                     sm.nh[w][l] = d.hydro[j];
                     sm.ns[w][l] = d.snd[j];
                 }
+                if constexpr (DISS) ds.nd[w][l] = d.diss[j];     // read only for gas pairs
                 if (CHECK) sm.norig[w][l] = d.orig[j];
             }
             if (lane == 0) wc[1] += 32u * (unsigned)((nnear + 1) & ~1);
@@ -413,6 +431,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                 const float4 gi = (SPH && valid) ? d.grav[s] : z4;
                 const float4 hi = (SPH && valid) ? d.hydro[s] : z4;
                 const float4 si = (SPH && valid) ? d.snd[s] : z4;
+                const float4 di = (DISS && gas_i) ? d.diss[s] : z4;
                 while (__any_sync(0xffffffffu, sbits != 0ull)) {
                     if (lane == 0) wc[2] += 32u;
                     if (sbits) {
@@ -470,13 +489,34 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                                 const float vx = hi.x - hj.x, vy = hi.y - hj.y, vz = hi.z - hj.z;
                                 const float vr = vx * dx + vy * dy + vz * dz;
                                 float visc = 0.f;
+                                // dissipation variants: w_ij = v_ij . r_ij / r and the signal velocity
+                                // v^sig_ij = c_i + c_j - min(w_ij, 0) (Eq. vsig)
+                                float4 dj = z4;
+                                float wij = 0.f, vsig = 0.f;
+                                if constexpr (DISS) {
+                                    dj = ds.nd[w][t];
+                                    wij = vr * rinv;
+                                    vsig = si.x + sj.x - fminf(wij, 0.f);
+                                    ds.vs[w][lane] = fmaxf(ds.vs[w][lane], vsig);
+                                }
                                 if (vr < 0.f) {
                                     const float hb = 0.5f * (gi.z + gj.z);
                                     const float mu = hb * vr * rcp_fast(r2 + 0.01f * hb * hb);
                                     sm.mum[w][lane] = fmaxf(sm.mum[w][lane], -mu);    // |mu| (vr < 0)
                                     const float cb = 0.5f * (si.x + sj.x);
                                     const float rb = 0.5f * (si.y + sj.y);
-                                    visc = (-kp.alpha * cb * mu + kp.beta * mu * mu) * rcp_fast(rb);
+                                    if constexpr (!DISS) {
+                                        visc = (-kp.alpha * cb * mu + kp.beta * mu * mu) * rcp_fast(rb);
+                                    } else {
+                                        // alpha_ij = (alpha_i + alpha_j)/2 (Eq. alphaswitch); Monaghan
+                                        // (Eq. mu_visc) or signal-velocity form (Eq. pvsig); Balsara
+                                        // limiter (f_i + f_j)/2
+                                        const float al = kp.var_alpha ? 0.5f * (di.x + dj.x) : kp.alpha;
+                                        visc = (kp.visc_form == EVOL_VISC_SIGNAL ? -al * vsig * wij
+                                                                                  : (-al * cb * mu + kp.beta * mu * mu)) *
+                                               rcp_fast(rb);
+                                        if (kp.balsara) visc *= 0.5f * (di.y + dj.y);
+                                    }
                                 }
                                 const float gbar = 0.5f * (kgi * fi + kgj * fj);
                                 const float pterm_i = hi.w * fi * kgi;
@@ -485,6 +525,21 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                                 acc.hy += sc * dy;
                                 acc.hz += sc * dz;
                                 acc.du += mj * (pterm_i + 0.5f * visc * gbar) * vr;
+                                if constexpr (DISS) {
+                                    if (kp.conduction) {
+                                        // artificial conductivity: du_i/dt += m_j Pi^u_ij |gradbar W_ij| with
+                                        // Pi^u = -alphabar^u v^u (u_i - u_j) / rhobar (gbar is the mean
+                                        // gradient over r); Brookshaw's sum 2 m_j (u_i - u_j)/rho_j |gradbar W|/r
+                                        const float irb = rcp_fast(0.5f * (si.y + sj.y));
+                                        const float duij = di.z - dj.z;
+                                        const float vu = kp.cond_vsig == EVOL_COND_VSIG_PRESSURE
+                                                             ? sqrtf(fabsf(si.w - sj.w) * irb)
+                                                             : vsig;
+                                        const float ag = fabsf(gbar);
+                                        acc.du -= mj * (0.5f * (di.w + dj.w)) * vu * duij * irb * ag * r;
+                                        ds.lap[w][lane] += 2.f * mj * duij * rcp_fast(sj.y) * ag;
+                                    }
+                                }
                             }
                         }
                     }
@@ -762,6 +817,26 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                 const float4 hv = d.hydro[s];
                 d.vah[s] = gas_i ? (float)(hv.x * thx + hv.y * thy + hv.z * thz) : 0.f;
             }
+            if constexpr (DISS) {
+                if (gas_i) {
+                    // v^sig_i = max(2 c_i, max_j v^sig_ij) (the self pair has w = 0); tau_i =
+                    // alpha_tau h_i / v^sig_i; the switches of alpha (Eq. alphaswitch) and alpha^u
+                    const float4 sn = d.snd[s], di = d.diss[s];
+                    const float h_i = g0.z;
+                    const float vs = fmaxf(ds.vs[w][lane], 2.f * sn.x);
+                    const float lap = ds.lap[w][lane];
+                    const float itau = vs / (kp.alpha_tau * h_i);
+                    d.vsig[s] = vs;
+                    d.lapu[s] = lap;
+                    if (kp.var_alpha)
+                        d.dalpha[s] = -(di.x - kp.alpha_min) * itau + kp.alpha_source * di.y * fmaxf(0.f, -d.divv_h[s]);
+                    if (kp.conduction) {
+                        const float src = kp.cond_source == EVOL_COND_SRC_LINEAR ? 0.1f * h_i * fabsf(lap)
+                                                                                 : h_i * fabsf(lap) * rsqrtf(di.z);
+                        d.dalpha_u[s] = -(di.w - kp.alpha_u_min) * itau + src;
+                    }
+                }
+            }
             if (CHECK) {
                 d.hash3[3 * s + 0] = hfar;
                 d.hash3[3 * s + 1] = hnear;
@@ -790,30 +865,43 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
     }
 }
 
-template <bool GRAV, bool SPH, bool MIXED, bool CHECK>
+template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS>
 void launch_walk(evol_ctx *c, const evol_kparams &kp)
 {
     static int blocks_per_sm = -1;
     if (blocks_per_sm < 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walk<GRAV, SPH, MIXED, CHECK>, WK_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walk<GRAV, SPH, MIXED, CHECK, DISS>,
+                                                      WK_THREADS, 0);
         if (blocks_per_sm < 1) blocks_per_sm = 1;
         if (blocks_per_sm > 8) blocks_per_sm = 8;          // stack slots exist for 32 warps per SM
     }
     unsigned long long *q = c->d.counters + 4;
     cudaMemsetAsync(q, 0, sizeof(unsigned long long), c->stream);
-    k_walk<GRAV, SPH, MIXED, CHECK><<<c->num_sms * blocks_per_sm, WK_THREADS, 0, c->stream>>>(c->d, kp, q);
+    k_walk<GRAV, SPH, MIXED, CHECK, DISS><<<c->num_sms * blocks_per_sm, WK_THREADS, 0, c->stream>>>(c->d, kp, q);
+}
+
+template <bool GRAV, bool SPH, bool DISS>
+void launch_walk_pcd(evol_ctx *c, const evol_kparams &kp, bool mixed, bool check)
+{
+    if (mixed) {
+        if (check) launch_walk<GRAV, SPH, true, true, DISS>(c, kp);
+        else launch_walk<GRAV, SPH, true, false, DISS>(c, kp);
+    } else {
+        if (check) launch_walk<GRAV, SPH, false, true, DISS>(c, kp);
+        else launch_walk<GRAV, SPH, false, false, DISS>(c, kp);
+    }
 }
 
 template <bool GRAV, bool SPH>
 void launch_walk_pc(evol_ctx *c, const evol_kparams &kp, bool mixed, bool check)
 {
-    if (mixed) {
-        if (check) launch_walk<GRAV, SPH, true, true>(c, kp);
-        else launch_walk<GRAV, SPH, true, false>(c, kp);
-    } else {
-        if (check) launch_walk<GRAV, SPH, false, true>(c, kp);
-        else launch_walk<GRAV, SPH, false, false>(c, kp);
+    if constexpr (SPH) {
+        if (kp.diss) {
+            launch_walk_pcd<GRAV, SPH, true>(c, kp, mixed, check);
+            return;
+        }
     }
+    launch_walk_pcd<GRAV, SPH, false>(c, kp, mixed, check);
 }
 
 }  // namespace
@@ -834,6 +922,17 @@ int evol_launch_walk(evol_ctx *c, const evol_particles *p, const evol_params *pr
     for (int a = 0; a < 3; ++a) kp.plen[a] = prm->periodic_hi[a] - prm->periodic_lo[a];
     kp.stack_cap = (int)c->wstack_lim;
     kp.stack_stride = (int)c->wstack_cap;
+    kp.diss = do_sph && evol_diss_on(prm);
+    kp.visc_form = prm->visc_form;
+    kp.balsara = prm->balsara;
+    kp.var_alpha = prm->variable_alpha;
+    kp.conduction = prm->conduction;
+    kp.cond_vsig = prm->cond_vsig;
+    kp.cond_source = prm->cond_source;
+    kp.alpha_min = prm->alpha_min;
+    kp.alpha_tau = prm->alpha_tau;
+    kp.alpha_source = prm->alpha_source;
+    kp.alpha_u_min = prm->alpha_u_min;
     bool mixed = prm->precision == EVOL_FP32_MIXED;
     bool check = c->check_mode != 0;
     if (do_grav && do_sph) launch_walk_pc<true, true>(c, kp, mixed, check);

@@ -7,7 +7,7 @@ import torch
 
 from . import evol as E
 
-OUT_LEN_GAS = {"rho", "P", "c", "omega", "zeta", "dudt"}
+OUT_LEN_GAS = {"rho", "P", "c", "omega", "zeta", "dudt", "dalpha", "dalpha_u"}
 
 
 class DeviceSet:
@@ -28,6 +28,10 @@ class DeviceSet:
             if k in ("u", "h"):
                 t = t[: max(self.n_gas, 1)].clone() if self.n_gas > 0 else t[:1].clone()
             self.inp[k] = t.to(self.device)
+        for k in ("alpha", "alpha_u"):        # per-particle dissipation inputs (gas), when the workload has them
+            a = getattr(w, k, None)
+            if a is not None and self.n_gas > 0:
+                self.inp[k] = torch.from_numpy(np.ascontiguousarray(a[: self.n_gas], np.float32)).to(self.device)
         names = outputs if outputs is not None else E.OUTPUT_FIELDS
         self.out = {}
         for k in names:

@@ -18,6 +18,10 @@ EVOL_EOVERFLOW, EVOL_ENOCONV, EVOL_ETIMEOUT, EVOL_ENAN, EVOL_ESTATE = -4, -5, -6
 EVOL_FP32_PLAIN, EVOL_FP32_MIXED = 0, 1
 EVOL_DBG_KEYS, EVOL_DBG_PERM, EVOL_DBG_NODES, EVOL_DBG_CUBE = 1, 2, 3, 4
 EVOL_DBG_MOMENTS, EVOL_DBG_HASHES, EVOL_DBG_COUNTS, EVOL_DBG_FLOW = 5, 6, 7, 8
+EVOL_DBG_DISS = 9
+EVOL_VISC_MONAGHAN, EVOL_VISC_SIGNAL = 0, 1
+EVOL_COND_VSIG_SOUND, EVOL_COND_VSIG_PRESSURE = 0, 1
+EVOL_COND_SRC_SQRTU, EVOL_COND_SRC_LINEAR = 0, 1
 
 _fp = C.POINTER(C.c_float)
 
@@ -26,7 +30,8 @@ class EvolParticles(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_gas", C.c_int64),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p),
-                ("m", C.c_void_p), ("u", C.c_void_p), ("h", C.c_void_p), ("eps", C.c_void_p)]
+                ("m", C.c_void_p), ("u", C.c_void_p), ("h", C.c_void_p), ("eps", C.c_void_p),
+                ("alpha", C.c_void_p), ("alpha_u", C.c_void_p)]
 
 
 class EvolParams(C.Structure):
@@ -35,7 +40,11 @@ class EvolParams(C.Structure):
                 ("gravity", C.c_int), ("sph", C.c_int), ("adaptive_softening", C.c_int),
                 ("use_tc_gradient", C.c_int), ("periodic_mask", C.c_int),
                 ("periodic_lo", C.c_float * 3), ("periodic_hi", C.c_float * 3),
-                ("precision", C.c_int), ("leaf_size", C.c_int), ("group_size", C.c_int)]
+                ("precision", C.c_int), ("leaf_size", C.c_int), ("group_size", C.c_int),
+                ("visc_form", C.c_int), ("balsara", C.c_int), ("balsara_eta", C.c_float),
+                ("variable_alpha", C.c_int), ("alpha_min", C.c_float), ("alpha_tau", C.c_float),
+                ("alpha_source", C.c_float), ("conduction", C.c_int), ("cond_vsig", C.c_int),
+                ("cond_source", C.c_int), ("alpha_u_min", C.c_float)]
 
 
 class EvolIntegrator(C.Structure):
@@ -46,11 +55,11 @@ class EvolIntegrator(C.Structure):
 
 class EvolOutputs(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("ax", "ay", "az", "pot", "rho", "P", "c", "omega", "zeta",
-                                           "dudt", "ups", "X")]
+                                           "dudt", "ups", "X", "dalpha", "dalpha_u")]
 
 
 OUTPUT_FIELDS = [f[0] for f in EvolOutputs._fields_]
-PARTICLE_FIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "eps"]
+PARTICLE_FIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "eps", "alpha", "alpha_u"]
 
 _lib = None
 
@@ -129,6 +138,13 @@ def make_params(p) -> EvolParams:
     e.precision = int(getattr(p, "precision", EVOL_FP32_PLAIN))
     e.leaf_size = int(getattr(p, "leaf_size", 8))
     e.group_size = int(getattr(p, "group_size", 32))
+    # dissipation variants (defaults: the paper's constants, every variant off)
+    for k, d in (("visc_form", 0), ("balsara", 0), ("variable_alpha", 0), ("conduction", 0), ("cond_vsig", 0),
+                 ("cond_source", 0)):
+        setattr(e, k, int(getattr(p, k, d)))
+    for k, d in (("balsara_eta", 1e-4), ("alpha_min", 0.01), ("alpha_tau", 0.1), ("alpha_source", 0.75),
+                 ("alpha_u_min", 0.0)):
+        setattr(e, k, float(getattr(p, k, d)))
     return e
 
 

@@ -257,7 +257,8 @@ def with_dissipation(w: Workload, seed: int = 7, alpha=(0.05, 1.5), alpha_u=(0.0
     out.alpha_u = np.ascontiguousarray(rng.uniform(alpha_u[0], alpha_u[1], ng), F32)
     if u_spread > 0 and ng:
         k = np.log1p(u_spread)
-        uu = w.u.astype(np.float64) * np.exp(rng.uniform(-k, k, ng))
+        uu = w.u.astype(np.float64).copy()
+        uu[:ng] *= np.exp(rng.uniform(-k, k, ng))
         out.u = np.ascontiguousarray(uu, F32)
     if sigma_v > 0:
         out.vx, out.vy, out.vz = (np.ascontiguousarray(a + rng.normal(0.0, sigma_v, w.n), F32)

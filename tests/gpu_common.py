@@ -73,6 +73,9 @@ def run_gpu(w, params=None, check=True, precision=0, api="step", max_n=None):
             res["hashes"] = E.evol_get_debug(ctx, E.EVOL_DBG_HASHES, np.uint64).reshape(-1, 3)
             res["counts"] = E.evol_get_debug(ctx, E.EVOL_DBG_COUNTS, np.int32).reshape(-1, 3)
         res["diag"] = E.evol_get_diagnostics(ctx)
+        if getattr(p, "sph", 0) and w.n_gas > 0 and (getattr(p, "visc_form", 0) or getattr(p, "balsara", 0) or
+                                                     getattr(p, "variable_alpha", 0) or getattr(p, "conduction", 0)):
+            res["dbg_diss"] = E.evol_get_debug(ctx, E.EVOL_DBG_DISS, np.float32).reshape(5, w.n).astype(np.float64)
     finally:
         E.evol_destroy(ctx)
     return res

@@ -44,9 +44,30 @@ def test_no_cpu_fallback_without_device():
     assert ei.value.code == E.EVOL_ECUDA
 
 
-def test_binding_struct_layouts_match_header():
-    # sizes of the C structs as laid out by the compiler (x86-64 / aarch64 LP64 ABI)
+def test_binding_struct_layouts_match_header(tmp_path):
+    # every field of the ctypes mirrors sits at the offset the C compiler gives it in include/evol.h,
+    # and the structs have the same size (a C program built against the header prints both)
+    import shutil
+    import subprocess
     from paper_0912_1786_gb300 import evol as E
-    assert ctypes.sizeof(E.EvolParticles) == 16 + 10 * 8
-    assert ctypes.sizeof(E.EvolOutputs) == 12 * 8
-    assert ctypes.sizeof(E.EvolParams) == 7 * 4 + 5 * 4 + 6 * 4 + 3 * 4
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"evol_particles": E.EvolParticles, "evol_params": E.EvolParams, "evol_outputs": E.EvolOutputs,
+               "evol_integrator": E.EvolIntegrator}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "evol.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln.strip())}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
