@@ -173,12 +173,12 @@ def oracle_state(w, leaf):
     elif p.gravity:
         st.update(eps=w.eps.astype(np.float64), ups=np.ones(n), X=np.zeros(n))
     if p.sph and ng:
-        h, _, rho, om, zeta = tree.solve_lengths(0, p.n_nei_sph, guess=w.h, idx=np.arange(ng), params=p)
+        h, nh, rho, om, zeta = tree.solve_lengths(0, p.n_nei_sph, guess=w.h, idx=np.arange(ng), params=p)
         P, c = np.zeros(n), np.zeros(n)
         lib.orc_eos(n, float(p.gamma), np.ascontiguousarray(rho), np.ascontiguousarray(w.u, np.float64), P, c)
         P[ng:] = 0
         c[ng:] = 0
-        st.update(h=h, rho=rho, omega=om, zeta=zeta, P=P, c=c)
+        st.update(h=h, rho=rho, omega=om, zeta=zeta, P=P, c=c, n_h=nh)
     st.update(vx=w.vx.astype(np.float64), vy=w.vy.astype(np.float64), vz=w.vz.astype(np.float64))
     return tree, st
 
@@ -424,6 +424,87 @@ def other_forms(torch, dev, stream, E, DeviceSet, w, steps, precision_used, leaf
     return forms, results
 
 
+DISSIPATION_ALL = dict(visc_form=1, balsara=1, variable_alpha=1, conduction=1)
+
+
+def dissipation_form(torch, dev, stream, E, DeviceSet, w, steps, leaf, ostate, sample=2000):
+    """The dissipation variants (signal-velocity viscosity, Balsara limiter, variable alpha,
+    conductivity) on the same particles with seeded velocities (sigma 0.1, so that the viscosity
+    acts), per-particle alpha, alpha^u and u spread: throughput of the standard form and of all
+    variants on that input, their walk times, and the variants' errors against the oracle on a
+    seeded sample (the oracle reuses the main form's lengths: the positions are the same)."""
+    import oracle
+    from paper_0912_1786_gb300 import workloads as W
+    wd = W.with_dissipation(w, seed=13, sigma_v=0.1, **DISSIPATION_ALL)
+    ws = W.with_dissipation(w, seed=13, sigma_v=0.1)           # same input, standard viscosity
+    out = {"input": "main workload + isotropic velocities sigma 0.1 (seed 13), alpha in [0.05, 1.5], "
+                    "alpha^u in [0, 1], u spread x[1/1.5, 1.5]"}
+    rates = {}
+    res = None
+    for name, ww in (("standard", ws), ("all_variants", wd)):
+        ds = DeviceSet(ww, device=str(dev))
+        ds.params.leaf_size = leaf
+        ctx = E.evol_create(ww.n, stream.cuda_stream)
+        try:
+            run = lambda: (ds.reset_lengths(), E.evol_step(ctx, ds.particles, ds.params, ds.outputs))
+            for _ in range(2):
+                run()
+            E.evol_sync(ctx)
+            walks = []
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ms = 0.0
+            for _ in range(steps):
+                ms += time_steps(torch, dev, stream, run, 1)
+                walks.append(E.evol_get_timings(ctx)[3])
+            E.evol_sync(ctx)
+            rates[name] = {"particles_per_s": ww.n * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                           "walk_ms": statistics.mean(walks)}
+            if name == "all_variants":
+                res = gpu_check_step(E, ctx, ds)
+        finally:
+            E.evol_destroy(ctx)
+    out["rates"] = rates
+    if ostate is None:
+        return out
+    # the oracle on the sample: lengths from the main form's solve, flow quantities with the new
+    # velocities, equation of state with the new u
+    tree, st0 = ostate
+    ng = wd.n_gas
+    gas = np.arange(ng, dtype=np.int64)
+    vx, vy, vz = (getattr(wd, k).astype(np.float64) for k in ("vx", "vy", "vz"))
+    divv, curl = tree.divv(0, st0["h"], st0["n_h"], st0["omega"], vx, vy, vz, idx=gas, params=wd.params, curl=True)
+    P, c = np.zeros(wd.n), np.zeros(wd.n)
+    oracle.lib().orc_eos(wd.n, float(wd.params.gamma), np.ascontiguousarray(st0["rho"]),
+                         np.ascontiguousarray(wd.u, np.float64), P, c)
+    P[ng:] = 0
+    c[ng:] = 0
+    fixed = {k: v for k, v in st0.items() if k not in ("vx", "vy", "vz", "n_h")}
+    fixed.update(P=P, c=c, divv_h=divv, curlv_h=curl)
+    sidx = np.sort(np.random.default_rng(17).choice(wd.n, min(wd.n, sample), replace=False))
+    ref = oracle.force_step(wd, idx=sidx, tree=tree, fixed_lengths=fixed)
+    gi = sidx[sidx < ng]
+    A = lambda x: np.stack([x["ax"], x["ay"], x["az"]], 1)
+    e = {"acc": _rel(A(res)[sidx], A(ref)[sidx], ref["aabs"][sidx]),
+         "dudt": _rel(res["dudt"][gi], ref["dudt"][gi], ref["duabs"][gi])}
+    tau = wd.params.alpha_tau * ref["state"]["h"][gi] / ref["vsig"][gi]
+    rs = ref["state"]
+    sc_a = np.abs(rs["alpha"][gi] - wd.params.alpha_min) / tau + wd.params.alpha_source * rs["f"][gi] * np.abs(divv[gi])
+    e["dalpha"] = _rel(res["dalpha"][gi], ref["dalpha"][gi], sc_a)
+    sc_u = (np.abs(rs["alpha_u"][gi] - wd.params.alpha_u_min) / tau +
+            ref["state"]["h"][gi] * ref["lapabs"][gi] / np.sqrt(rs["u"][gi]))
+    e["dalpha_u"] = _rel(res["dalpha_u"][gi], ref["dalpha_u"][gi], sc_u)
+    oh = np.stack([ref["hfar"], ref["hnear"], ref["hsph"]], 1)[sidx]
+    bad = np.any(res["hashes"][sidx] != oh, axis=1)
+    e["set_mismatches"] = int(bad.sum())
+    e["set_mismatches_explained"] = int((ref["margin"][sidx][bad] < EXPLAIN_MARGIN).sum())
+    ok = all(v["median"] <= TOL_MEDIAN and v["p99"] <= TOL_P99 for v in e.values() if isinstance(v, dict))
+    e["within_tolerance"] = bool(ok and e["set_mismatches"] == e["set_mismatches_explained"])
+    e["sample"] = f"{len(sidx)} particles (seed 17), {len(gi)} gas"
+    out["accuracy"] = e
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -590,6 +671,7 @@ def main():
     forms = {main_form: value}
     accuracy = None
     ostate = None
+    diss_block = None
     if not args.no_forms:
         g_main = gpu_check_step(E, ctx, ds, offsets)
         rates, results = other_forms(torch, dev, stream, E, DeviceSet, w, max(2, min(args.steps, 5)), prec,
@@ -615,6 +697,10 @@ def main():
         for name, g in results.items():
             if name != main_form:
                 accuracy[f"{name}_vs_{main_form}"] = _rel(A(g), A(g_main))
+        # the dissipation variants (Sect. 3.3.3) on the gas of a single system
+        if w.params.sph and w.n_gas > 0 and offsets is None and rank == 0 and world == 1:
+            diss_block = dissipation_form(torch, dev, stream, E, DeviceSet, w, max(2, min(args.steps, 5)),
+                                          int(ds.params.leaf_size), ostate)
 
     # ---- roofline of the dominant kernel (the force walk) ----
     far, pp, sph, soft = float(cnt[0]), float(cnt[1]), float(cnt[2]), float(cnt[8])
@@ -670,6 +756,7 @@ def main():
                 "counters": cnt,
                 "forms_particles_per_s": forms,
                 "forms_accuracy": accuracy,
+                "dissipation_variants": diss_block,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": None}
         lps = launches_per_step(w)

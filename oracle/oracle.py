@@ -353,7 +353,8 @@ def _dissipation_rates(w, p, res, st):
     printed e-folding constant."""
     n, ng = w.n, w.n_gas
     h, vs = st["h"][:ng], res["vsig"][:ng]
-    tau = float(getattr(p, "alpha_tau", 0.1)) * h / vs
+    with np.errstate(divide="ignore"):        # particles outside an index sample have v^sig = 0
+        tau = float(getattr(p, "alpha_tau", 0.1)) * h / vs
     out = {}
     if getattr(p, "variable_alpha", 0):
         da = np.zeros(n)
@@ -388,10 +389,13 @@ def kdk(w, dt: float, nsteps: int, params=None):
     U = w.u.astype(np.float64).copy()
     cur = copy.copy(w)
 
+    sw = _Switches(w, p, cur)
+
     def forces():
         cur.x, cur.y, cur.z = (np.ascontiguousarray(X[:, a], np.float32) for a in range(3))
         cur.vx, cur.vy, cur.vz = (np.ascontiguousarray(V[:, a], np.float32) for a in range(3))
         cur.u = np.ascontiguousarray(U, np.float32)
+        sw.hand_over()
         r = force_step(cur, params=p)
         A = np.stack([r["ax"], r["ay"], r["az"]], 1)
         return A, r["dudt"], r
@@ -402,6 +406,7 @@ def kdk(w, dt: float, nsteps: int, params=None):
     for _ in range(nsteps):
         V += 0.5 * dt * A
         U[:ng] += 0.5 * dt * DU[:ng]
+        sw.kick(0.5 * dt, r)
         X += dt * V
         for a in range(3):
             if (getattr(p, "periodic_mask", 0) >> a) & 1:
@@ -409,8 +414,44 @@ def kdk(w, dt: float, nsteps: int, params=None):
         A, DU, r = forces()
         V += 0.5 * dt * A
         U[:ng] += 0.5 * dt * DU[:ng]
+        sw.kick(0.5 * dt, r)
     return {"x": X[:, 0], "y": X[:, 1], "z": X[:, 2], "vx": V[:, 0], "vy": V[:, 1], "vz": V[:, 2], "u": U,
-            "last": r}
+            **sw.result(), "last": r}
+
+
+class _Switches:
+    """The per-particle dissipation switches alpha_i (variable alpha) and alpha^u_i (conduction) as
+    integrator state: kept in FP64, handed to each force step rounded to float32, and advanced by
+    the kicks with their time derivatives, as u is (no prediction)."""
+
+    def __init__(self, w, p, cur):
+        ng = w.n_gas
+        self.cur = cur
+        self.al = (np.asarray(w.alpha, np.float64)[:ng].copy()
+                   if getattr(p, "variable_alpha", 0) and getattr(w, "alpha", None) is not None else None)
+        self.alu = (np.asarray(w.alpha_u, np.float64)[:ng].copy()
+                    if getattr(p, "conduction", 0) and getattr(w, "alpha_u", None) is not None else None)
+
+    def hand_over(self):
+        if self.al is not None:
+            self.cur.alpha = np.ascontiguousarray(self.al, np.float32)
+        if self.alu is not None:
+            self.cur.alpha_u = np.ascontiguousarray(self.alu, np.float32)
+
+    def kick(self, hdt, r):
+        ng = len(self.al) if self.al is not None else (len(self.alu) if self.alu is not None else 0)
+        if self.al is not None:
+            self.al += hdt * r["dalpha"][:ng]
+        if self.alu is not None:
+            self.alu += hdt * r["dalpha_u"][:ng]
+
+    def result(self):
+        out = {}
+        if self.al is not None:
+            out["alpha"] = self.al
+        if self.alu is not None:
+            out["alpha_u"] = self.alu
+        return out
 
 
 @dataclass
@@ -433,7 +474,8 @@ def timestep_criteria(w, res, vx, vy, vz, u, ts, params=None):
       dt_acc = eta_acc sqrt(L / |a|)
       dt_vel = eta_vel L / |v|                      (reading: the printed square root is not a time)
       dt_av  = eta_av |v| / |a|                     (reading: the same)
-      dt_C   = eta_C h / (h |div v| + c + 1.2 (alpha c + beta max_j |mu_ij|))     (gas)
+      dt_C   = eta_C h / (h |div v| + c + 1.2 (alpha c + beta max_j |mu_ij|))     (gas; alpha_i
+               with variable alpha)
       dt_u   = eta_u |u / (du/dt)|                                                 (gas)
     div v is the smoothing-kernel estimate of the continuity equation.  Returns a dict of arrays
     (inf where a criterion does not apply)."""
@@ -454,7 +496,9 @@ def timestep_criteria(w, res, vx, vy, vz, u, ts, params=None):
         if p.sph and ng:
             h = res["h"][:ng]
             c = res["c"][:ng]
-            den = h * np.abs(res["divv_h"][:ng]) + c + 1.2 * (p.alpha * c + p.beta * res["mumax"][:ng])
+            # alpha_i with variable alpha (the value the force step used)
+            al = res["state"]["alpha"][:ng] if getattr(p, "variable_alpha", 0) else p.alpha
+            den = h * np.abs(res["divv_h"][:ng]) + c + 1.2 * (al * c + p.beta * res["mumax"][:ng])
             c_[:ng] = ts.eta_courant * h / den if ts.eta_courant > 0 else np.inf
             uu[:ng] = ts.eta_u * np.abs(np.asarray(u[:ng], np.float64) / res["dudt"][:ng]) if ts.eta_u > 0 else np.inf
         out["courant"] = c_
@@ -488,10 +532,13 @@ def run(w, nsteps: int, ts: TimeStep, params=None, predicted=True):
     U = w.u.astype(np.float64).copy()
     cur = copy.copy(w)
 
+    sw = _Switches(w, p, cur)
+
     def forces(vel, uu):
         cur.x, cur.y, cur.z = (np.ascontiguousarray(X[:, a], np.float32) for a in range(3))
         cur.vx, cur.vy, cur.vz = (np.ascontiguousarray(vel[:, a], np.float32) for a in range(3))
         cur.u = np.ascontiguousarray(uu, np.float32)
+        sw.hand_over()
         r = force_step(cur, params=p)
         return np.stack([r["ax"], r["ay"], r["az"]], 1), r["dudt"], r
 
@@ -505,6 +552,7 @@ def run(w, nsteps: int, ts: TimeStep, params=None, predicted=True):
         dts.append(dt)
         V += 0.5 * dt * A
         U[:ng] += 0.5 * dt * DU[:ng]
+        sw.kick(0.5 * dt, r)
         X += dt * V
         for a in range(3):
             if (getattr(p, "periodic_mask", 0) >> a) & 1:
@@ -518,5 +566,6 @@ def run(w, nsteps: int, ts: TimeStep, params=None, predicted=True):
         A, DU, r = forces(Vp, Up)
         V += 0.5 * dt * A
         U[:ng] += 0.5 * dt * DU[:ng]
+        sw.kick(0.5 * dt, r)
     return {"x": X[:, 0], "y": X[:, 1], "z": X[:, 2], "vx": V[:, 0], "vy": V[:, 1], "vz": V[:, 2], "u": U,
-            "dts": dts, "last": r}
+            **sw.result(), "dts": dts, "last": r}

@@ -14,8 +14,8 @@
 int evol_launch_pack(evol_ctx *c, const evol_particles *p, const evol_params *prm, int do_grav, int do_sph);
 int evol_launch_unpermute_ex(evol_ctx *c, const evol_particles *p, const evol_outputs *o, int what, int add_acc);
 int evol_lengths_warps_per_block();
-int evol_launch_kick(evol_ctx *c, const evol_particles *p, float half_dt, const float *ax, const float *ay,
-                     const float *az, const float *dudt);
+int evol_launch_kick(evol_ctx *c, const evol_particles *p, const evol_params *prm, float half_dt, const float *ax,
+                     const float *ay, const float *az, const float *dudt, const float *dalpha, const float *dalpha_u);
 int evol_launch_drift(evol_ctx *c, const evol_particles *p, const evol_params *prm, float dt);
 int evol_noalloc_setup_current_device();
 
@@ -154,7 +154,7 @@ int record_phase(evol_ctx *c, int k, evol_particles *p, const evol_params *prm, 
     case 4: {
         int what = EVOL_UNPERM_ACC | (grav ? EVOL_UNPERM_EPSOUT : 0) |
                    (sph ? (EVOL_UNPERM_LENGTHS | EVOL_UNPERM_DENSITY | EVOL_UNPERM_DUDT) : 0) |
-                   (sph && evol_diss_on(prm) ? EVOL_UNPERM_DISS : 0);
+                   (sph ? evol_unperm_switches(prm) : 0);
         rc = evol_launch_unpermute(c, p, out, what);
         if (!rc) rc = evol_launch_diagnostics(c, p, prm);
         break;
@@ -242,7 +242,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     if (!rc && cudaMallocHost((void **)&c->h_sys_off, (NSYS_CAP + 1) * sizeof(int32_t)) != cudaSuccess) rc = EVOL_ENOMEM;
     rc |= dalloc(&d.hash3, 3 * n); rc |= dalloc(&d.cnt3, 3 * n);
     rc |= dalloc(&c->stage, 26 * n);
-    rc |= dalloc(&c->kdk_acc, 4 * n);
+    rc |= dalloc(&c->kdk_acc, 6 * n);
     for (int k = 0; k < 6 && !rc; ++k)
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) rc = EVOL_ECUDA;
     if (!rc) {
@@ -341,7 +341,7 @@ int evol_sph_forces(evol_ctx *c, const evol_particles *p, const evol_params *prm
     if ((rc = evol_launch_node_lengths(c, prm, (int)p->n_gas))) return set_err(c, rc);
     if ((rc = evol_launch_walk(c, p, prm, 0, 1))) return set_err(c, rc);
     if ((rc = evol_launch_unpermute_ex(c, p, out,
-                                       EVOL_UNPERM_ACC | EVOL_UNPERM_DUDT | (evol_diss_on(prm) ? EVOL_UNPERM_DISS : 0),
+                                       EVOL_UNPERM_ACC | EVOL_UNPERM_DUDT | evol_unperm_switches(prm),
                                        1)))
         return set_err(c, rc);
     return EVOL_OK;
@@ -459,6 +459,8 @@ int evol_kdk(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_output
     o.ay = c->kdk_acc + cap;
     o.az = c->kdk_acc + 2 * cap;
     o.dudt = c->kdk_acc + 3 * cap;
+    o.dalpha = c->kdk_acc + 4 * cap;
+    o.dalpha_u = c->kdk_acc + 5 * cap;
     // forces at the starting positions
     if ((rc = evol_step(c, p, prm, &o))) return rc;
     if (nsteps > 0) {
@@ -489,10 +491,10 @@ int evol_kdk(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_output
             if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
                 prc = EVOL_ECUDA;
             } else {
-                prc = evol_launch_kick(c, p, 0.5f * dt, o.ax, o.ay, o.az, o.dudt);
+                prc = evol_launch_kick(c, p, prm, 0.5f * dt, o.ax, o.ay, o.az, o.dudt, o.dalpha, o.dalpha_u);
                 if (!prc) prc = evol_launch_drift(c, p, prm, dt);
                 for (int k = 0; k < NPHASE && !prc; ++k) prc = record_phase(c, k, p, prm, &o);
-                if (!prc) prc = evol_launch_kick(c, p, 0.5f * dt, o.ax, o.ay, o.az, o.dudt);
+                if (!prc) prc = evol_launch_kick(c, p, prm, 0.5f * dt, o.ax, o.ay, o.az, o.dudt, o.dalpha, o.dalpha_u);
                 cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
                 if (!prc && (e != cudaSuccess || !graph)) prc = EVOL_ECUDA;
                 if (!prc && cudaGraphInstantiate(&c->kdk_exec, graph, 0) != cudaSuccess) {
@@ -512,13 +514,14 @@ int evol_kdk(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_output
         for (int k = 0; k < nsteps; ++k)
             if (cudaGraphLaunch(c->kdk_exec, c->stream) != cudaSuccess) return set_err(c, EVOL_ECUDA);
     }
-    // hand the last accelerations and du/dt to the caller
+    // hand the last accelerations, du/dt and switch rates to the caller
     const int64_t n = p->n, ng = p->n_gas;
-    float *dst[4] = {out ? out->ax : nullptr, out ? out->ay : nullptr, out ? out->az : nullptr,
-                     out ? out->dudt : nullptr};
-    const float *src[4] = {o.ax, o.ay, o.az, o.dudt};
-    const int64_t len[4] = {n, n, n, ng};
-    for (int k = 0; k < 4; ++k)
+    float *dst[6] = {out ? out->ax : nullptr, out ? out->ay : nullptr, out ? out->az : nullptr,
+                     out ? out->dudt : nullptr, out && prm->variable_alpha ? out->dalpha : nullptr,
+                     out && prm->conduction ? out->dalpha_u : nullptr};
+    const float *src[6] = {o.ax, o.ay, o.az, o.dudt, o.dalpha, o.dalpha_u};
+    const int64_t len[6] = {n, n, n, ng, ng, ng};
+    for (int k = 0; k < 6; ++k)
         if (dst[k] && len[k] > 0)
             cudaMemcpyAsync(dst[k], src[k], len[k] * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
     return EVOL_OK;
@@ -542,6 +545,8 @@ int evol_run(evol_ctx *c, evol_particles *p, const evol_params *prm, const evol_
     o.ay = c->kdk_acc + cap;
     o.az = c->kdk_acc + 2 * cap;
     o.dudt = c->kdk_acc + 3 * cap;
+    o.dalpha = c->kdk_acc + 4 * cap;
+    o.dalpha_u = c->kdk_acc + 5 * cap;
     const double t0 = time ? *time : 0.0;
     if (cudaMemcpyAsync(c->d.time, &t0, sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return set_err(c, EVOL_ECUDA);
@@ -611,13 +616,14 @@ int evol_run(evol_ctx *c, evol_particles *p, const evol_params *prm, const evol_
             }
     }
     c->want_divv = 0;
-    // hand the last accelerations and du/dt to the caller
+    // hand the last accelerations, du/dt and switch rates to the caller
     const int64_t n = p->n, ng = p->n_gas;
-    float *dst[4] = {out ? out->ax : nullptr, out ? out->ay : nullptr, out ? out->az : nullptr,
-                     out ? out->dudt : nullptr};
-    const float *src[4] = {o.ax, o.ay, o.az, o.dudt};
-    const int64_t len[4] = {n, n, n, ng};
-    for (int k = 0; k < 4; ++k)
+    float *dst[6] = {out ? out->ax : nullptr, out ? out->ay : nullptr, out ? out->az : nullptr,
+                     out ? out->dudt : nullptr, out && prm->variable_alpha ? out->dalpha : nullptr,
+                     out && prm->conduction ? out->dalpha_u : nullptr};
+    const float *src[6] = {o.ax, o.ay, o.az, o.dudt, o.dalpha, o.dalpha_u};
+    const int64_t len[6] = {n, n, n, ng, ng, ng};
+    for (int k = 0; k < 6; ++k)
         if (dst[k] && len[k] > 0)
             cudaMemcpyAsync(dst[k], src[k], len[k] * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
     double tt = t0;

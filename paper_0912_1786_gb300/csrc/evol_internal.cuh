@@ -137,13 +137,20 @@ int evol_launch_integrator_step(evol_ctx *c, const evol_particles *p, const evol
 #define EVOL_UNPERM_ACC     4
 #define EVOL_UNPERM_DUDT    8
 #define EVOL_UNPERM_EPSOUT  16
-#define EVOL_UNPERM_DISS    32
+#define EVOL_UNPERM_DALPHA  32
+#define EVOL_UNPERM_DALPHA_U 64
 
 // Any dissipation variant of Sect. 3.3.3 on (they act on SPH pairs only).
 static inline bool evol_diss_on(const evol_params *prm)
 {
     return prm->sph &&
            (prm->visc_form != EVOL_VISC_MONAGHAN || prm->balsara || prm->variable_alpha || prm->conduction);
+}
+// The switch rates a step writes out (variable alpha, conduction).
+static inline int evol_unperm_switches(const evol_params *prm)
+{
+    return (prm->sph && prm->variable_alpha ? EVOL_UNPERM_DALPHA : 0) |
+           (prm->sph && prm->conduction ? EVOL_UNPERM_DALPHA_U : 0);
 }
 // The Balsara factor (limiter, alpha source) needs div v and |curl v| from the h solve.
 static inline bool evol_needs_curl(const evol_params *prm) { return prm->sph && (prm->balsara || prm->variable_alpha); }

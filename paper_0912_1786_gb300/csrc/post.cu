@@ -108,10 +108,8 @@ __global__ void k_unpermute(int n, int n_gas, int what, int add_acc, evol_dev d,
         }
     }
     if ((what & EVOL_UNPERM_DUDT) && gas) put(dudt, d.dudt[s]);
-    if ((what & EVOL_UNPERM_DISS) && gas) {
-        if (dalpha) put(dalpha, d.dalpha[s]);
-        if (dalpha_u) put(dalpha_u, d.dalpha_u[s]);
-    }
+    if ((what & EVOL_UNPERM_DALPHA) && gas && dalpha) put(dalpha, d.dalpha[s]);
+    if ((what & EVOL_UNPERM_DALPHA_U) && gas && dalpha_u) put(dalpha_u, d.dalpha_u[s]);
     if (!fin) evol_flag(d.err, EVOL_ENAN);
 }
 
@@ -169,8 +167,21 @@ __global__ void k_diag_final(int nparts, const double *part, const int32_t *nnod
 
 // Leapfrog pieces (Sect. 4.1, KDK): half kick of v (and u for gas), drift of x with periodic
 // wrapping, in the caller's order.
+// Per-particle switches advanced with the kicks, like u (caller order, gas): alpha by d alpha/dt
+// and alpha^u by d alpha^u/dt, each only where both pointers are set.
+struct SwitchKick {
+    float *alpha, *alpha_u;
+    const float *dalpha, *dalpha_u;
+};
+
+__device__ __forceinline__ void kick_switches(const SwitchKick &sk, int i, float hdt)
+{
+    if (sk.alpha && sk.dalpha) sk.alpha[i] += hdt * sk.dalpha[i];
+    if (sk.alpha_u && sk.dalpha_u) sk.alpha_u[i] += hdt * sk.dalpha_u[i];
+}
+
 __global__ void k_kick(int n, int n_gas, float half_dt, float *vx, float *vy, float *vz, float *u, const float *ax,
-                       const float *ay, const float *az, const float *dudt)
+                       const float *ay, const float *az, const float *dudt, SwitchKick sk)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -178,6 +189,7 @@ __global__ void k_kick(int n, int n_gas, float half_dt, float *vx, float *vy, fl
     vy[i] += half_dt * ay[i];
     vz[i] += half_dt * az[i];
     if (u && dudt && i < n_gas) u[i] += half_dt * dudt[i];
+    if (i < n_gas) kick_switches(sk, i, half_dt);
 }
 
 __global__ void k_drift(int n, float dt, float *x, float *y, float *z, const float *vx, const float *vy,
@@ -211,6 +223,7 @@ __global__ void k_drift(int n, float dt, float *x, float *y, float *z, const flo
 struct TsParams {
     float eta_acc, eta_vel, eta_av, eta_c, eta_u, alpha, beta;
     int gravity, sph;
+    int var_alpha;           // the Courant term takes alpha_i (packed with the dissipation operands)
 };
 
 __global__ void k_dt_criteria(int n, int n_gas, evol_dev d, TsParams tp, const float *vx, const float *vy,
@@ -232,8 +245,9 @@ __global__ void k_dt_criteria(int n, int n_gas, evol_dev d, TsParams tp, const f
         if (gas) {
             const int s = d.inv[j];
             const float cs = d.snd[s].x, hj = h[j];
+            const float al = tp.var_alpha ? d.diss[s].x : tp.alpha;
             if (tp.eta_c > 0.f)
-                c[3] = tp.eta_c * hj / (hj * fabsf(d.divv_h[s]) + cs + 1.2f * (tp.alpha * cs + tp.beta * d.mumax[s]));
+                c[3] = tp.eta_c * hj / (hj * fabsf(d.divv_h[s]) + cs + 1.2f * (al * cs + tp.beta * d.mumax[s]));
             if (tp.eta_u > 0.f) c[4] = tp.eta_u * fabsf(u[j] / acc[3 * stride + j]);
         }
 #pragma unroll
@@ -256,9 +270,9 @@ __global__ void k_dt_final(float *dt, const unsigned *dtbits, double *time, floa
     *time += (double)v;
 }
 
-// Kick with the device time step: v += f dt a (u += f dt du/dt for gas), caller order.
+// Kick with the device time step: v += f dt a (u += f dt du/dt and the switches for gas), caller order.
 __global__ void k_kick_dev(int n, int n_gas, const float *dtp, float f, float *vx, float *vy, float *vz, float *u,
-                           const float *acc, int64_t stride)
+                           const float *acc, int64_t stride, SwitchKick sk)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -267,6 +281,7 @@ __global__ void k_kick_dev(int n, int n_gas, const float *dtp, float f, float *v
     vy[i] += hdt * acc[stride + i];
     vz[i] += hdt * acc[2 * stride + i];
     if (u && i < n_gas) u[i] += hdt * acc[3 * stride + i];
+    if (i < n_gas) kick_switches(sk, i, hdt);
 }
 
 __global__ void k_drift_dev(int n, const float *dtp, float *x, float *y, float *z, const float *vx, const float *vy,
@@ -308,12 +323,28 @@ __global__ void k_predict_lengths(int n, int n_gas, evol_dev d, const float *dtp
 
 }  // namespace
 
-int evol_launch_kick(evol_ctx *c, const evol_particles *p, float half_dt, const float *ax, const float *ay,
-                     const float *az, const float *dudt)
+static SwitchKick switch_kick(const evol_particles *p, const evol_params *prm, const float *dalpha,
+                              const float *dalpha_u)
+{
+    SwitchKick sk{};
+    if (prm->sph && prm->variable_alpha) {
+        sk.alpha = (float *)p->alpha;
+        sk.dalpha = dalpha;
+    }
+    if (prm->sph && prm->conduction) {
+        sk.alpha_u = (float *)p->alpha_u;
+        sk.dalpha_u = dalpha_u;
+    }
+    return sk;
+}
+
+int evol_launch_kick(evol_ctx *c, const evol_particles *p, const evol_params *prm, float half_dt, const float *ax,
+                     const float *ay, const float *az, const float *dudt, const float *dalpha, const float *dalpha_u)
 {
     int n = (int)p->n;
     k_kick<<<(n + 255) / 256, 256, 0, c->stream>>>(n, (int)p->n_gas, half_dt, (float *)p->vx, (float *)p->vy,
-                                                   (float *)p->vz, (float *)p->u, ax, ay, az, dudt);
+                                                   (float *)p->vz, (float *)p->u, ax, ay, az, dudt,
+                                                   switch_kick(p, prm, dalpha, dalpha_u));
     return evol_cuda_ok(cudaGetLastError());
 }
 
@@ -368,7 +399,8 @@ int evol_launch_diagnostics(evol_ctx *c, const evol_particles *p, const evol_par
 
 // One global-step KDK step around a force step: stage 0 = time step, first half kick, drift and
 // the predicted starting lengths; stage 1 = the second half kick.  The accelerations and du/dt of
-// the last force step are c->kdk_acc (caller order: ax | ay | az | du/dt, c->cap apart).
+// the last force step are c->kdk_acc (caller order: ax | ay | az | du/dt | d alpha/dt | d alpha^u/dt,
+// c->cap apart).
 int evol_launch_integrator_step(evol_ctx *c, const evol_particles *p, const evol_params *prm, const evol_integrator *ip,
                                 int stage)
 {
@@ -376,16 +408,17 @@ int evol_launch_integrator_step(evol_ctx *c, const evol_particles *p, const evol
     const int tb = 256, gb = (n + tb - 1) / tb;
     const int64_t cap = c->cap;
     unsigned *dtbits = reinterpret_cast<unsigned *>(c->d.dt + 1);
+    const SwitchKick sk = switch_kick(p, prm, c->kdk_acc + 4 * cap, c->kdk_acc + 5 * cap);
     if (stage == 0) {
         TsParams tp{ip->eta_acc, ip->eta_vel, ip->eta_av, ip->eta_courant, ip->eta_u, prm->alpha, prm->beta,
-                    prm->gravity, prm->sph && p->n_gas > 0};
+                    prm->gravity, prm->sph && p->n_gas > 0, prm->sph && prm->variable_alpha};
         // all bits set: above every non-negative float's bits, so the first criterion replaces it
         cudaMemsetAsync(dtbits, 0xff, sizeof(unsigned), c->stream);
         k_dt_criteria<<<c->num_sms * 4, 256, 0, c->stream>>>(n, ng, c->d, tp, p->vx, p->vy, p->vz, p->u, c->kdk_acc,
                                                               cap, p->h, p->eps, dtbits);
         k_dt_final<<<1, 32, 0, c->stream>>>(c->d.dt, dtbits, c->d.time, ip->dt_min, ip->dt_max);
         k_kick_dev<<<gb, tb, 0, c->stream>>>(n, ng, c->d.dt, 0.5f, (float *)p->vx, (float *)p->vy, (float *)p->vz,
-                                             (float *)p->u, c->kdk_acc, cap);
+                                             (float *)p->u, c->kdk_acc, cap, sk);
         k_drift_dev<<<gb, tb, 0, c->stream>>>(
             n, c->d.dt, (float *)p->x, (float *)p->y, (float *)p->z, p->vx, p->vy, p->vz, prm->periodic_mask,
             prm->periodic_lo[0], prm->periodic_lo[1], prm->periodic_lo[2], prm->periodic_hi[0] - prm->periodic_lo[0],
@@ -396,7 +429,7 @@ int evol_launch_integrator_step(evol_ctx *c, const evol_particles *p, const evol
                                                         prm->gravity && prm->adaptive_softening);
     } else {
         k_kick_dev<<<gb, tb, 0, c->stream>>>(n, ng, c->d.dt, 0.5f, (float *)p->vx, (float *)p->vy, (float *)p->vz,
-                                             (float *)p->u, c->kdk_acc, cap);
+                                             (float *)p->u, c->kdk_acc, cap, sk);
     }
     return evol_cuda_ok(cudaGetLastError());
 }

@@ -141,3 +141,70 @@ def test_dissipation_arguments_rejected():
         assert E.evol_sync(ctx) == 0
     finally:
         E.evol_destroy(ctx)
+
+
+def _run_device(w, nsteps, ts=None, kdk_dt=None):
+    """evol_run (global step, ts given) or evol_kdk (fixed step kdk_dt); returns the final state
+    including alpha and alpha^u, and the last force step's outputs."""
+    import torch
+    from paper_0912_1786_gb300 import build, evol as E
+    from paper_0912_1786_gb300.device import DeviceSet
+    build.build()
+    ds = DeviceSet(w)
+    ctx = E.evol_create(w.n, torch.cuda.current_stream().cuda_stream)
+    try:
+        if ts is not None:
+            ip = E.make_integrator(ts.eta_acc, ts.eta_vel, ts.eta_av, ts.eta_courant, ts.eta_u, ts.dt_min, ts.dt_max,
+                                   1, 1)
+            t, _ = E.evol_run(ctx, ds.particles, ds.params, ip, ds.outputs, nsteps)
+        else:
+            E.evol_kdk(ctx, ds.particles, ds.params, ds.outputs, kdk_dt, nsteps)
+            t = nsteps * kdk_dt
+        assert E.evol_sync(ctx, raise_on_error=False) == 0
+        st = {k: v.cpu().numpy().astype(np.float64) for k, v in ds.inp.items()}
+        st.update({k: v.cpu().numpy().astype(np.float64) for k, v in ds.out.items()})
+    finally:
+        E.evol_destroy(ctx)
+    return t, st
+
+
+def test_fixed_step_kdk_decays_the_switches_of_static_gas():
+    # closed form (the oracle pins the same scheme): a static periodic lattice, no forces; with
+    # x = k dt/2, k = 2c/(0.1 h), alpha - alpha_min ends at (1 - x)^2 (1 - 2x)^(N-1) of its start
+    nx = 16
+    g = (np.arange(nx) + 0.5) / nx
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    n = len(P)
+    rng = np.random.default_rng(48)
+    f = lambda a: np.ascontiguousarray(a, np.float32)
+    p = W.Params(theta=0.5, gravity=0, sph=1, adaptive_softening=0, n_nei_sph=40.0, leaf_size=8,
+                 periodic_mask=7, periodic_lo=(0, 0, 0), periodic_hi=(1, 1, 1), variable_alpha=1, conduction=1,
+                 alpha_min=0.0625, alpha_u_min=0.0)
+    u = 0.7
+    w = W.Workload("lattice", f(P[:, 0]), f(P[:, 1]), f(P[:, 2]), *(f(np.zeros(n)),) * 3, f(np.full(n, 1.0 / n)),
+                   f(np.full(n, u)), f(np.full(n, 1.2 / nx)), f(np.full(n, 1.2 / nx)), n_gas=n, params=p)
+    w.alpha = f(rng.uniform(0.1, 1.5, n))
+    w.alpha_u = f(rng.uniform(0.0, 1.0, n))
+    o = oracle.force_step(w)
+    k = float(np.median(o["vsig"] / (0.1 * o["h"])))
+    dt = 0.2 / k
+    _, st = _run_device(w, 3, kdk_dt=dt)
+    fac = (1.0 - 0.1) ** 2 * (1.0 - 0.2) ** 2
+    assert_tol("alpha_decay", st["alpha"] - 0.0625, (w.alpha.astype(np.float64) - 0.0625) * fac)
+    assert_tol("alpha_u_decay", st["alpha_u"], w.alpha_u.astype(np.float64) * fac)
+
+
+def test_global_step_run_tracks_the_oracle_with_all_variants():
+    w = W.with_dissipation(W.evrard_sphere(2048, seed=49, sigma_v=0.1), seed=10, **ALL)
+    ts = oracle.TimeStep(eta_acc=0.1, eta_courant=0.2, eta_u=0.2, dt_max=0.05)
+    o = oracle.run(w, 3, ts)
+    t, g = _run_device(w, 3, ts=ts)
+    assert abs(t - sum(o["dts"])) <= 1e-4 * sum(o["dts"])
+    X = np.stack([g["x"], g["y"], g["z"]], 1)
+    Xo = np.stack([o["x"], o["y"], o["z"]], 1)
+    err = np.linalg.norm(X - Xo, axis=1)
+    assert np.median(err) < 1e-6 and err.max() < 1e-4, (np.median(err), err.max())
+    # the switches after three steps, on the scale of their change
+    for k in ("alpha", "alpha_u"):
+        a0 = getattr(w, k).astype(np.float64)
+        assert_tol(k + "_after_run", g[k] - a0, o[k] - a0, scale=np.abs(o[k] - a0) + 1e-3 * np.abs(a0))

@@ -351,3 +351,30 @@ def test_all_variants_conserve_momentum_and_energy():
     e = m * ((v * a).sum(1) + r["dudt"])
     assert abs(e.sum()) < 1e-13 * np.abs(m * (v * a).sum(1)).sum()
     assert np.all(np.isfinite(r["dalpha"])) and np.all(np.isfinite(r["dalpha_u"]))
+
+
+def test_switches_integrated_by_the_kicks():
+    # static periodic lattice: no forces, du/dt = 0, div v = 0, lap u = 0; each switch decays as
+    # d(a - a_min)/dt = -k (a - a_min), k = 2c / (0.1 h).  The kicks use the rate of the last force
+    # step, as for u.  With x = k dt/2, the value handed to the first force step is (1 - x) of the
+    # start, each later one (1 - 2x) of the one before, and a step ends at (1 - x) of its force
+    # step's value: after N steps a - a_min is (1 - x)^2 (1 - 2x)^(N-1) of its start.
+    nx = 8
+    g = (np.arange(nx) + 0.5) / nx
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    n = len(P)
+    rng = np.random.default_rng(47)
+    alpha = rng.uniform(0.1, 1.5, n).astype(np.float32)
+    alpha_u = rng.uniform(0.0, 1.0, n).astype(np.float32)
+    p = _params(n_nei_sph=40.0, periodic_mask=7, periodic_lo=(0, 0, 0), periodic_hi=(1, 1, 1), variable_alpha=1,
+                conduction=1, alpha_min=0.0625, alpha_u_min=0.0)
+    w = _wl(P, np.full(n, 1.0 / n), u=np.full(n, 0.7), h=np.full(n, 1.2 / nx), params=p, alpha=alpha,
+            alpha_u=alpha_u)
+    r0 = oracle.force_step(w)
+    k = r0["vsig"] / (0.1 * r0["h"])
+    assert np.allclose(k, k[0], rtol=1e-12)
+    dt = 0.2 / k[0]                        # k dt / 2 = 0.1
+    res = oracle.kdk(w, dt, 3)
+    f = (1.0 - 0.1) ** 2 * (1.0 - 0.2) ** 2
+    assert np.allclose(res["alpha"] - 0.0625, (alpha.astype(np.float64) - 0.0625) * f, rtol=1e-6, atol=0)
+    assert np.allclose(res["alpha_u"], alpha_u.astype(np.float64) * f, rtol=1e-6, atol=0)
