@@ -511,6 +511,54 @@ static int64_t orc_gather(const orc_tree *t, const orc_period *pp, const double 
  *         from L_grav (Eq. Lgrav) for unequal masses gives the mass-weighted X, which equals
  *         m * xi for equal masses.  The double sum in L_grav includes k = j, so X does too.
  * Returns 0, or -2 if no root exists (too few particles), -3 on neighbour overflow. */
+static int orc_cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* The "standard SPH scheme" of Sect. 3 (the alternative to the n-h relation): h is chosen so that
+ * a fixed number N of gas particles, the particle itself included, lies inside the kernel's
+ * support sphere r < 2h, and the grad-h terms are dropped (Omega* = 1, zeta = 0).  Reading: the
+ * sphere is the kernel support 2h, which keeps N the same neighbour number as in
+ * N = 4/3 pi (2 eta)^3 of the n-h scheme; any 2h in (r_(N), r_(N+1)] holds exactly N particles
+ * (r_(k): the k-th smallest distance, r_(1) = 0 the particle itself), and the midpoint
+ * h = (r_(N) + r_(N+1)) / 4 is taken, the choice farthest from changing the count.  Then n and rho
+ * are the usual kernel sums at that h.  out as orc_solve_one, mode 0. */
+static int orc_solve_standard(const orc_tree *t, const orc_period *pp, int nstd, int64_t i, double guess,
+                              double *out, int64_t *scratch, double *rscr, int64_t cap)
+{
+    double p[3] = {t->x[i], t->y[i], t->z[i]};
+    double R = (guess > 0 ? 2.0 * guess * 1.25 : 2.0 * t->side / cbrt((double)t->n));
+    double span = t->side * 4.0;
+    int64_t cnt;
+    for (;;) {
+        cnt = orc_gather(t, pp, p, R, 1, scratch, rscr, cap);
+        if (cnt < 0) return -3;
+        if (cnt >= nstd + 1) break;
+        if (R > span) return -2;         /* fewer than N + 1 gas particles in reach */
+        R *= 2.0;
+    }
+    /* every particle closer than the (N+1)-th is inside R: sort the distances (indices follow) */
+    double *rs = malloc(cnt * sizeof(double));
+    if (!rs) return -3;
+    memcpy(rs, rscr, cnt * sizeof(double));
+    qsort(rs, cnt, sizeof(double), orc_cmp_double);
+    double L = 0.25 * (rs[nstd - 1] + rs[nstd]);
+    free(rs);
+    double nsum = 0, rho = 0;
+    for (int64_t k = 0; k < cnt; ++k) {
+        nsum += orc_W(rscr[k], L);
+        rho += t->m[scratch[k]] * orc_W(rscr[k], L);
+    }
+    out[0] = L;
+    out[1] = nsum;
+    out[2] = rho;
+    out[3] = 1.0;      /* Omega*: grad-h terms dropped */
+    out[4] = 0.0;      /* zeta */
+    return 0;
+}
+
 static int orc_solve_one(const orc_tree *t, const orc_period *pp, int mode, double eta, int64_t i,
                          double guess, double *out /* [5] */, int64_t *scratch, double *rscr, int64_t cap)
 {
@@ -564,9 +612,10 @@ static int orc_solve_one(const orc_tree *t, const orc_period *pp, int mode, doub
 }
 
 /* Solve for the particles listed in idx (all particles of the mode's species if idx == NULL).
- * guess: original-order float array of starting lengths (may be NULL).  Outputs are written at
- * the particle's original index in out0..out4 (arrays of length n).  Returns 0 or the first
- * error code met. */
+ * mode 0: gas h from the n-h relation; 1: eps; 2: gas h of the standard scheme with
+ * N = n_nei (rounded) neighbours.  guess: original-order float array of starting lengths (may be
+ * NULL).  Outputs are written at the particle's original index in out0..out4 (arrays of length
+ * n).  Returns 0 or the first error code met. */
 int orc_solve_lengths(const orc_tree *t, int mode, double n_nei, const int64_t *idx, int64_t nidx,
                       const float *guess, int periodic_mask, const double *plo, const double *phi_,
                       double *out0, double *out1, double *out2, double *out3, double *out4)
@@ -575,7 +624,8 @@ int orc_solve_lengths(const orc_tree *t, int mode, double n_nei, const int64_t *
     orc_period per = {periodic_mask, {0, 0, 0}, {1, 1, 1}};
     for (int a = 0; a < 3; ++a)
         if ((periodic_mask >> a) & 1) { per.lo[a] = plo[a]; per.len[a] = phi_[a] - plo[a]; }
-    int64_t count = idx ? nidx : (mode == 0 ? t->n_gas : t->n);
+    int64_t count = idx ? nidx : (mode != 1 ? t->n_gas : t->n);
+    int nstd = (int)nearbyint(n_nei);
     int err = 0;
 #pragma omp parallel
     {
@@ -586,7 +636,10 @@ int orc_solve_lengths(const orc_tree *t, int mode, double n_nei, const int64_t *
         for (int64_t q = 0; q < count; ++q) {
             int64_t i = idx ? idx[q] : q;
             double o[5];
-            int rc = (scr && rs) ? orc_solve_one(t, &per, mode, eta, i, guess ? guess[i] : 0.0, o, scr, rs, cap) : -3;
+            double gs = guess ? guess[i] : 0.0;
+            int rc = !(scr && rs) ? -3
+                     : mode == 2  ? orc_solve_standard(t, &per, nstd, i, gs, o, scr, rs, cap)
+                                  : orc_solve_one(t, &per, mode, eta, i, gs, o, scr, rs, cap);
             if (rc != 0) {
 #pragma omp critical
                 if (!err) err = rc;

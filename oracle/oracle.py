@@ -177,7 +177,8 @@ class OracleTree:
         return int(getattr(params, "periodic_mask", 0)), lo, hi
 
     def solve_lengths(self, mode: int, n_nei: float, guess=None, idx=None, params=None):
-        """mode 0: gas h -> (h, n, rho, Omega*, zeta); mode 1: eps -> (eps, n, Upsilon, X)."""
+        """mode 0: gas h -> (h, n, rho, Omega*, zeta); mode 1: eps -> (eps, n, Upsilon, X);
+        mode 2: gas h of the standard scheme (N = n_nei neighbours inside 2h) -> (h, n, rho, 1, 0)."""
         n = self.n
         outs = [np.zeros(n) for _ in range(5)]
         pm, lo, hi = self._period(params)
@@ -277,7 +278,8 @@ def force_step(w, params=None, idx=None, use_tc=None, tree=None, fixed_lengths=N
             res.update(eps=eps, n_eps=neps, ups=ups, X=X)
         if p.sph and w.n_gas > 0:
             gidx = np.arange(w.n_gas, dtype=np.int64)
-            h, nh, rho, om, zeta = t.solve_lengths(0, p.n_nei_sph, guess=w.h, idx=gidx, params=p)
+            hmode = 2 if int(getattr(p, "sph_scheme", 0)) == 1 else 0
+            h, nh, rho, om, zeta = t.solve_lengths(hmode, p.n_nei_sph, guess=w.h, idx=gidx, params=p)
             P, c = np.zeros(n), np.zeros(n)
             lib().orc_eos(n, float(p.gamma), _c(rho, np.float64), _c(w.u.astype(np.float64), np.float64), P, c)
             P[w.n_gas:] = 0
