@@ -58,6 +58,13 @@ extern "C" {
 #define EVOL_COND_SRC_SQRTU       0  /* conductivity switch source h |lap u| / sqrt(u) */
 #define EVOL_COND_SRC_LINEAR      1  /* 0.1 h |lap u| */
 
+/* ---- SPH schemes (Sect. 3) ------------------------------------------------------------ */
+#define EVOL_SPH_LAGRANGIAN       0  /* h from the n-h relation h^3 n(h) = eta^3, grad-h terms kept */
+#define EVOL_SPH_STANDARD         1  /* h with N = n_nei_sph (rounded) gas particles, the particle
+                                        itself included, inside 2h: h = (r_(N) + r_(N+1)) / 4 from
+                                        the N-th and (N+1)-th smallest gas distances; grad-h terms
+                                        dropped (Omega* = 1, zeta = 0) */
+
 /* ---- precision forms -------------------------------------------------------------- */
 #define EVOL_FP32_PLAIN  0   /* FP32 moments and FP32 accumulation of per-particle sums */
 #define EVOL_FP32_MIXED  1   /* FP64 multipole/centre-of-mass accumulation and FP64 totals of
@@ -119,6 +126,8 @@ typedef struct {
     int cond_source;           /* S^u from Brookshaw's lap u_i = sum_j 2 m_j (u_i - u_j)/rho_j
                                   |gradbar W_ij|/r_ij: EVOL_COND_SRC_SQRTU or EVOL_COND_SRC_LINEAR */
     float alpha_u_min;         /* paper: 0 */
+    int sph_scheme;            /* EVOL_SPH_LAGRANGIAN (0) or EVOL_SPH_STANDARD; the standard scheme
+                                  needs 1 <= n_nei_sph (rounded) <= 335 */
 } evol_params;
 
 /* Outputs, caller order.  Any pointer may be NULL (not written). */

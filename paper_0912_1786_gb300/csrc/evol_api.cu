@@ -14,6 +14,7 @@
 int evol_launch_pack(evol_ctx *c, const evol_particles *p, const evol_params *prm, int do_grav, int do_sph);
 int evol_launch_unpermute_ex(evol_ctx *c, const evol_particles *p, const evol_outputs *o, int what, int add_acc);
 int evol_lengths_warps_per_block();
+int evol_lengths_list_cap();
 int evol_launch_kick(evol_ctx *c, const evol_particles *p, const evol_params *prm, float half_dt, const float *ax,
                      const float *ay, const float *az, const float *dudt, const float *dalpha, const float *dalpha_u);
 int evol_launch_drift(evol_ctx *c, const evol_particles *p, const evol_params *prm, float dt);
@@ -83,6 +84,11 @@ int check_args(evol_ctx *c, const evol_particles *p, const evol_params *prm)
     if (prm->cond_source != EVOL_COND_SRC_SQRTU && prm->cond_source != EVOL_COND_SRC_LINEAR) return EVOL_EINVAL;
     if (prm->balsara && !(prm->balsara_eta >= 0.f)) return EVOL_EINVAL;
     if ((prm->variable_alpha || prm->conduction) && !(prm->alpha_tau > 0.f)) return EVOL_EINVAL;
+    if (prm->sph_scheme != EVOL_SPH_LAGRANGIAN && prm->sph_scheme != EVOL_SPH_STANDARD) return EVOL_EINVAL;
+    if (prm->sph && prm->sph_scheme == EVOL_SPH_STANDARD) {
+        const long nstd = lrintf(prm->n_nei_sph);
+        if (nstd < 1 || nstd + 1 > evol_lengths_list_cap()) return EVOL_EINVAL;
+    }
     if (prm->sph && p->n_gas > 0) {
         if (prm->variable_alpha && !p->alpha) return EVOL_EINVAL;
         if (prm->conduction && !p->alpha_u) return EVOL_EINVAL;

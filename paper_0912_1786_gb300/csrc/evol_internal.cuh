@@ -236,6 +236,7 @@ struct evol_kparams {
     int nsys;
     int want_divv;           // length solves also form div v
     int want_curl;           // the h solve also forms |curl v| (Balsara limiter, alpha switch)
+    int standard, nstd;      // h solve by the standard scheme with nstd neighbours inside 2h
     // dissipation variants (Sect. 3.3.3); diss = any of them on
     int diss, visc_form, balsara, var_alpha, conduction, cond_vsig, cond_source;
     float alpha_min, alpha_tau, alpha_source, alpha_u_min;

@@ -23,6 +23,10 @@
 //                           X = -(pi eps^2/(3 Sw)) sum_k m_k eps^2 dphi/deps   (Sect. 2.1)
 // On request, either mode:   div v = 3 sum_j ((v_i - v_j).(r_i - r_j)/r_ij) w'(u) / (L Suw)
 //                           (the discretised continuity equation of Sect. 2.1)
+// Standard SPH scheme (Sect. 3, mode 0 on request): no root is solved.  Once a gathered ball holds
+// at least N + 1 gas particles (the particle itself included), h = (r_(N) + r_(N+1)) / 4 from the
+// N-th and (N+1)-th smallest distances, so that exactly N lie inside 2h; then one evaluation with
+// Omega* = 1, zeta = 0 (the grad-h terms are dropped) and div v, curl v normalised by n alone.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,6 +56,22 @@ struct LenSmem {
     float2 nb[LW_WARPS][PCAP];        // (distance, index bits) of the neighbours of the particle solved
     unsigned lc[LW_WARPS][4];         // work counts of the warp's current item (kept by lane 0)
 };
+
+// The k-th smallest (k >= 1) of the cnt <= PCAP listed distances: the smallest x with at least k
+// distances <= x, by bisection on the bit patterns (non-negative floats order like their bits).
+__device__ __forceinline__ float kth_distance(const float2 *nb, int cnt, int k, int lane)
+{
+    unsigned lo = 0u, hi = 0x7f800000u;
+    while (lo < hi) {
+        const unsigned mid = lo + ((hi - lo) >> 1);
+        int c = 0;
+        for (int e = lane; e < cnt; e += 32) c += __float_as_uint(nb[e].x) <= mid ? 1 : 0;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (c >= k) hi = mid;
+        else lo = mid + 1u;
+    }
+    return __uint_as_float(lo);
+}
 
 // Particles of the listed leaves against the particle at (px, py, pz), 32 at a time across
 // leaves: those within R2 (gas only in mode 0) are appended to the neighbour list.  Returns the
@@ -531,7 +551,24 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         continue;
                     }
                 }
-                // sums over the list: lane l takes entries l, l + 32, ...
+                if (MODE == 0 && kp.standard && status == ST_ACTIVE) {
+                    // standard scheme: widen the ball until it holds N + 1 gas particles, then h
+                    // from the N-th and (N+1)-th distances (every particle closer than the
+                    // (N+1)-th is in the list: the list holds the whole ball)
+                    if (cnt < kp.nstd + 1) {
+                        if (Rc > 8.f * sd) {                  // fewer gas particles than N + 1
+                            give_up(EVOL_ENOCONV);
+                            break;
+                        }
+                        L = Rc;
+                        stale = true;
+                        continue;
+                    }
+                    const float rN = kth_distance(nb, cnt, kp.nstd, lane);
+                    const float rN1 = kth_distance(nb, cnt, kp.nstd + 1, lane);
+                    L = 0.25f * (rN + rN1);
+                    status = ST_LAST;
+                }
                 // Sums over the list (lane l takes entries l, l + 32, ...), combined across the warp.
                 // A Newton iteration needs Sw and Suw; the last evaluation also needs the
                 // mass-weighted sums of the outputs.
@@ -621,8 +658,8 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                             d.len_h[si] = L;
                             d.nh[si] = nsum;
                             d.rho[si] = Smw * inv_pi * Linv * Linv * Linv;
-                            d.omega[si] = -Suw / (3.f * Sw);
-                            d.zeta[si] = (3.f * Smw + Smuw) / (3.f * Sw);
+                            d.omega[si] = kp.standard ? 1.f : -Suw / (3.f * Sw);
+                            d.zeta[si] = kp.standard ? 0.f : (3.f * Smw + Smuw) / (3.f * Sw);
                         } else {
                             d.len_eps[si] = L;
                             d.neps[si] = nsum;
@@ -631,10 +668,15 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         }
                         // div v = -1/(n C) sum_j (v_i - v_j).grad_i W = 3 S5 / (L Suw), C = Upsilon
                         // or Omega* = -Suw/(3 Sw), n = Sw/(pi L^3), grad W = r_ij/r w'(u)/(pi L^4)
-                        if (kp.want_divv) (MODE == 0 ? d.divv_h : d.divv_e)[si] = 3.f * S5 / (L * Suw);
+                        // (the standard scheme takes C = 1: div v = -S5 / (L Sw))
+                        const bool stdc = MODE == 0 && kp.standard;
+                        if (kp.want_divv)
+                            (MODE == 0 ? d.divv_h : d.divv_e)[si] = stdc ? -S5 / (L * Sw) : 3.f * S5 / (L * Suw);
                         // |curl v| = |1/(n C) sum_j (v_i - v_j) x grad_i W| = 3 |S6| / (L |Suw|)
-                        if (MODE == 0 && kp.want_curl)
-                            d.curlv_h[si] = 3.f * sqrtf(S6x * S6x + S6y * S6y + S6z * S6z) / (L * fabsf(Suw));
+                        if (MODE == 0 && kp.want_curl) {
+                            const float s6 = sqrtf(S6x * S6x + S6y * S6y + S6z * S6z);
+                            d.curlv_h[si] = stdc ? s6 / (L * Sw) : 3.f * s6 / (L * fabsf(Suw));
+                        }
                     }
                     status = ST_DONE;
                 } else {
@@ -694,6 +736,8 @@ int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params 
     kp.periodic_mask = prm->periodic_mask;
     for (int a = 0; a < 3; ++a) kp.plen[a] = prm->periodic_hi[a] - prm->periodic_lo[a];
     kp.want_curl = mode == 0 && evol_needs_curl(prm);
+    kp.standard = mode == 0 && prm->sph_scheme == EVOL_SPH_STANDARD;
+    kp.nstd = (int)lrintf(prm->n_nei_sph);
     kp.want_divv = c->want_divv || kp.want_curl;
     kp.stack_cap = (int)c->wstack_lim;
     kp.stack_stride = (int)c->wstack_cap;
@@ -708,3 +752,4 @@ int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params 
 }
 
 int evol_lengths_warps_per_block() { return LW_WARPS; }
+int evol_lengths_list_cap() { return PCAP; }

@@ -22,6 +22,7 @@ EVOL_DBG_DISS = 9
 EVOL_VISC_MONAGHAN, EVOL_VISC_SIGNAL = 0, 1
 EVOL_COND_VSIG_SOUND, EVOL_COND_VSIG_PRESSURE = 0, 1
 EVOL_COND_SRC_SQRTU, EVOL_COND_SRC_LINEAR = 0, 1
+EVOL_SPH_LAGRANGIAN, EVOL_SPH_STANDARD = 0, 1
 
 _fp = C.POINTER(C.c_float)
 
@@ -44,7 +45,7 @@ class EvolParams(C.Structure):
                 ("visc_form", C.c_int), ("balsara", C.c_int), ("balsara_eta", C.c_float),
                 ("variable_alpha", C.c_int), ("alpha_min", C.c_float), ("alpha_tau", C.c_float),
                 ("alpha_source", C.c_float), ("conduction", C.c_int), ("cond_vsig", C.c_int),
-                ("cond_source", C.c_int), ("alpha_u_min", C.c_float)]
+                ("cond_source", C.c_int), ("alpha_u_min", C.c_float), ("sph_scheme", C.c_int)]
 
 
 class EvolIntegrator(C.Structure):
@@ -140,7 +141,7 @@ def make_params(p) -> EvolParams:
     e.group_size = int(getattr(p, "group_size", 32))
     # dissipation variants (defaults: the paper's constants, every variant off)
     for k, d in (("visc_form", 0), ("balsara", 0), ("variable_alpha", 0), ("conduction", 0), ("cond_vsig", 0),
-                 ("cond_source", 0)):
+                 ("cond_source", 0), ("sph_scheme", 0)):
         setattr(e, k, int(getattr(p, k, d)))
     for k, d in (("balsara_eta", 1e-4), ("alpha_min", 0.01), ("alpha_tau", 0.1), ("alpha_source", 0.75),
                  ("alpha_u_min", 0.0)):
