@@ -5,5 +5,5 @@ import this package.  The CUDA library never calls it and has no fallback to it.
 """
 from .oracle import (  # noqa: F401
     build_oracle, lib, kernels, OracleTree, force_step, kdk, eta_from_nnei, hash_id,
-    TimeStep, timestep_criteria, global_timestep, run,
+    TimeStep, timestep_criteria, global_timestep, run, Bins, run_bins, step_ticks, active_force_step,
 )

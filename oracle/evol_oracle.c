@@ -1028,6 +1028,43 @@ void orc_forces(orc_tree *t, double theta, double G, double gamma, double alpha,
     }
 }
 
+/* Wake-up input of the individual time steps (Sect. 4.2.1): for every gas particle j, the smallest
+ * key[i] over the listed gas particles i (the active ones) that are its SPH neighbours, i.e. with
+ * r_ij < 2 max(h_i, h_j), i != j.  out (length n) must hold +inf on entry; entries without such a
+ * neighbour keep it.  h: original order (gas entries used).  Returns 0, or -3 on overflow. */
+int orc_sph_nbmin(const orc_tree *t, const double *h, const int64_t *idx, int64_t nidx, const double *key,
+                  int periodic_mask, const double *plo, const double *phi_, double *out)
+{
+    orc_period per = {periodic_mask, {0, 0, 0}, {1, 1, 1}};
+    for (int a = 0; a < 3; ++a)
+        if ((periodic_mask >> a) & 1) { per.lo[a] = plo[a]; per.len[a] = phi_[a] - plo[a]; }
+    double hmax = 0;
+    for (int64_t j = 0; j < t->n_gas; ++j)
+        if (h[j] > hmax) hmax = h[j];
+    int64_t cap = 1 << 16;
+    int64_t *scr = malloc(cap * sizeof(int64_t));
+    double *rs = malloc(cap * sizeof(double));
+    int err = (scr && rs) ? 0 : -3;
+    for (int64_t q = 0; q < nidx && !err; ++q) {
+        int64_t i = idx[q];
+        if (i >= t->n_gas) continue;
+        double p[3] = {t->x[i], t->y[i], t->z[i]};
+        int64_t cnt = orc_gather(t, &per, p, 2.0 * (h[i] > hmax ? h[i] : hmax), 1, scr, rs, cap);
+        if (cnt < 0) {
+            err = -3;
+            break;
+        }
+        for (int64_t k = 0; k < cnt; ++k) {
+            int64_t j = scr[k];
+            double R = 2.0 * (h[i] > h[j] ? h[i] : h[j]);
+            if (j != i && rs[k] < R && key[i] < out[j]) out[j] = key[i];
+        }
+    }
+    free(scr);
+    free(rs);
+    return err;
+}
+
 /* Ideal-gas equation of state (App. B; Sect. 3.3.1): P = (gamma-1) rho u, c = sqrt(gamma(gamma-1)u). */
 void orc_eos(int64_t n, double gamma, const double *rho, const double *u, double *P, double *c)
 {

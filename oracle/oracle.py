@@ -73,6 +73,8 @@ def lib():
         L.orc_divv.argtypes = [C.c_void_p, C.c_int, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, C.c_void_p,
                                C.c_int64, C.c_int, _f64p, _f64p, _f64p, C.c_void_p]
         L.orc_eos.argtypes = [C.c_int64, d, _f64p, _f64p, _f64p, _f64p]
+        L.orc_sph_nbmin.restype = C.c_int
+        L.orc_sph_nbmin.argtypes = [C.c_void_p, _f64p, C.c_void_p, C.c_int64, _f64p, C.c_int, _f64p, _f64p, _f64p]
         L.orc_num_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -237,6 +239,18 @@ class OracleTree:
         res["lapu"] = lapu
         res["lapabs"] = lapabs
         return res
+
+    def sph_nbmin(self, h, idx, key, params=None):
+        """For every gas particle j the smallest key[i] over the gas particles i in idx that are its SPH
+        neighbours (r_ij < 2 max(h_i, h_j), i != j); +inf where there is none."""
+        out = np.full(self.n, np.inf)
+        pm, lo, hi = self._period(params)
+        ix = _c(idx, np.int64)
+        rc = lib().orc_sph_nbmin(self.ptr, _c(h, np.float64), ix.ctypes.data, int(len(ix)), _c(key, np.float64),
+                                 pm, lo, hi, out)
+        if rc != 0:
+            raise RuntimeError(f"oracle neighbour minimum failed (code {rc})")
+        return out
 
     def divv(self, mode: int, L, nsum, corr, vx, vy, vz, idx=None, params=None, curl=False):
         """Velocity divergence from the discretised continuity equation (Sect. 2.1): mode 1 with the
@@ -571,3 +585,232 @@ def run(w, nsteps: int, ts: TimeStep, params=None, predicted=True):
         sw.kick(0.5 * dt, r)
     return {"x": X[:, 0], "y": X[:, 1], "z": X[:, 2], "vx": V[:, 0], "vy": V[:, 1], "vz": V[:, 2], "u": U,
             **sw.result(), "dts": dts, "last": r}
+
+
+# ---- individual power-of-two time steps (Sect. 4.2.1) -----------------------------------------
+
+_PERSIST = ("eps", "ups", "X", "h", "n_h", "rho", "omega", "zeta", "divv_h", "curlv_h")
+
+
+def active_force_step(w, active, pers, params=None):
+    """Force step in which only the particles in `active` (original indices) are evaluated.
+
+    Their eps (all species, adaptive softening) and h (gas) are solved again from the starting
+    guesses w.eps / w.h, and div v, curl v formed for the active gas; every other particle keeps
+    what `pers` holds from its last evaluation (eps, Upsilon, X, h, n, rho, Omega*, zeta, div v,
+    curl v).  The equation of state takes every gas particle's current u.  `pers` is updated in
+    place for the active particles.  Returns a force_step-like dict for all particles, whose
+    force results are valid at the active ones."""
+    p = params or w.params
+    t = OracleTree(w.x, w.y, w.z, w.m, w.n_gas, p.leaf_size)
+    n, ng = w.n, w.n_gas
+    act = np.asarray(active, np.int64)
+    actg = act[act < ng]
+    if p.gravity:
+        if p.adaptive_softening:
+            if len(act):
+                eps, _, ups, X, _ = t.solve_lengths(1, p.n_nei_grav, guess=w.eps, idx=act, params=p)
+                for k, v in (("eps", eps), ("ups", ups), ("X", X)):
+                    pers[k][act] = v[act]
+        else:
+            pers["eps"][:] = w.eps
+            pers["ups"][:] = 1.0
+            pers["X"][:] = 0.0
+    st = {"vx": w.vx.astype(np.float64), "vy": w.vy.astype(np.float64), "vz": w.vz.astype(np.float64)}
+    if p.gravity:
+        st.update(eps=pers["eps"].copy(), ups=pers["ups"].copy(), X=pers["X"].copy())
+    if p.sph and ng:
+        hmode = 2 if int(getattr(p, "sph_scheme", 0)) == 1 else 0
+        if len(actg):
+            h, nh, rho, om, zeta = t.solve_lengths(hmode, p.n_nei_sph, guess=w.h, idx=actg, params=p)
+            for k, v in (("h", h), ("n_h", nh), ("rho", rho), ("omega", om), ("zeta", zeta)):
+                pers[k][actg] = v[actg]
+            dv, cv = t.divv(0, pers["h"], pers["n_h"], pers["omega"], st["vx"], st["vy"], st["vz"], idx=actg,
+                            params=p, curl=True)
+            pers["divv_h"][actg] = dv[actg]
+            pers["curlv_h"][actg] = cv[actg]
+        P, c = np.zeros(n), np.zeros(n)
+        lib().orc_eos(n, float(p.gamma), _c(pers["rho"], np.float64), _c(w.u.astype(np.float64), np.float64), P, c)
+        P[ng:] = 0
+        c[ng:] = 0
+        st.update(h=pers["h"].copy(), rho=pers["rho"].copy(), omega=pers["omega"].copy(),
+                  zeta=pers["zeta"].copy(), P=P, c=c)
+    res = {k: pers[k].copy() for k in _PERSIST}
+    if p.sph and ng:
+        res.update(P=st["P"], c=st["c"])
+    diss = p.sph and ng > 0 and _dissipation_on(p)
+    if diss:
+        st.update(_dissipation_state(w, p, res, st))
+        res["balsara_f"] = st["f"]
+    res.update(t.forces(p, st, idx=act))
+    if diss:
+        res.update(_dissipation_rates(w, p, res, st))
+    res["tree"] = t
+    res["state"] = st
+    return res
+
+
+@dataclass
+class Bins:
+    """Individual time steps (Sect. 4.2.1): steps dt_max / 2^k, 0 <= k <= max_bin, on an integer
+    timeline of 2^max_bin ticks per largest step; wake_factor > 1 wakes an inactive gas particle
+    whose step exceeds wake_factor times the step of an active SPH neighbour (0: off)."""
+    max_bin: int = 6
+    wake_factor: float = 0.0
+
+
+def step_ticks(dt, T: int, tick: float):
+    """The largest power-of-two step, in ticks, not longer than dt: L = 2^m with L tick <= dt,
+    clamped to [1, T] (a criterion shorter than one tick gets the finest step).
+
+    Reading: the printed rule takes the smallest n with dt_max / 2^n >= dt_i, which n = 0 always
+    meets; the step is meant not to exceed the criterion, so the largest such step is taken."""
+    dt = np.asarray(dt, np.float64)
+    L = np.ones(dt.shape, np.int64)
+    for _ in range(63):
+        grow = (2 * L <= T) & (2 * L * tick <= dt)
+        if not grow.any():
+            break
+        L = np.where(grow, 2 * L, L)
+    return L
+
+
+def _lowbit(t):
+    t = np.asarray(t, np.int64)
+    return t & -t
+
+
+def run_bins(w, nlargest: int, ts: TimeStep, bins: Bins, params=None, predicted=True, stop_after=None):
+    """Individual power-of-two time steps (Sect. 4.2.1) with KDK kicks, in FP64.
+
+    Integer timeline: T = 2^max_bin ticks per largest step ts.dt_max.  Each particle has a step
+    [tb, te] whose length is a power of two that divides tb.  A system step:
+      1. t_next = min te; every particle drifts x += v (t_next - t_sys) (v: its half-kicked velocity);
+      2. the particles with te = t_next are active: a force step evaluates them only (active_force_step),
+         the SPH terms using every particle's velocity and u predicted to t_next,
+         v_p = v + a (t_next - (tb + te)/2), u likewise (Sect. 4.1; off with predicted=False);
+      3. active particles: second half kick v += a (te - tb)/2, u and the dissipation switches alike;
+      4. wake-up: an inactive gas particle j whose step exceeds wake_factor times the step just
+         completed by an active SPH neighbour ends its step early, at the first multiple of
+         L' > t_next, L' the largest power of two <= wake_factor times that neighbour step; the
+         first half kick it received is cut to the shortened step (energy and momentum are then
+         not exactly conserved, as the paper says);
+      5. active particles, unless t_next ends the run: the criteria of the global step (Sect. 4.2)
+         give L = step_ticks(dt_i); a longer step than before only where t_next is a multiple of it:
+         L = min(L, largest power of two dividing t_next); tb = t_next, te = t_next + L; first half
+         kick v += a L/2.
+    Everything starts synchronised at t = 0 with a force step of all particles and ends so at
+    nlargest * T (stop_after: end after that many system steps instead, mid-run).  Returns the
+    final state, the per-particle steps and counts."""
+    import copy
+
+    p = params or w.params
+    n, ng = w.n, w.n_gas
+    K = int(bins.max_bin)
+    T = 1 << K
+    tick = ts.dt_max / T
+    t_end = int(nlargest) * T
+    X = np.stack([w.x, w.y, w.z], 1).astype(np.float64)
+    V = np.stack([w.vx, w.vy, w.vz], 1).astype(np.float64)
+    U = w.u.astype(np.float64).copy()
+    cur = copy.copy(w)
+    sw = _Switches(w, p, cur)
+    pers = {k: np.zeros(n) for k in _PERSIST}
+    pers["h"][:ng] = w.h[:ng]
+    pers["eps"][:] = w.eps
+    lo = np.asarray(getattr(p, "periodic_lo", (0, 0, 0)), np.float64)
+    hi = np.asarray(getattr(p, "periodic_hi", (1, 1, 1)), np.float64)
+    gas = np.arange(n) < ng
+
+    def evaluate(active, vel, uu):
+        cur.x, cur.y, cur.z = (np.ascontiguousarray(X[:, a], np.float32) for a in range(3))
+        cur.vx, cur.vy, cur.vz = (np.ascontiguousarray(vel[:, a], np.float32) for a in range(3))
+        cur.u = np.ascontiguousarray(uu, np.float32)
+        cur.h = np.ascontiguousarray(np.where(gas, pers["h"], w.h), np.float32)
+        cur.eps = np.ascontiguousarray(pers["eps"], np.float32)
+        sw.hand_over()
+        return active_force_step(cur, active, pers, p)
+
+    def kick(idx, f_ticks, r_acc, r_du, r_sw):
+        hdt = (f_ticks * tick)
+        V[idx] += hdt[:, None] * r_acc[idx]
+        U[idx] += np.where(gas[idx], hdt * r_du[idx], 0.0)
+        for k, arr in (("al", "dalpha"), ("alu", "dalpha_u")):
+            a = getattr(sw, k)
+            if a is not None:
+                g = idx[idx < ng]
+                a[g] += (f_ticks[idx < ng] * tick) * r_sw[arr][g]
+
+    allp = np.arange(n, dtype=np.int64)
+    A = np.zeros((n, 3))
+    DU = np.zeros(n)
+    rates = {"dalpha": np.zeros(n), "dalpha_u": np.zeros(n)}
+    r = evaluate(allp, V, U)
+
+    def take(r, idx):
+        A[idx] = np.stack([r["ax"], r["ay"], r["az"]], 1)[idx]
+        DU[idx] = r["dudt"][idx]
+        for k in rates:
+            if k in r:
+                rates[k][idx] = r[k][idx]
+
+    def new_steps(r, idx, tnow):
+        crit = timestep_criteria(cur, r, V[:, 0], V[:, 1], V[:, 2], U, ts, params=p)
+        dt = np.min(np.stack([c for c in crit.values()]), 0)
+        dt = np.where(np.isfinite(dt), dt, ts.dt_max)
+        L = step_ticks(dt[idx], T, tick)
+        if tnow > 0:
+            L = np.minimum(L, int(_lowbit(tnow)))
+        tb[idx] = tnow
+        te[idx] = tnow + L
+        kick(idx, 0.5 * L.astype(np.float64), A, DU, rates)
+        return dt
+
+    take(r, allp)
+    tb = np.zeros(n, np.int64)
+    te = np.zeros(n, np.int64)
+    stats = {"system_steps": 0, "active_evaluations": n, "wakeups": 0}
+    if t_end > 0:
+        new_steps(r, allp, 0)
+    tsys = 0
+    while tsys < t_end:
+        tnext = int(te.min())
+        X += V * ((tnext - tsys) * tick)
+        for a in range(3):
+            if (getattr(p, "periodic_mask", 0) >> a) & 1:
+                X[:, a] = lo[a] + np.mod(X[:, a] - lo[a], hi[a] - lo[a])
+        act = np.flatnonzero(te == tnext).astype(np.int64)
+        if predicted:
+            tau = (tnext - 0.5 * (tb + te)) * tick
+            Vp = V + tau[:, None] * A
+            Up = U + np.where(gas, tau * DU, 0.0)
+        else:
+            Vp, Up = V, U
+        r = evaluate(act, Vp, Up)
+        take(r, act)
+        kick(act, 0.5 * (te[act] - tb[act]).astype(np.float64), A, DU, rates)
+        if bins.wake_factor > 0 and ng:
+            key = np.full(n, np.inf)
+            key[act] = (te[act] - tb[act]).astype(np.float64)
+            m = r["tree"].sph_nbmin(pers["h"], act, key, params=p)
+            inact = np.flatnonzero(gas & (te != tnext) & np.isfinite(m))
+            for j in inact:
+                Lj = int(te[j] - tb[j])
+                if Lj > bins.wake_factor * m[j]:
+                    Lw = int(step_ticks(np.array([bins.wake_factor * m[j] * tick]), T, tick)[0])
+                    if Lw < Lj:
+                        tn = (tnext // Lw + 1) * Lw
+                        if tn < te[j]:
+                            cut = 0.5 * (Lj - (tn - tb[j]))
+                            kick(np.array([j]), np.array([-cut]), A, DU, rates)
+                            te[j] = tn
+                            stats["wakeups"] += 1
+        if tnext < t_end:
+            new_steps(r, act, tnext)
+        tsys = tnext
+        stats["system_steps"] += 1
+        stats["active_evaluations"] += len(act)
+        if stop_after is not None and stats["system_steps"] >= stop_after:
+            break
+    return {"x": X[:, 0], "y": X[:, 1], "z": X[:, 2], "vx": V[:, 0], "vy": V[:, 1], "vz": V[:, 2], "u": U,
+            **sw.result(), "tb": tb, "te": te, "stats": stats, "last": r}
