@@ -228,6 +228,40 @@ typedef struct {
 int evol_run(evol_ctx *ctx, evol_particles *p, const evol_params *prm, const evol_integrator *ip,
              evol_outputs *out, int nsteps, double *time, float *last_dt);
 
+/* Individual power-of-two time steps (Sect. 4.2.1).  Steps are dt_max / 2^k, 0 <= k <= max_bin, on an
+ * integer timeline of T = 2^max_bin ticks per largest step.  Each particle's step [tb, te] has a
+ * power-of-two length that divides tb; the step is the largest power of two not longer than the
+ * particle's criterion (those of evol_integrator; the finest where a criterion is below one tick),
+ * and it can grow only where the current time is a multiple of the new length, so that everyone is
+ * synchronised at the end of every largest step. */
+typedef struct {
+    evol_integrator crit;           /* criteria (etas), predicted_velocity, and dt_max = the largest
+                                       step; dt_min and predict_lengths are not used */
+    int max_bin;                    /* 0 <= max_bin <= 30 */
+    float wake_factor;              /* 0: no wake-up; else > 1 (the paper suggests 4 to 8) */
+} evol_bins;
+
+/* KDK leapfrog with individual steps (Sect. 4.1, 4.2.1), entirely on the device, for nlargest
+ * largest steps from a synchronised start.  A force step of all particles starts the run; then
+ * each system step: t_next = the earliest step end; every particle drifts to t_next with its
+ * half-kicked velocity; the particles whose step ends there (active) are the only ones evaluated --
+ * tree of all particles at their drifted positions, eps and h solves, density and force walks over
+ * the active list -- while the others keep the lengths, densities and accelerations of their last
+ * evaluation (their velocity and u predicted to t_next for the SPH terms when predicted_velocity);
+ * active particles get their second half kick, a new step and its first half kick.  With
+ * wake_factor > 1, an inactive gas particle whose step exceeds wake_factor times the step just
+ * completed by an active SPH neighbour ends its step at the first multiple of the largest power of
+ * two <= wake_factor x that step, and the part of its first half kick beyond it is taken back.
+ * One system step is a CUDA graph recorded once and replayed; the host reads the system time
+ * after each (one stream synchronisation per system step).  x, y, z, vx, vy, vz, u, h, eps (and
+ * alpha, alpha_u with their switches) are updated IN PLACE.  *time (may be NULL) advances by
+ * nlargest * dt_max; stats (may be NULL): [0] system steps, [1] particle evaluations including the
+ * start, [2] wake-ups, [3] new steps whose criterion was below one tick.  out receives the last
+ * force step's outputs (every particle is active in it).  Single system only (no evol_step_batched
+ * offsets).  EVOL_EINVAL for bad parameters. */
+int evol_run_bins(evol_ctx *ctx, evol_particles *p, const evol_params *prm, const evol_bins *bp, evol_outputs *out,
+                  int nlargest, double *time, int64_t stats[4]);
+
 /* evol_step on HOST buffers: copies the inputs host -> device into context-owned buffers,
  * runs the step and copies every non-NULL output (and h, eps) back, then synchronises.
  * The particle and output pointers of this call are host pointers (pinned memory is
@@ -289,6 +323,7 @@ int evol_get_counters(evol_ctx *ctx, uint64_t out[32]);
  *   EVOL_DBG_DISS   float[5*n]  caller order, gas: div v and |curl v| with the smoothing kernel,
  *                               Balsara f_i, v^sig_i, Brookshaw lap u_i (as printed, with
  *                               |gradbar W|; conduction only)
+ *   EVOL_DBG_BINS   int64[2*n]  caller order: step start tb and end te (ticks) after evol_run_bins
  * Hashes and per-particle counts are written only while check mode is on; the divergences only
  * by evol_run's force steps or when a dissipation variant needs them (Balsara, variable alpha);
  * EVOL_DBG_DISS only by steps with a dissipation variant on. */
@@ -301,6 +336,7 @@ int evol_get_counters(evol_ctx *ctx, uint64_t out[32]);
 #define EVOL_DBG_COUNTS   7
 #define EVOL_DBG_FLOW     8
 #define EVOL_DBG_DISS     9
+#define EVOL_DBG_BINS    10
 int64_t evol_get_debug(evol_ctx *ctx, int what, void *host_dst, int64_t cap_bytes);
 
 /* Check mode (0/1): the walks also record, per particle, order-independent 64-bit hashes

@@ -759,6 +759,12 @@ def run_bins(w, nlargest: int, ts: TimeStep, bins: Bins, params=None, predicted=
         dt = np.min(np.stack([c for c in crit.values()]), 0)
         dt = np.where(np.isfinite(dt), dt, ts.dt_max)
         L = step_ticks(dt[idx], T, tick)
+        # how close each decision came to a boundary of its power-of-two interval (relative): an
+        # FP32 evaluation of the criteria can only decide otherwise below about 1e-6
+        q = dt[idx] / (L * tick)
+        free = (L < T) & (q >= 1.0)
+        if free.any():
+            stats["step_margin"] = min(stats["step_margin"], float(np.min(np.minimum(q[free] - 1.0, 2.0 - q[free]) / 2.0)))
         if tnow > 0:
             L = np.minimum(L, int(_lowbit(tnow)))
         tb[idx] = tnow
@@ -769,7 +775,7 @@ def run_bins(w, nlargest: int, ts: TimeStep, bins: Bins, params=None, predicted=
     take(r, allp)
     tb = np.zeros(n, np.int64)
     te = np.zeros(n, np.int64)
-    stats = {"system_steps": 0, "active_evaluations": n, "wakeups": 0}
+    stats = {"system_steps": 0, "active_evaluations": n, "wakeups": 0, "step_margin": np.inf}
     if t_end > 0:
         new_steps(r, allp, 0)
     tsys = 0

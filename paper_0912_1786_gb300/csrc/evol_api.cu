@@ -38,7 +38,8 @@ void free_all(evol_ctx *c)
 {
     evol_dev &d = c->d;
     void *ptrs[] = {d.pos, d.vel, d.grav, d.hydro, d.snd, d.vah, d.orig, d.inv, d.divv_h, d.divv_e, d.mumax, d.dt, d.time, d.len_h, d.len_eps, d.nh, d.omega,
-                    d.diss, d.curlv_h, d.vsig, d.lapu, d.dalpha, d.dalpha_u,
+                    d.diss, d.curlv_h, d.vsig, d.lapu, d.dalpha, d.dalpha_u, d.tb, d.te, d.bact, d.pred_tau,
+                    d.pers, d.actf, d.acts, d.act, d.nbmin, d.bt,
                     d.zeta, d.rho, d.neps, d.ups, d.X, d.acc, d.dudt, d.keys_a, d.keys_b, d.vals_a, d.vals_b,
                     d.hist, d.lcp, d.cnt, d.base, d.scan_part, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
                     d.nnch, d.narrive, d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nM64, d.nC64, d.nQ64, d.nBmin,
@@ -53,6 +54,8 @@ void free_all(evol_ctx *c)
         if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
     if (c->kdk_exec) cudaGraphExecDestroy(c->kdk_exec);
     if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
+    if (c->bins_exec) cudaGraphExecDestroy(c->bins_exec);
+    if (c->h_bt) cudaFreeHost(c->h_bt);
 }
 
 int check_args(evol_ctx *c, const evol_particles *p, const evol_params *prm)
@@ -160,7 +163,8 @@ int record_phase(evol_ctx *c, int k, evol_particles *p, const evol_params *prm, 
     case 4: {
         int what = EVOL_UNPERM_ACC | (grav ? EVOL_UNPERM_EPSOUT : 0) |
                    (sph ? (EVOL_UNPERM_LENGTHS | EVOL_UNPERM_DENSITY | EVOL_UNPERM_DUDT) : 0) |
-                   (sph ? evol_unperm_switches(prm) : 0);
+                   (sph ? evol_unperm_switches(prm) : 0) | (c->persist ? EVOL_UNPERM_PERSIST : 0) |
+                   (c->bins_active ? EVOL_UNPERM_ACTIVE : 0);
         rc = evol_launch_unpermute(c, p, out, what);
         if (!rc) rc = evol_launch_diagnostics(c, p, prm);
         break;
@@ -225,6 +229,10 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.divv_h, n); rc |= dalloc(&d.divv_e, n); rc |= dalloc(&d.mumax, n);
     rc |= dalloc(&d.diss, n); rc |= dalloc(&d.curlv_h, n); rc |= dalloc(&d.vsig, n); rc |= dalloc(&d.lapu, n);
     rc |= dalloc(&d.dalpha, n); rc |= dalloc(&d.dalpha_u, n);
+    rc |= dalloc(&d.tb, n); rc |= dalloc(&d.te, n); rc |= dalloc(&d.bact, n); rc |= dalloc(&d.pred_tau, n);
+    rc |= dalloc(&d.pers, 7 * n); rc |= dalloc(&d.actf, n); rc |= dalloc(&d.acts, n + 1); rc |= dalloc(&d.act, n);
+    rc |= dalloc(&d.nbmin, n); rc |= dalloc(&d.bt, 8);
+    if (!rc && cudaMallocHost((void **)&c->h_bt, 8 * sizeof(unsigned long long)) != cudaSuccess) rc = EVOL_ENOMEM;
     rc |= dalloc(&d.dt, 4); rc |= dalloc(&d.time, 1);
     rc |= dalloc(&d.keys_a, n); rc |= dalloc(&d.keys_b, n); rc |= dalloc(&d.vals_a, n); rc |= dalloc(&d.vals_b, n);
     rc |= dalloc(&d.hist, 256 * c->sort_blocks + 1);
@@ -366,6 +374,7 @@ static int run_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol
     sig = fnv(sig, &c->wstack_lim, sizeof c->wstack_lim);
     sig = fnv(sig, &c->want_divv, sizeof c->want_divv);
     sig = fnv(sig, &c->pred_dt, sizeof c->pred_dt);
+    sig = fnv(sig, &c->persist, sizeof c->persist);
     sig = fnv(sig, &c->stream, sizeof c->stream);
     if (!c->graph_exec[0] || sig != c->graph_sig) {
         for (int k = 0; k < NPHASE; ++k)
@@ -642,6 +651,163 @@ int evol_run(evol_ctx *c, evol_particles *p, const evol_params *prm, const evol_
     return EVOL_OK;
 }
 
+int evol_run_bins(evol_ctx *c, evol_particles *p, const evol_params *prm, const evol_bins *bp, evol_outputs *out,
+                  int nlargest, double *time, int64_t stats[4])
+{
+    int rc = check_args(c, p, prm);
+    if (rc || (p && p->n == 0)) return rc;
+    if (!bp || nlargest < 0 || bp->max_bin < 0 || bp->max_bin > 30) return EVOL_EINVAL;
+    const evol_integrator *ip = &bp->crit;
+    const float et[5] = {ip->eta_acc, ip->eta_vel, ip->eta_av, ip->eta_courant, ip->eta_u};
+    for (float e : et)
+        if (!(e >= 0.f)) return EVOL_EINVAL;
+    if (!(ip->dt_max > 0.f) || ip->dt_max > 3.0e38f) return EVOL_EINVAL;
+    if (!(bp->wake_factor == 0.f || bp->wake_factor > 1.f) || !(bp->wake_factor < 3.0e38f)) return EVOL_EINVAL;
+    if (!p->vx || !p->vy || !p->vz) return EVOL_EINVAL;
+    const int64_t cap = c->cap, n = p->n, ng = p->n_gas;
+    const unsigned long long t_end = (unsigned long long)nlargest << bp->max_bin;
+    // every evaluation's accelerations, du/dt and switch rates go to kdk_acc (caller order)
+    evol_outputs o = out ? *out : evol_outputs{};
+    o.ax = c->kdk_acc;
+    o.ay = c->kdk_acc + cap;
+    o.az = c->kdk_acc + 2 * cap;
+    o.dudt = c->kdk_acc + 3 * cap;
+    o.dalpha = c->kdk_acc + 4 * cap;
+    o.dalpha_u = c->kdk_acc + 5 * cap;
+    auto reset = [&]() {
+        c->want_divv = 0;
+        c->persist = 0;
+        c->bins_active = 0;
+        c->bins_wake = 0;
+        c->pred_tau = nullptr;
+        c->pred_dt = nullptr;
+    };
+    // the start: every particle evaluated, its state kept for the steps in which it is inactive
+    reset();
+    c->want_divv = 1;
+    c->persist = 1;
+    c->bins_t_end = t_end;
+    if ((rc = evol_step(c, p, prm, &o))) {
+        reset();
+        return rc;
+    }
+    const bool wake = bp->wake_factor > 0.f && prm->sph && ng > 0;
+    if (t_end > 0) {
+        if ((rc = evol_launch_bins(c, p, prm, bp, 0))) {
+            reset();
+            return set_err(c, rc);
+        }
+        uint64_t sig = 0x9e3779b97f4a7c15ull;
+        sig = fnv(sig, p, sizeof *p);
+        sig = fnv(sig, prm, sizeof *prm);
+        sig = fnv(sig, bp, sizeof *bp);
+        sig = fnv(sig, &o, sizeof o);
+        sig = fnv(sig, &t_end, sizeof t_end);
+        sig = fnv(sig, &c->check_mode, sizeof c->check_mode);
+        sig = fnv(sig, &c->wstack_lim, sizeof c->wstack_lim);
+        sig = fnv(sig, &c->stream, sizeof c->stream);
+        if (!c->bins_exec || sig != c->bins_sig) {
+            if (c->bins_exec) {
+                cudaGraphExecDestroy(c->bins_exec);
+                c->bins_exec = nullptr;
+            }
+            cudaStream_t cap_stream = c->stream;
+            bool own = false;
+            if (!cap_stream) {
+                if (cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                    reset();
+                    return set_err(c, EVOL_ECUDA);
+                }
+                own = true;
+            }
+            cudaStream_t saved = c->stream;
+            c->stream = cap_stream;
+            cudaGraph_t graph = nullptr;
+            int prc = EVOL_OK;
+            if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                prc = EVOL_ECUDA;
+            } else {
+                const bool grav = prm->gravity != 0, sph = prm->sph != 0 && ng > 0;
+                // t_next, drift, active flags, prediction times
+                prc = evol_launch_bins(c, p, prm, bp, 1);
+                // tree of every particle (velocities and u predicted per particle)
+                c->pred_tau = ip->predicted_velocity ? c->d.pred_tau : nullptr;
+                if (!prc) prc = record_phase(c, 0, p, prm, &o);
+                if (!prc) prc = evol_launch_active_list(c, (int)n);
+                // solves and walk over the active list; the inactive keep their last evaluation
+                c->bins_active = 1;
+                c->bins_wake = wake;
+                if (!prc && grav && prm->adaptive_softening) prc = evol_launch_lengths(c, p, prm, 1);
+                if (!prc && sph) prc = evol_launch_lengths(c, p, prm, 0);
+                if (!prc) prc = evol_launch_bins(c, p, prm, bp, 2);
+                if (!prc) prc = evol_launch_pack(c, p, prm, grav, sph);
+                if (!prc) prc = evol_launch_node_lengths(c, prm, (int)ng);
+                if (!prc && wake && cudaMemsetAsync(c->d.nbmin, 0xff, n * sizeof(unsigned), cap_stream) != cudaSuccess)
+                    prc = EVOL_ECUDA;
+                if (!prc) prc = record_phase(c, 3, p, prm, &o);
+                if (!prc) prc = record_phase(c, 4, p, prm, &o);
+                // kicks, new steps, wake-up, t_sys = t_next
+                if (!prc) prc = evol_launch_bins(c, p, prm, bp, 3);
+                cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
+                if (!prc && (e != cudaSuccess || !graph)) prc = EVOL_ECUDA;
+                if (!prc && cudaGraphInstantiate(&c->bins_exec, graph, 0) != cudaSuccess) {
+                    c->bins_exec = nullptr;
+                    prc = EVOL_ECUDA;
+                }
+            }
+            if (graph) cudaGraphDestroy(graph);
+            c->stream = saved;
+            if (own) cudaStreamDestroy(cap_stream);
+            if (prc) {
+                cudaGetLastError();
+                reset();
+                return set_err(c, prc);
+            }
+            c->bins_sig = sig;
+        }
+        // system steps until the end; each advances the time by at least one tick
+        unsigned long long tsys = 0;
+        for (unsigned long long it = 0; it < t_end && tsys < t_end; ++it) {
+            if (cudaGraphLaunch(c->bins_exec, c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(c->h_bt, c->d.bt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess) {
+                reset();
+                return set_err(c, EVOL_ECUDA);
+            }
+            // a system step that did not advance the time would repeat forever: stop
+            if (c->h_bt[0] <= tsys) {
+                reset();
+                return set_err(c, EVOL_ESTATE);
+            }
+            tsys = c->h_bt[0];
+        }
+    }
+    reset();
+    // hand the last accelerations, du/dt and switch rates to the caller
+    float *dst[6] = {out ? out->ax : nullptr, out ? out->ay : nullptr, out ? out->az : nullptr,
+                     out ? out->dudt : nullptr, out && prm->variable_alpha ? out->dalpha : nullptr,
+                     out && prm->conduction ? out->dalpha_u : nullptr};
+    const float *src[6] = {o.ax, o.ay, o.az, o.dudt, o.dalpha, o.dalpha_u};
+    const int64_t len[6] = {n, n, n, ng, ng, ng};
+    for (int k = 0; k < 6; ++k)
+        if (dst[k] && len[k] > 0)
+            cudaMemcpyAsync(dst[k], src[k], len[k] * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    if (cudaMemcpyAsync(c->h_bt, c->d.bt, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return set_err(c, EVOL_ECUDA);
+    if (stats) {
+        const bool ran = t_end > 0;
+        stats[0] = ran ? (int64_t)c->h_bt[2] : 0;
+        stats[1] = (ran ? (int64_t)c->h_bt[3] : 0) + n;
+        stats[2] = ran ? (int64_t)c->h_bt[4] : 0;
+        stats[3] = ran ? (int64_t)c->h_bt[5] : 0;
+    }
+    if (time) *time += (double)nlargest * (double)ip->dt_max;
+    return EVOL_OK;
+}
+
 int evol_step_host(evol_ctx *c, evol_particles *ph, const evol_params *prm, evol_outputs *oh)
 {
     int rc = check_args(c, ph, prm);
@@ -882,6 +1048,13 @@ int64_t evol_get_debug(evol_ctx *c, int what, void *dst, int64_t cap)
             }
         }
         return 3 * n;
+    }
+    case EVOL_DBG_BINS: {
+        if (dst && cap >= 2 * n * 8) {
+            cudaMemcpy(dst, c->d.tb, n * 8, cudaMemcpyDeviceToHost);
+            cudaMemcpy((char *)dst + n * 8, c->d.te, n * 8, cudaMemcpyDeviceToHost);
+        }
+        return 2 * n;
     }
     case EVOL_DBG_DISS: {
         if (dst && cap >= 5 * n * 4) {

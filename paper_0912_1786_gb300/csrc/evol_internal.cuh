@@ -40,6 +40,14 @@ struct evol_dev {
     float *curlv_h;          // |curl v| with the smoothing kernel (sorted)
     float *vsig, *lapu;      // v^sig_i and Brookshaw lap u_i of the last walk (sorted)
     float *dalpha, *dalpha_u;    // d alpha/dt and d alpha^u/dt (sorted)
+    // individual time steps (caller order unless noted)
+    unsigned long long *tb, *te;    // step [tb, te] of each particle, in ticks
+    int32_t *bact;                  // 1: the particle is active in the current system step
+    float *pred_tau;                // t_now - (tb + te)/2 (time units): prediction of v and u
+    float *pers;                    // last evaluation: rho, Omega*, zeta, Upsilon, X, div v, |curl v| (7 x cap)
+    int32_t *actf, *acts, *act;     // sorted: active flags, their exclusive scan (+ total), the list
+    unsigned *nbmin;                // sorted: smallest active-neighbour step (wake-up)
+    unsigned long long *bt;         // [0] t_sys [1] t_next (ticks); [2..5] run counts
     float *dt;               // integrator scalars: [0] time step, [1] criterion minimum (as bits)
     double *time;            // integrator time
     float *dudt;             // sorted
@@ -100,6 +108,11 @@ struct evol_ctx {
     int check_mode;
     int want_divv;           // the length solves also form div v (integrator)
     const float *pred_dt;    // device time step of the predicted pack (integrator), or NULL
+    const float *pred_tau;   // per-particle prediction times (individual steps), or NULL
+    int persist;             // the un-permute also keeps the last-evaluation state (d.pers)
+    int bins_active;         // the walks being recorded take the active list
+    int bins_wake;           // and the force walk records the wake-up minimum
+    unsigned long long bins_t_end;   // end of the current individual-step run (ticks)
     // state of the last build / density
     int64_t built_n, built_ngas;
     int nsys;                // systems of the current particle set (1 unless batched)
@@ -120,6 +133,9 @@ struct evol_ctx {
     uint64_t kdk_sig;
     cudaGraphExec_t run_exec;        // one global-step KDK step (evol_run)
     uint64_t run_sig;
+    cudaGraphExec_t bins_exec;       // one system step of evol_run_bins
+    uint64_t bins_sig;
+    unsigned long long *h_bt;        // pinned host copy of the system time
 };
 
 // ---- host-side launch helpers (defined in evol_api.cu / tree.cu / walks) ------------------
@@ -131,6 +147,8 @@ int evol_launch_unpermute(evol_ctx *c, const evol_particles *p, const evol_outpu
 int evol_launch_diagnostics(evol_ctx *c, const evol_particles *p, const evol_params *prm);
 int evol_launch_integrator_step(evol_ctx *c, const evol_particles *p, const evol_params *prm, const evol_integrator *ip,
                                 int stage);
+int evol_launch_bins(evol_ctx *c, const evol_particles *p, const evol_params *prm, const evol_bins *bp, int stage);
+int evol_launch_active_list(evol_ctx *c, int n);
 
 #define EVOL_UNPERM_LENGTHS 1
 #define EVOL_UNPERM_DENSITY 2
@@ -139,6 +157,8 @@ int evol_launch_integrator_step(evol_ctx *c, const evol_particles *p, const evol
 #define EVOL_UNPERM_EPSOUT  16
 #define EVOL_UNPERM_DALPHA  32
 #define EVOL_UNPERM_DALPHA_U 64
+#define EVOL_UNPERM_ACTIVE  128   // only particles flagged in d.bact
+#define EVOL_UNPERM_PERSIST 256   // the persistent last-evaluation state d.pers (individual steps)
 
 // Any dissipation variant of Sect. 3.3.3 on (they act on SPH pairs only).
 static inline bool evol_diss_on(const evol_params *prm)
@@ -237,6 +257,10 @@ struct evol_kparams {
     int want_divv;           // length solves also form div v
     int want_curl;           // the h solve also forms |curl v| (Balsara limiter, alpha switch)
     int standard, nstd;      // h solve by the standard scheme with nstd neighbours inside 2h
+    // individual time steps: the walks take only the particles of the active list d.act (sorted
+    // positions, ascending; its length at d.acts[n]); the force walk also records, per SPH
+    // neighbour, the smallest step (ticks) of an active particle next to it (wake-up)
+    int active, wake;
     // dissipation variants (Sect. 3.3.3); diss = any of them on
     int diss, visc_form, balsara, var_alpha, conduction, cond_vsig, cond_source;
     float alpha_min, alpha_tau, alpha_source, alpha_u_min;

@@ -405,7 +405,9 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
     int *stk = reinterpret_cast<int *>(d.wstack + (size_t)wslot * kp.stack_stride);
     const int stack_cap = 2 * kp.stack_cap;
     const int n = kp.n;
-    const int ngroups = (n + SUB - 1) / SUB;       // the queue hands out SUB particles at a time
+    // individual time steps: items of SUB consecutive entries of the active list
+    const int nlist = kp.active ? d.acts[n] : n;
+    const int ngroups = (nlist + SUB - 1) / SUB;   // the queue hands out SUB particles at a time
     const float eta = MODE == 0 ? kp.eta_h : kp.eta_e;
     const float eta3 = eta * eta * eta;
     const float inv_pi = 1.f / EVOL_PI_F;
@@ -418,8 +420,9 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
         if (lane == 0) g = (int)atomicAdd(queue, 1ull);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ngroups) break;
-        const int s = g * SUB + lane;                 // lanes 0 .. SUB-1 hold the particles
-        const bool valid = lane < SUB && s < n;
+        const int e = g * SUB + lane;                 // lanes 0 .. SUB-1 hold the particles
+        const bool valid = lane < SUB && e < nlist;
+        const int s = kp.active ? (valid ? d.act[e] : 0) : e;
         const float4 pi4 = valid ? d.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
         const bool gas_i = valid && d.orig[s] < kp.n_gas;
         const bool act = MODE == 0 ? gas_i : valid;
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
             auto give_up = [&](int code) {
                 if (lane == 0) evol_flag(d.err, code);
                 if (lane == t) {
-                    const int si = g * SUB + t;
+                    const int si = s;                  // lane t holds particle t
                     const float qnan = __int_as_float(0x7fc00000);
                     if (MODE == 0) {
                         d.len_h[si] = L;
@@ -587,7 +590,8 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                 } else {
                     // the neighbours' masses (and, for the continuity equation, positions and
                     // velocities) are read from the sorted particle state
-                    const float4 vi = kp.want_divv ? d.vel[g * SUB + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int st = __shfl_sync(0xffffffffu, s, t);
+                    const float4 vi = kp.want_divv ? d.vel[st] : make_float4(0.f, 0.f, 0.f, 0.f);
                     for (int e = lane; e < cnt; e += 32) {
                         const float2 rj = nb[e];
                         const int j = __float_as_int(rj.y);
@@ -652,7 +656,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                 const float Smw = S3, Smuw = S4;
                 if (status == ST_LAST) {
                     if (lane == t) {
-                        const int si = g * SUB + t;
+                        const int si = s;                  // lane t holds particle t
                         const float nsum = Sw * inv_pi * Linv * Linv * Linv;
                         if (MODE == 0) {
                             d.len_h[si] = L;
@@ -735,6 +739,7 @@ int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params 
     kp.eta_e = 0.5f * cbrtf(3.f * prm->n_nei_grav / (4.f * EVOL_PI_F));
     kp.periodic_mask = prm->periodic_mask;
     for (int a = 0; a < 3; ++a) kp.plen[a] = prm->periodic_hi[a] - prm->periodic_lo[a];
+    kp.active = c->bins_active;
     kp.want_curl = mode == 0 && evol_needs_curl(prm);
     kp.standard = mode == 0 && prm->sph_scheme == EVOL_SPH_STANDARD;
     kp.nstd = (int)lrintf(prm->n_nei_sph);

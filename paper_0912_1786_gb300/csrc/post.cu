@@ -66,10 +66,12 @@ __global__ void k_pack(int n, int n_gas, int do_grav, int adaptive, int do_sph, 
 // that had no root reports ENOCONV).
 __global__ void k_unpermute(int n, int n_gas, int what, int add_acc, evol_dev d, float *h, float *eps, float *ax,
                             float *ay, float *az, float *pot, float *rho, float *P, float *c, float *omega,
-                            float *zeta, float *dudt, float *ups, float *X, float *dalpha, float *dalpha_u)
+                            float *zeta, float *dudt, float *ups, float *X, float *dalpha, float *dalpha_u,
+                            int64_t stride)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
+    if ((what & EVOL_UNPERM_ACTIVE) && !d.bact[j]) return;     // individual steps: evaluated ones only
     const int s = d.inv[j];
     const bool gas = j < n_gas;
     bool fin = true;
@@ -110,6 +112,19 @@ __global__ void k_unpermute(int n, int n_gas, int what, int add_acc, evol_dev d,
     if ((what & EVOL_UNPERM_DUDT) && gas) put(dudt, d.dudt[s]);
     if ((what & EVOL_UNPERM_DALPHA) && gas && dalpha) put(dalpha, d.dalpha[s]);
     if ((what & EVOL_UNPERM_DALPHA_U) && gas && dalpha_u) put(dalpha_u, d.dalpha_u[s]);
+    if (what & EVOL_UNPERM_PERSIST) {
+        // the last evaluation of the particle, kept for the system steps in which it is inactive
+        float *q = d.pers + j;
+        if (gas) {
+            q[0] = d.rho[s];
+            q[stride] = d.omega[s];
+            q[2 * stride] = d.zeta[s];
+            q[5 * stride] = d.divv_h[s];
+            q[6 * stride] = d.curlv_h[s];
+        }
+        q[3 * stride] = d.ups[s];
+        q[4 * stride] = d.X[s];
+    }
     if (!fin) evol_flag(d.err, EVOL_ENAN);
 }
 
@@ -226,34 +241,43 @@ struct TsParams {
     int var_alpha;           // the Courant term takes alpha_i (packed with the dissipation operands)
 };
 
+// The smallest of the criteria for caller index j (INFINITY where none applies).
+__device__ float particle_criterion(int j, int n_gas, const evol_dev &d, const TsParams &tp, const float *vx,
+                                    const float *vy, const float *vz, const float *u, const float *acc,
+                                    int64_t stride, const float *h, const float *eps)
+{
+    const float ax = acc[j], ay = acc[stride + j], az = acc[2 * stride + j];
+    const float a = sqrtf(ax * ax + ay * ay + az * az);
+    const float v = sqrtf(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]);
+    const bool gas = tp.sph && j < n_gas;
+    float L = tp.gravity ? eps[j] : INFINITY;
+    if (gas) L = fminf(L, h[j]);
+    float c[5] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY};
+    if (tp.eta_acc > 0.f) c[0] = tp.eta_acc * sqrtf(L / a);
+    if (tp.eta_vel > 0.f) c[1] = tp.eta_vel * L / v;
+    if (tp.eta_av > 0.f) c[2] = tp.eta_av * v / a;
+    if (gas) {
+        const int s = d.inv[j];
+        const float cs = d.snd[s].x, hj = h[j];
+        const float al = tp.var_alpha ? d.diss[s].x : tp.alpha;
+        if (tp.eta_c > 0.f)
+            c[3] = tp.eta_c * hj / (hj * fabsf(d.divv_h[s]) + cs + 1.2f * (al * cs + tp.beta * d.mumax[s]));
+        if (tp.eta_u > 0.f) c[4] = tp.eta_u * fabsf(u[j] / acc[3 * stride + j]);
+    }
+    float dt = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+        if (c[k] > 0.f && c[k] < INFINITY) dt = fminf(dt, c[k]);      // NaN and 0 are left out
+    return dt;
+}
+
 __global__ void k_dt_criteria(int n, int n_gas, evol_dev d, TsParams tp, const float *vx, const float *vy,
                               const float *vz, const float *u, const float *acc, int64_t stride, const float *h,
                               const float *eps, unsigned *dtbits)
 {
     float dt = INFINITY;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const float ax = acc[j], ay = acc[stride + j], az = acc[2 * stride + j];
-        const float a = sqrtf(ax * ax + ay * ay + az * az);
-        const float v = sqrtf(vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]);
-        const bool gas = tp.sph && j < n_gas;
-        float L = tp.gravity ? eps[j] : INFINITY;
-        if (gas) L = fminf(L, h[j]);
-        float c[5] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY};
-        if (tp.eta_acc > 0.f) c[0] = tp.eta_acc * sqrtf(L / a);
-        if (tp.eta_vel > 0.f) c[1] = tp.eta_vel * L / v;
-        if (tp.eta_av > 0.f) c[2] = tp.eta_av * v / a;
-        if (gas) {
-            const int s = d.inv[j];
-            const float cs = d.snd[s].x, hj = h[j];
-            const float al = tp.var_alpha ? d.diss[s].x : tp.alpha;
-            if (tp.eta_c > 0.f)
-                c[3] = tp.eta_c * hj / (hj * fabsf(d.divv_h[s]) + cs + 1.2f * (al * cs + tp.beta * d.mumax[s]));
-            if (tp.eta_u > 0.f) c[4] = tp.eta_u * fabsf(u[j] / acc[3 * stride + j]);
-        }
-#pragma unroll
-        for (int k = 0; k < 5; ++k)
-            if (c[k] > 0.f && c[k] < INFINITY) dt = fminf(dt, c[k]);      // NaN and 0 are left out
-    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        dt = fminf(dt, particle_criterion(j, n_gas, d, tp, vx, vy, vz, u, acc, stride, h, eps));
     for (int o = 16; o > 0; o >>= 1) dt = fminf(dt, __shfl_xor_sync(0xffffffffu, dt, o));
     if ((threadIdx.x & 31) == 0) atomicMin(dtbits, __float_as_uint(dt));
 }
@@ -321,6 +345,174 @@ __global__ void k_predict_lengths(int n, int n_gas, evol_dev d, const float *dtp
     if (do_h && j < n_gas) h[j] *= __expf(d.divv_h[s] * k);
 }
 
+// ---- individual power-of-two time steps (Sect. 4.2.1) -----------------------------------------
+// Integer timeline: T = 2^K ticks per largest step dt_max, tick = dt_max / T.  Particle j's step is
+// [tb_j, te_j]; d.bt holds t_sys, t_next and the run counts (system steps, active evaluations,
+// wake-ups, criteria below one tick).
+struct BinsParams {
+    unsigned long long T, t_end;
+    float tick, wake;
+    int n, n_gas, periodic_mask;
+    float lo[3], len[3];
+};
+
+// The largest power-of-two step (ticks) not longer than dt, in [1, T].
+__device__ __forceinline__ unsigned long long step_for(float dt, const BinsParams &bp)
+{
+    unsigned long long L = 1ull;
+    while (2ull * L <= bp.T && (float)(2ull * L) * bp.tick <= dt) L *= 2ull;
+    return L;
+}
+
+// t_next = the smallest step end (d.bt[1] must hold all bits set on entry)
+__global__ void k_bins_next(BinsParams bp, evol_dev d)
+{
+    unsigned long long m = ~0ull;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < bp.n; j += gridDim.x * blockDim.x)
+        m = min(m, d.te[j]);
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(&d.bt[1], m);
+}
+
+// Everyone drifts to t_next with its half-kicked velocity; the particles whose step ends there are
+// flagged active; each particle's prediction time t_next - (tb + te)/2 for v and u.
+__global__ void k_bins_drift(BinsParams bp, evol_dev d, float *x, float *y, float *z, const float *vx, const float *vy,
+                             const float *vz)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= bp.n) return;
+    const unsigned long long tn = d.bt[1], ts = d.bt[0];
+    const float dt = (float)(tn - ts) * bp.tick;
+    float p[3] = {x[j] + dt * vx[j], y[j] + dt * vy[j], z[j] + dt * vz[j]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if ((bp.periodic_mask >> a) & 1) {
+            float t = p[a] - bp.lo[a];
+            t -= bp.len[a] * floorf(t / bp.len[a]);
+            if (t >= bp.len[a]) t -= bp.len[a];
+            if (t < 0.f) t = 0.f;
+            p[a] = bp.lo[a] + t;
+        }
+    x[j] = p[0];
+    y[j] = p[1];
+    z[j] = p[2];
+    const unsigned long long tb = d.tb[j], te = d.te[j];
+    d.bact[j] = te == tn ? 1 : 0;
+    // t_next - (tb + te)/2 in ticks: exact in integers (times two), then to time units
+    d.pred_tau[j] = (float)((long long)(2ull * tn) - (long long)(tb + te)) * 0.5f * bp.tick;
+}
+
+// Inactive particles: the lengths and densities of their last evaluation, into sorted order.
+__global__ void k_bins_fill(BinsParams bp, evol_dev d, int64_t stride)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= bp.n) return;
+    const int j = d.orig[s];
+    if (d.bact[j]) return;
+    const float *q = d.pers + j;
+    if (j < bp.n_gas) {
+        d.rho[s] = q[0];
+        d.omega[s] = q[stride];
+        d.zeta[s] = q[2 * stride];
+        d.divv_h[s] = q[5 * stride];
+        d.curlv_h[s] = q[6 * stride];
+    }
+    d.ups[s] = q[3 * stride];
+    d.X[s] = q[4 * stride];
+}
+
+// A kick of the flagged particles (caller order): v += f a, u += f du/dt, switches alike, with
+// f = fac * (te - tb) * tick (second half kick: fac = 1/2).
+__global__ void k_bins_kick2(BinsParams bp, evol_dev d, float *vx, float *vy, float *vz, float *u, const float *acc,
+                             int64_t stride, SwitchKick sk)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= bp.n || !d.bact[j]) return;
+    const float f = 0.5f * (float)(d.te[j] - d.tb[j]) * bp.tick;
+    vx[j] += f * acc[j];
+    vy[j] += f * acc[stride + j];
+    vz[j] += f * acc[2 * stride + j];
+    if (j < bp.n_gas) {
+        if (u) u[j] += f * acc[3 * stride + j];
+        kick_switches(sk, j, f);
+    }
+}
+
+// Active particles, unless t_next ends the run: the step from the criteria, longer than before only
+// where t_next is a multiple of it; [tb, te] = [t_next, t_next + L]; first half kick v += a L/2.
+__global__ void k_bins_newstep(BinsParams bp, evol_dev d, TsParams tp, float *vx, float *vy, float *vz, float *u,
+                               const float *acc, int64_t stride, const float *h, const float *eps, SwitchKick sk)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= bp.n || !d.bact[j]) return;
+    const unsigned long long tn = d.bt[1];
+    if (tn >= bp.t_end) return;
+    const float dt = particle_criterion(j, bp.n_gas, d, tp, vx, vy, vz, u, acc, stride, h, eps);
+    unsigned long long L = step_for(dt, bp);
+    if (!((float)bp.tick <= dt)) atomicAdd(&d.bt[5], 1ull);       // below one tick (or none): finest step
+    if (tn > 0) L = min(L, tn & (~tn + 1ull));                      // the largest power of two dividing t_next
+    d.tb[j] = tn;
+    d.te[j] = tn + L;
+    const float f = 0.5f * (float)L * bp.tick;
+    vx[j] += f * acc[j];
+    vy[j] += f * acc[stride + j];
+    vz[j] += f * acc[2 * stride + j];
+    if (j < bp.n_gas) {
+        if (u) u[j] += f * acc[3 * stride + j];
+        kick_switches(sk, j, f);
+    }
+}
+
+// Wake-up: an inactive gas particle whose step exceeds wake times the step just completed by an
+// active SPH neighbour (d.nbmin, sorted) ends its step at the first multiple of L' > t_next, L' the
+// largest power of two <= wake x that step; the part of its first half kick beyond the shortened
+// step is taken back.
+__global__ void k_bins_wake(BinsParams bp, evol_dev d, float *vx, float *vy, float *vz, float *u, const float *acc,
+                            int64_t stride, SwitchKick sk)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= bp.n_gas || d.bact[j]) return;
+    const unsigned m = d.nbmin[d.inv[j]];
+    if (m == 0xffffffffu) return;
+    const unsigned long long tb = d.tb[j], te = d.te[j], Lj = te - tb, tn = d.bt[1];
+    const float lim = bp.wake * (float)m;
+    if (!((float)Lj > lim)) return;
+    unsigned long long Lw = 1ull;
+    while (2ull * Lw <= bp.T && (float)(2ull * Lw) <= lim) Lw *= 2ull;
+    if (Lw >= Lj) return;
+    const unsigned long long ten = (tn / Lw + 1ull) * Lw;
+    if (ten >= te) return;
+    const float f = -0.5f * (float)(Lj - (ten - tb)) * bp.tick;
+    vx[j] += f * acc[j];
+    vy[j] += f * acc[stride + j];
+    vz[j] += f * acc[2 * stride + j];
+    if (u) u[j] += f * acc[3 * stride + j];
+    kick_switches(sk, j, f);
+    d.te[j] = ten;
+    atomicAdd(&d.bt[4], 1ull);
+}
+
+// t_sys = t_next; counts
+__global__ void k_bins_advance(BinsParams bp, evol_dev d)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    d.bt[0] = d.bt[1];
+    d.bt[2] += 1ull;
+    d.bt[3] += (unsigned long long)d.acts[bp.n];
+}
+
+// Start of a run: every particle active at t = 0 (its first step is chosen by k_bins_newstep).
+__global__ void k_bins_start(BinsParams bp, evol_dev d)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < bp.n) {
+        d.tb[j] = 0ull;
+        d.te[j] = 0ull;
+        d.bact[j] = 1;
+    }
+    if (j < 6) d.bt[j] = 0ull;
+}
+
 }  // namespace
 
 static SwitchKick switch_kick(const evol_particles *p, const evol_params *prm, const float *dalpha,
@@ -380,7 +572,7 @@ int evol_launch_unpermute_ex(evol_ctx *c, const evol_particles *p, const evol_ou
     const evol_outputs *q = o ? o : &z;
     k_unpermute<<<(n + 255) / 256, 256, 0, c->stream>>>(n, (int)p->n_gas, what, add_acc, c->d, p->h, p->eps, q->ax,
                                                         q->ay, q->az, q->pot, q->rho, q->P, q->c, q->omega, q->zeta,
-                                                        q->dudt, q->ups, q->X, q->dalpha, q->dalpha_u);
+                                                        q->dudt, q->ups, q->X, q->dalpha, q->dalpha_u, c->cap);
     return evol_cuda_ok(cudaGetLastError());
 }
 
@@ -430,6 +622,60 @@ int evol_launch_integrator_step(evol_ctx *c, const evol_particles *p, const evol
     } else {
         k_kick_dev<<<gb, tb, 0, c->stream>>>(n, ng, c->d.dt, 0.5f, (float *)p->vx, (float *)p->vy, (float *)p->vz,
                                              (float *)p->u, c->kdk_acc, cap, sk);
+    }
+    return evol_cuda_ok(cudaGetLastError());
+}
+
+// Individual time steps (Sect. 4.2.1): the kernels of one stage of a system step (see evol_run_bins).
+//   stage 0: start (every particle active at t = 0, first steps and first half kicks)
+//   stage 1: t_next, drift, active flags, prediction times
+//   stage 2: inactive particles' last evaluation into sorted order
+//   stage 3: second half kicks, new steps and first half kicks, wake-up, t_sys = t_next
+int evol_launch_bins(evol_ctx *c, const evol_particles *p, const evol_params *prm, const evol_bins *bp, int stage)
+{
+    const int n = (int)p->n, ng = (int)p->n_gas;
+    const int tb = 256, gb = (n + tb - 1) / tb;
+    const int64_t cap = c->cap;
+    BinsParams b{};
+    b.T = 1ull << bp->max_bin;
+    b.tick = (float)((double)bp->crit.dt_max / (double)b.T);
+    b.wake = bp->wake_factor;
+    b.n = n;
+    b.n_gas = ng;
+    b.periodic_mask = prm->periodic_mask;
+    for (int a = 0; a < 3; ++a) {
+        b.lo[a] = prm->periodic_lo[a];
+        b.len[a] = prm->periodic_hi[a] - prm->periodic_lo[a];
+    }
+    b.t_end = c->bins_t_end;
+    const SwitchKick sk = switch_kick(p, prm, c->kdk_acc + 4 * cap, c->kdk_acc + 5 * cap);
+    const evol_integrator *ip = &bp->crit;
+    TsParams tp{ip->eta_acc, ip->eta_vel, ip->eta_av, ip->eta_courant, ip->eta_u, prm->alpha, prm->beta,
+                prm->gravity, prm->sph && ng > 0, prm->sph && prm->variable_alpha};
+    float *vx = (float *)p->vx, *vy = (float *)p->vy, *vz = (float *)p->vz, *u = (float *)p->u;
+    switch (stage) {
+    case 0:
+        k_bins_start<<<gb, tb, 0, c->stream>>>(b, c->d);
+        k_bins_newstep<<<gb, tb, 0, c->stream>>>(b, c->d, tp, vx, vy, vz, u, c->kdk_acc, cap, p->h, p->eps, sk);
+        break;
+    case 1:
+        cudaMemsetAsync(c->d.bt + 1, 0xff, sizeof(unsigned long long), c->stream);
+        k_bins_next<<<c->num_sms * 4, 256, 0, c->stream>>>(b, c->d);
+        k_bins_drift<<<gb, tb, 0, c->stream>>>(b, c->d, (float *)p->x, (float *)p->y, (float *)p->z, p->vx, p->vy,
+                                               p->vz);
+        break;
+    case 2:
+        k_bins_fill<<<gb, tb, 0, c->stream>>>(b, c->d, cap);
+        break;
+    case 3:
+        k_bins_kick2<<<gb, tb, 0, c->stream>>>(b, c->d, vx, vy, vz, u, c->kdk_acc, cap, sk);
+        k_bins_newstep<<<gb, tb, 0, c->stream>>>(b, c->d, tp, vx, vy, vz, u, c->kdk_acc, cap, p->h, p->eps, sk);
+        if (bp->wake_factor > 0.f && ng > 0)
+            k_bins_wake<<<(ng + tb - 1) / tb, tb, 0, c->stream>>>(b, c->d, vx, vy, vz, u, c->kdk_acc, cap, sk);
+        k_bins_advance<<<1, 32, 0, c->stream>>>(b, c->d);
+        break;
+    default:
+        return EVOL_EINVAL;
     }
     return evol_cuda_ok(cudaGetLastError());
 }

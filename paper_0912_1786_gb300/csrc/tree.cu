@@ -293,7 +293,8 @@ __global__ void k_permute(int n, int n_gas, const int32_t *__restrict__ perm, co
                           const float *__restrict__ u, const float *__restrict__ h, const float *__restrict__ eps,
                           float4 *__restrict__ pos, float4 *__restrict__ vel, float *__restrict__ lh,
                           float *__restrict__ le, int32_t *__restrict__ orig, int32_t *__restrict__ inv,
-                          const float *__restrict__ pred_dt, const float *__restrict__ pred_acc, int64_t stride)
+                          const float *__restrict__ pred_dt, const float *__restrict__ pred_acc, int64_t stride,
+                          const float *__restrict__ pred_tau)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -301,12 +302,13 @@ __global__ void k_permute(int n, int n_gas, const int32_t *__restrict__ perm, co
     bool gas = j < n_gas;
     pos[s] = make_float4(x[j], y[j], z[j], m[j]);
     float4 v = make_float4(vx ? vx[j] : 0.f, vy ? vy[j] : 0.f, vz ? vz[j] : 0.f, (gas && u) ? u[j] : 0.f);
-    if (pred_dt) {
+    if (pred_dt || pred_tau) {
         // integrator: the force step sees the velocity and internal energy predicted to the end of
         // the step, v_n + a_n dt and u_n + (du/dt)_n dt (Sect. 4.1); the caller's arrays hold the
         // half-kicked values, so half a step of the previous accelerations (pred_acc: ax | ay | az |
-        // du/dt in the caller's order, `stride` apart) is added
-        const float hdt = 0.5f * *pred_dt;
+        // du/dt in the caller's order, `stride` apart) is added -- with individual steps each
+        // particle's own time since the middle of its step, pred_tau[j]
+        const float hdt = pred_tau ? pred_tau[j] : 0.5f * *pred_dt;
         v.x += hdt * pred_acc[j];
         v.y += hdt * pred_acc[stride + j];
         v.z += hdt * pred_acc[2 * stride + j];
@@ -887,6 +889,36 @@ static int scan_i32(evol_ctx *c, int n, const int32_t *in, int32_t *out, int wri
     return evol_cuda_ok(cudaGetLastError());
 }
 
+namespace {
+__global__ void k_active_flags(int n, const int32_t *__restrict__ orig, const int32_t *__restrict__ bact,
+                               int32_t *__restrict__ actf)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) actf[s] = bact[orig[s]];
+}
+
+__global__ void k_active_scatter(int n, const int32_t *__restrict__ actf, const int32_t *__restrict__ acts,
+                                 int32_t *__restrict__ act)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n && actf[s]) act[acts[s]] = s;
+}
+}  // namespace
+
+// The active list of an individual-time-step system step: the sorted positions of the flagged
+// particles in ascending order (so that consecutive entries stay close in space), and their
+// number at d.acts[n].
+int evol_launch_active_list(evol_ctx *c, int n)
+{
+    evol_dev &d = c->d;
+    int tb = 256, gb = (n + tb - 1) / tb;
+    k_active_flags<<<gb, tb, 0, c->stream>>>(n, d.orig, d.bact, d.actf);
+    int rc = scan_i32(c, n, d.actf, d.acts, 1);
+    if (rc) return rc;
+    k_active_scatter<<<gb, tb, 0, c->stream>>>(n, d.actf, d.acts, d.act);
+    return evol_cuda_ok(cudaGetLastError());
+}
+
 int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *prm)
 {
     evol_dev &d = c->d;
@@ -936,7 +968,7 @@ int evol_launch_build(evol_ctx *c, const evol_particles *p, const evol_params *p
     }
     k_permute<<<gb, tb, 0, st>>>(n, (int)p->n_gas, d.vals_a, p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->u,
                                  p->h, p->eps, d.pos, d.vel, d.len_h, d.len_eps, d.orig, d.inv,
-                                 c->pred_dt, c->kdk_acc, c->cap);
+                                 c->pred_dt, c->kdk_acc, c->cap, c->pred_tau);
     k_lcp<<<gb, tb, 0, st>>>(n, d.keys_a, d.sys_off, nsys, d.lcp, d.sys_sorted);
     k_count<<<gb, tb, 0, st>>>(n, d.lcp, leaf, d.cnt);
     int rc = scan_i32(c, n, d.cnt, d.base, 1);

@@ -60,6 +60,8 @@ struct WalkSmem {
     float4 gbox[WK_WARPS][3];     // group bounds: centre, 0 | half widths, 0 | emax, emin, hmax, hmin
     unsigned wc[WK_WARPS][8];     // per-group work counts kept by lane 0 (see the end of k_walk)
     float mum[WK_WARPS][32];      // largest |mu_ij| of each lane's particle (viscosity)
+    int gs[WK_WARPS][32];         // active list: the sorted position of each lane's particle
+    unsigned gself[WK_WARPS][32]; // active list: the lane whose particle is a leaf chunk's entry
 };
 
 // The kernel functions of the pair loop in a division-free form: each takes u and iu = 1/u (iu is
@@ -222,7 +224,9 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int n = kp.n;
-    const int ngroups = (n + 31) >> 5;
+    // individual time steps: groups of 32 consecutive entries of the active list
+    const int nlist = kp.active ? d.acts[n] : n;
+    const int ngroups = (nlist + 31) >> 5;
     // periodic axes come only with SPH alone (periodic gravity is rejected by the entry points)
     const int pm = (SPH && !GRAV) ? kp.periodic_mask : 0;
     const float plen0 = kp.plen[0], plen1 = kp.plen[1], plen2 = kp.plen[2];
@@ -233,9 +237,12 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
         if (lane == 0) g = (int)atomicAdd(queue, 1ull);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ngroups) break;
-        const int s = g * 32 + lane;
-        const bool valid = s < n;
+        const int e = g * 32 + lane;
+        const bool valid = e < nlist;
+        const int s = kp.active ? (valid ? d.act[e] : 0) : e;
         const float4 pi = valid ? d.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        // the group's sorted positions, for the self test of the near list (active list only)
+        if (kp.active) sm.gs[w][lane] = valid ? s : -1;
         // this lane's hydro operands (v, P/rho^2, c, rho, 1/h, zeta/Omega*) are read where they are
         // used, in the SPH pass, which keeps them out of the traversal's live registers
         const float4 g0 = valid ? d.grav[s] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -432,6 +439,12 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                 const float4 hi = (SPH && valid) ? d.hydro[s] : z4;
                 const float4 si = (SPH && valid) ? d.snd[s] : z4;
                 const float4 di = (DISS && gas_i) ? d.diss[s] : z4;
+                // wake-up: this particle's step (ticks), recorded at each SPH neighbour
+                unsigned Li = 0u;
+                if (kp.wake && gas_i) {
+                    const int ji = d.orig[s];
+                    Li = (unsigned)(d.te[ji] - d.tb[ji]);
+                }
                 while (__any_sync(0xffffffffu, sbits != 0ull)) {
                     if (lane == 0) wc[2] += 32u;
                     if (sbits) {
@@ -475,6 +488,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                                 ++csph;
                                 hsph += evol_mix64((unsigned long long)sm.norig[w][t]);
                             }
+                            if (kp.wake) atomicMin(&d.nbmin[sm.near_j[w][t]], Li);
                             if (r2 > 0.f) {
                                 const float4 hj = sm.nh[w][t];
                                 const float4 sj = sm.ns[w][t];
@@ -746,11 +760,26 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                 for (int b = b0; b < e0; b += 32) {
                     const int kc = min(32, e0 - b);
                     if (nnear + kc > NEARCAP) flush_near();
-                    if (lane < kc) {
-                        // the particle itself never pairs with itself: its lane leaves the entry's mask
-                        const int j = b + lane, sl = j - g * 32;
-                        sm.near_j[w][nnear + lane] = j;
-                        sm.near_mask[w][nnear + lane] = ok & ~((sl >= 0 && sl < 32) ? (1u << sl) : 0u);
+                    if (!kp.active) {
+                        if (lane < kc) {
+                            // the particle itself never pairs with itself: its lane leaves the mask
+                            const int j = b + lane, sl = j - g * 32;
+                            sm.near_j[w][nnear + lane] = j;
+                            sm.near_mask[w][nnear + lane] = ok & ~((sl >= 0 && sl < 32) ? (1u << sl) : 0u);
+                        }
+                    } else {
+                        // active list: the group's lanes hold arbitrary sorted positions; the lane
+                        // whose particle is entry b + q marks slot q, and that bit leaves the mask
+                        if (lane < kc) sm.gself[w][lane] = 0u;
+                        __syncwarp();
+                        const int mine = sm.gs[w][lane];
+                        if (mine >= b && mine < b + kc) sm.gself[w][mine - b] = 1u << lane;
+                        __syncwarp();
+                        if (lane < kc) {
+                            sm.near_j[w][nnear + lane] = b + lane;
+                            sm.near_mask[w][nnear + lane] = ok & ~sm.gself[w][lane];
+                        }
+                        __syncwarp();
                     }
                     nnear += kc;
                 }
@@ -922,6 +951,8 @@ int evol_launch_walk(evol_ctx *c, const evol_particles *p, const evol_params *pr
     for (int a = 0; a < 3; ++a) kp.plen[a] = prm->periodic_hi[a] - prm->periodic_lo[a];
     kp.stack_cap = (int)c->wstack_lim;
     kp.stack_stride = (int)c->wstack_cap;
+    kp.active = c->bins_active;
+    kp.wake = c->bins_active && do_sph && c->d.nbmin != nullptr && c->bins_wake;
     kp.diss = do_sph && evol_diss_on(prm);
     kp.visc_form = prm->visc_form;
     kp.balsara = prm->balsara;

@@ -18,7 +18,7 @@ EVOL_EOVERFLOW, EVOL_ENOCONV, EVOL_ETIMEOUT, EVOL_ENAN, EVOL_ESTATE = -4, -5, -6
 EVOL_FP32_PLAIN, EVOL_FP32_MIXED = 0, 1
 EVOL_DBG_KEYS, EVOL_DBG_PERM, EVOL_DBG_NODES, EVOL_DBG_CUBE = 1, 2, 3, 4
 EVOL_DBG_MOMENTS, EVOL_DBG_HASHES, EVOL_DBG_COUNTS, EVOL_DBG_FLOW = 5, 6, 7, 8
-EVOL_DBG_DISS = 9
+EVOL_DBG_DISS, EVOL_DBG_BINS = 9, 10
 EVOL_VISC_MONAGHAN, EVOL_VISC_SIGNAL = 0, 1
 EVOL_COND_VSIG_SOUND, EVOL_COND_VSIG_PRESSURE = 0, 1
 EVOL_COND_SRC_SQRTU, EVOL_COND_SRC_LINEAR = 0, 1
@@ -54,6 +54,10 @@ class EvolIntegrator(C.Structure):
                 ("predicted_velocity", C.c_int), ("predict_lengths", C.c_int)]
 
 
+class EvolBins(C.Structure):
+    _fields_ = [("crit", EvolIntegrator), ("max_bin", C.c_int), ("wake_factor", C.c_float)]
+
+
 class EvolOutputs(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("ax", "ay", "az", "pot", "rho", "P", "c", "omega", "zeta",
                                            "dudt", "ups", "X", "dalpha", "dalpha_u")]
@@ -86,6 +90,8 @@ def lib():
         L.evol_kdk.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs), C.c_float, C.c_int]
         L.evol_run.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolIntegrator), pp(EvolOutputs), C.c_int,
                                pp(C.c_double), pp(C.c_float)]
+        L.evol_run_bins.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolBins), pp(EvolOutputs), C.c_int,
+                                    pp(C.c_double), pp(C.c_int64)]
         L.evol_sync.argtypes = [vp]
         L.evol_get_diagnostics.argtypes = [vp, pp(C.c_double)]
         L.evol_get_timings.argtypes = [vp, pp(C.c_float)]
@@ -249,6 +255,25 @@ def evol_run(ctx, particles, params, integrator, outputs, nsteps: int, time: flo
     _check(lib().evol_run(ctx, C.byref(particles), C.byref(params), C.byref(integrator), C.byref(outputs),
                           int(nsteps), C.byref(t), C.byref(dt)), "evol_run")
     return t.value, dt.value
+
+
+def make_bins(max_bin=6, wake_factor=0.0, **crit) -> EvolBins:
+    """EvolBins: crit takes make_integrator's keywords (dt_max is the largest step)."""
+    b = EvolBins()
+    b.crit = make_integrator(**crit)
+    b.max_bin = int(max_bin)
+    b.wake_factor = float(wake_factor)
+    return b
+
+
+def evol_run_bins(ctx, particles, params, bins, outputs, nlargest: int, time: float = 0.0):
+    """Individual power-of-two time steps on the device for nlargest largest steps; updates the
+    particle arrays in place.  Returns (time, [system steps, evaluations, wake-ups, clamped])."""
+    t = C.c_double(float(time))
+    st = (C.c_int64 * 4)()
+    _check(lib().evol_run_bins(ctx, C.byref(particles), C.byref(params), C.byref(bins), C.byref(outputs),
+                               int(nlargest), C.byref(t), st), "evol_run_bins")
+    return t.value, list(st)
 
 
 def evol_sync(ctx, raise_on_error=True):

@@ -54,7 +54,7 @@ def test_binding_struct_layouts_match_header(tmp_path):
     if not cc:
         pytest.skip("no C compiler")
     structs = {"evol_particles": E.EvolParticles, "evol_params": E.EvolParams, "evol_outputs": E.EvolOutputs,
-               "evol_integrator": E.EvolIntegrator}
+               "evol_integrator": E.EvolIntegrator, "evol_bins": E.EvolBins}
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "evol.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
