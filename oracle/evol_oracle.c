@@ -715,6 +715,128 @@ int orc_divv(const orc_tree *t, int mode, const double *L, const double *nsum, c
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Periodic gravity by the Ewald method (Sect. 4.3).                                        */
+/* ------------------------------------------------------------------------------------ */
+
+#define ORC_EWALD_N 64           /* table intervals per axis over the octant [0, L/2] */
+
+/* Ewald correction for a unit mass in a periodic cube of side L (Sect. 4.3, the series of
+ * Hernquist et al. 1991 and Springel 2001 as printed), x = r_i - r_j (nearest image):
+ *   f(x) = x/|x|^3 - sum_{|n|<5} (x - nL)/r_n^3 (erfc(w r_n) + 2 w r_n/sqrt(pi) exp(-w^2 r_n^2))
+ *          - 2/L^2 sum_{0<|h|<5} h/h^2 exp(-pi^2 h^2/(w^2 L^2)) sin(2 pi h.x/L),      w = 2/L,
+ * r_n = |x - nL|, n and h integer triplets; i receives G m_j f(x) beyond the nearest-image force.
+ * Reading: the paper prints the acceleration only; the potential is the matching zero-mean
+ * periodic one, g(x) = 1/|x| - psi(x) with
+ *   psi(x) = sum_n erfc(w r_n)/r_n + 1/(pi L) sum_h exp(-pi^2 h^2/(w^2 L^2))/h^2 cos(2 pi h.x/L)
+ *            - pi/(w^2 L^3),
+ * so that f = -grad g and the potential of i gains G m_j g(x) (g(0), the images of i itself, is
+ * finite).  Reading: |n| < 5 and |h| < 5 are Euclidean norms. */
+void orc_ewald_exact(const double *x, double L, double f[3], double *g)
+{
+    const double w = 2.0 / L, sqpi = sqrt(ORC_PI);
+    double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    double F[3] = {0, 0, 0}, psi = 0.0;
+    for (int a = -4; a <= 4; ++a)
+        for (int b = -4; b <= 4; ++b)
+            for (int c = -4; c <= 4; ++c) {
+                int n2 = a * a + b * b + c * c;
+                if (n2 >= 25) continue;
+                double d[3] = {x[0] - a * L, x[1] - b * L, x[2] - c * L};
+                double rn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                if (n2 == 0) {
+                    /* with the direct term: x/r^3 (1 - erfc - 2 w r/sqrt(pi) e^{-w^2 r^2}) and
+                     * 1/r - erfc/r = erf/r; for small w r by their series */
+                    double z = w * rn;
+                    if (z < 1e-3) {
+                        double z2 = z * z;
+                        double k3 = 4.0 / (3.0 * sqpi) * w * w * w * (1.0 - 0.6 * z2);
+                        for (int q = 0; q < 3; ++q) F[q] += x[q] * k3;
+                        psi += 2.0 * w / sqpi * (1.0 - z2 / 3.0);
+                    } else {
+                        double k = (erf(z) - 2.0 * z / sqpi * exp(-z * z)) / (rn * rn * rn);
+                        for (int q = 0; q < 3; ++q) F[q] += x[q] * k;
+                        psi += erf(z) / rn;
+                    }
+                    continue;
+                }
+                double z = w * rn;
+                double k = (erfc(z) + 2.0 * z / sqpi * exp(-z * z)) / (rn * rn * rn);
+                for (int q = 0; q < 3; ++q) F[q] -= d[q] * k;
+                psi -= erfc(z) / rn;
+            }
+    /* here F = x/r^3 - (real-space sum) and psi (accumulating g) = 1/r - (real-space sum) */
+    for (int a = -4; a <= 4; ++a)
+        for (int b = -4; b <= 4; ++b)
+            for (int c = -4; c <= 4; ++c) {
+                int h2 = a * a + b * b + c * c;
+                if (h2 == 0 || h2 >= 25) continue;
+                double e = exp(-ORC_PI * ORC_PI * h2 / (w * w * L * L));
+                double ph = 2.0 * ORC_PI * (a * x[0] + b * x[1] + c * x[2]) / L;
+                double ks = 2.0 / (L * L) * e / h2 * sin(ph);
+                F[0] -= ks * a;
+                F[1] -= ks * b;
+                F[2] -= ks * c;
+                psi -= e / (ORC_PI * L * h2) * cos(ph);
+            }
+    psi += ORC_PI / (w * w * L * L * L);
+    (void)r;
+    f[0] = F[0];
+    f[1] = F[1];
+    f[2] = F[2];
+    *g = psi;
+}
+
+/* The table of the method (Sect. 4.3): f and g for L = 1 at the grid points (i, j, k) / (2N) of the
+ * octant [0, 1/2]^3, 0 <= i, j, k <= N = ORC_EWALD_N, four values each; built once per process. */
+static double *orc_ewald_tab = NULL;
+
+const double *orc_ewald_table(void)
+{
+    if (orc_ewald_tab) return orc_ewald_tab;
+    const int N = ORC_EWALD_N, M = N + 1;
+    double *tab = malloc((size_t)M * M * M * 4 * sizeof(double));
+    if (!tab) return NULL;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j)
+            for (int k = 0; k < M; ++k) {
+                double x[3] = {0.5 * i / N, 0.5 * j / N, 0.5 * k / N};
+                double *o = tab + 4 * (((size_t)i * M + j) * M + k);
+                orc_ewald_exact(x, 1.0, o, o + 3);
+            }
+    orc_ewald_tab = tab;
+    return tab;
+}
+
+/* Trilinear interpolation in the table (Sect. 4.3) for a nearest-image x (|x_a| <= L/2) in a cube of
+ * side L: each component of f is odd in its own coordinate and even in the others, g is even, so
+ * the octant table serves every x: f_a(x) = sign(x_a) F_a(|x|) / L^2, g(x) = G(|x|) / L. */
+void orc_ewald_interp(double L, const double *x, double f[3], double *g)
+{
+    const double *tab = orc_ewald_table();
+    const int N = ORC_EWALD_N, M = N + 1;
+    int i0[3];
+    double t[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = fabs(x[a]) / L * 2.0 * N;
+        int i = (int)floor(u);
+        if (i > N - 1) i = N - 1;
+        if (i < 0) i = 0;
+        i0[a] = i;
+        t[a] = u - i;
+    }
+    double v[4] = {0, 0, 0, 0};
+    for (int c = 0; c < 8; ++c) {
+        int di = c >> 2 & 1, dj = c >> 1 & 1, dk = c & 1;
+        double wgt = (di ? t[0] : 1 - t[0]) * (dj ? t[1] : 1 - t[1]) * (dk ? t[2] : 1 - t[2]);
+        const double *o = tab + 4 * (((size_t)(i0[0] + di) * M + (i0[1] + dj)) * M + (i0[2] + dk));
+        for (int q = 0; q < 4; ++q) v[q] += wgt * o[q];
+    }
+    for (int a = 0; a < 3; ++a) f[a] = (x[a] < 0 ? -v[a] : v[a]) / (L * L);
+    *g = v[3] / L;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Forces: tree walk with the Dubinski opening criterion, far nodes by monopole +          */
 /* quadrupole, near particles by the softened symmetric pair force with the adaptive      */
 /* softening correction, and SPH pressure + viscosity + du/dt on the same near list.       */
@@ -738,6 +860,7 @@ typedef struct {
     double theta, G, gamma, alpha, beta;
     int gravity, sph, adaptive, use_tc;
     orc_diss ds;
+    double ewald_L;       /* > 0: periodic gravity in a cube of this side (Ewald, Sect. 4.3) */
 } orc_params;
 
 /* Per-particle state needed by the force pass (original order, length n).  Fields of species
@@ -812,6 +935,14 @@ static void orc_pair(const orc_tree *t, const orc_params *pr, const orc_state *s
             }
             for (int a = 0; a < 3; ++a) res->a[a] += f * rv[a];
             res->aabs += fabs(f) * r;
+        }
+        if (pr->ewald_L > 0) {
+            /* the replicas of j beyond its nearest image (Sect. 4.3, tabulated correction) */
+            double fe[3], ge;
+            orc_ewald_interp(pr->ewald_L, rv, fe, &ge);
+            for (int a = 0; a < 3; ++a) res->a[a] += pr->G * mj * fe[a];
+            res->aabs += pr->G * mj * sqrt(fe[0] * fe[0] + fe[1] * fe[1] + fe[2] * fe[2]);
+            res->pot += pr->G * mj * ge;
         }
     }
     if (pr->sph && i < t->n_gas && j < t->n_gas) {
@@ -893,10 +1024,14 @@ static void orc_pair(const orc_tree *t, const orc_params *pr, const orc_state *s
 /* Far node: Newtonian monopole + traceless quadrupole about the centre of mass,
  * d = r_i - com: a = -G M d/d^3 + G [Q d / d^5 - 5/2 (d.Q.d) d / d^7],
  * phi = -G M / d - G/2 (d.Q.d) / d^5. */
-static void orc_far(const orc_tree *t, const orc_params *pr, int64_t id, const double *p, orc_result *res)
+static void orc_far(const orc_tree *t, const orc_params *pr, const orc_period *pp, int64_t id, const double *p,
+                    orc_result *res)
 {
     const double *c = &t->com[3 * id], *q = &t->Q[6 * id];
+    /* periodic gravity: the nearest image of the centre of mass */
     double d[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+    if (pr->ewald_L > 0)
+        for (int a = 0; a < 3; ++a) d[a] = orc_wrap(pp, a, d[a]);
     double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     double di = 1.0 / sqrt(d2), di2 = di * di;
     double di3 = di * di2, di5 = di3 * di2, di7 = di5 * di2;
@@ -912,6 +1047,15 @@ static void orc_far(const orc_tree *t, const orc_params *pr, int64_t id, const d
     }
     res->aabs += sqrt(mag);
     res->pot += pr->G * (-M * di - 0.5 * dQd * di5);
+    if (pr->ewald_L > 0) {
+        /* replicas of the node: its mass at the centre of mass (reading: the correction is taken
+         * for the monopole; the quadrupole's replicas are left out) */
+        double fe[3], ge;
+        orc_ewald_interp(pr->ewald_L, d, fe, &ge);
+        for (int a = 0; a < 3; ++a) res->a[a] += pr->G * M * fe[a];
+        res->aabs += pr->G * M * sqrt(fe[0] * fe[0] + fe[1] * fe[1] + fe[2] * fe[2]);
+        res->pot += pr->G * M * ge;
+    }
 }
 
 /* Opening test of node id for particle i (Sect. 2.2, Eq. opcrit plus the near test).
@@ -936,11 +1080,25 @@ static int orc_accept(const orc_tree *t, const orc_params *pr, const orc_period 
     int far = bd > R;
     if (pr->gravity) {
         const double *c = &t->com[3 * id];
-        double d = sqrt((p[0] - c[0]) * (p[0] - c[0]) + (p[1] - c[1]) * (p[1] - c[1]) +
-                        (p[2] - c[2]) * (p[2] - c[2]));
+        double dv[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+        if (pr->ewald_L > 0)
+            for (int a = 0; a < 3; ++a) dv[a] = orc_wrap(pp, a, dv[a]);
+        double d = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
         double ropen = (pr->theta > 0) ? t->l[id] / pr->theta + t->delta[id] : INFINITY;
         orc_margin(res, d, ropen);
         far = far && (d > ropen);
+        if (pr->ewald_L > 0) {
+            /* periodic gravity: the node is taken whole at one image only if its particle box
+             * lies inside the cube of side L centred on the particle (every particle of the node
+             * then has its nearest image in that box): |r_i - box centre|_a + half width_a < L/2 */
+            for (int a = 0; a < 3; ++a) {
+                double bc = 0.5 * (t->bmin[3 * id + a] + t->bmax[3 * id + a]);
+                double bw = 0.5 * (t->bmax[3 * id + a] - t->bmin[3 * id + a]);
+                double e = fabs(orc_wrap(pp, a, p[a] - bc)) + bw;
+                orc_margin(res, e, 0.5 * pr->ewald_L);
+                far = far && (e < 0.5 * pr->ewald_L);
+            }
+        }
     }
     return far;
 }
@@ -956,7 +1114,7 @@ static void orc_force_one(const orc_tree *t, const orc_params *pr, const orc_per
     /* Pre-order walk; nnext skips a subtree. */
     while (id < nn) {
         if (orc_accept(t, pr, pp, st, i, id, p, res)) {
-            if (pr->gravity) orc_far(t, pr, id, p, res);
+            if (pr->gravity) orc_far(t, pr, pp, id, p, res);
             res->nfar += 1;
             res->hfar += orc_hash_id((uint64_t)id);
             id = t->nnext[id];
@@ -977,6 +1135,12 @@ static void orc_force_one(const orc_tree *t, const orc_params *pr, const orc_per
     }
     /* self term of the potential, phi(0, eps_i) (the double sum of Eq. Lgrav includes k = j) */
     if (pr->gravity) res->pot += pr->G * t->m[i] * orc_phi(0.0, st->eps[i]);
+    /* periodic gravity: the particle's own replicas */
+    if (pr->gravity && pr->ewald_L > 0) {
+        double z[3] = {0, 0, 0}, fe[3], ge;
+        orc_ewald_interp(pr->ewald_L, z, fe, &ge);
+        res->pot += pr->G * t->m[i] * ge;
+    }
 }
 
 /* Force pass for the particles in idx (all if idx == NULL).  Outputs at original index. */
@@ -994,12 +1158,17 @@ void orc_forces(orc_tree *t, double theta, double G, double gamma, double alpha,
                 double *aabs, double *duabs, double *mumax,
                 const orc_diss *diss, double *vsig, double *lapu, double *lapabs)
 {
-    orc_params pr = {theta, G, gamma, alpha, beta, gravity, sph, adaptive, use_tc, {0}};
+    orc_params pr = {theta, G, gamma, alpha, beta, gravity, sph, adaptive, use_tc, {0}, 0.0};
     if (diss) pr.ds = *diss;
     orc_state st = {vx, vy, vz, eps, ups, X, h, rho, P, c, om, zeta};
     orc_period per = {periodic_mask, {0, 0, 0}, {1, 1, 1}};
     for (int a = 0; a < 3; ++a)
         if ((periodic_mask >> a) & 1) { per.lo[a] = plo[a]; per.len[a] = phi_[a] - plo[a]; }
+    /* periodic gravity: a cube periodic in all three axes (Sect. 4.3); the table is built first */
+    if (gravity && periodic_mask == 7) {
+        pr.ewald_L = per.len[0];
+        orc_ewald_table();
+    }
     orc_set_node_lengths(t, gravity ? eps : NULL, sph ? h : NULL);
     int64_t count = idx ? nidx : t->n;
 #pragma omp parallel for schedule(dynamic, 32)

@@ -73,6 +73,8 @@ def lib():
         L.orc_divv.argtypes = [C.c_void_p, C.c_int, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, C.c_void_p,
                                C.c_int64, C.c_int, _f64p, _f64p, _f64p, C.c_void_p]
         L.orc_eos.argtypes = [C.c_int64, d, _f64p, _f64p, _f64p, _f64p]
+        L.orc_ewald_exact.argtypes = [_f64p, d, _f64p, _f64p]
+        L.orc_ewald_interp.argtypes = [d, _f64p, _f64p, _f64p]
         L.orc_sph_nbmin.restype = C.c_int
         L.orc_sph_nbmin.argtypes = [C.c_void_p, _f64p, C.c_void_p, C.c_int64, _f64p, C.c_int, _f64p, _f64p, _f64p]
         L.orc_num_threads.restype = C.c_int
@@ -102,6 +104,19 @@ class _Kernels:
 
 
 kernels = _Kernels()
+
+
+def ewald(x, L: float = 1.0, exact: bool = True):
+    """The Ewald correction (Sect. 4.3) for a unit mass at nearest-image offset x in a periodic
+    cube of side L: (f, g), the acceleration (per G m) and potential (per G m) of the replicas beyond
+    the nearest image; exact series, or the table interpolation the force pass uses."""
+    xv = np.ascontiguousarray(x, np.float64)
+    f, g = np.zeros(3), np.zeros(1)
+    if exact:
+        lib().orc_ewald_exact(xv, float(L), f, g)
+    else:
+        lib().orc_ewald_interp(float(L), xv, f, g)
+    return f, float(g[0])
 
 
 def eta_from_nnei(n_nei: float) -> float:
