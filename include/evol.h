@@ -15,6 +15,7 @@
  *   - the SPH pressure + artificial-viscosity acceleration and du/dt (Eqs. motionvarmass1,
  *     thermalvarmass1, mu_visc; App. B), with the Thomas-Couchman kernel gradient (Sect. 3
  *     footnote) and nearest-image periodic axes (Sect. 4.3),
+ *   - optionally periodic gravity in a cube by the Ewald method (Sect. 4.3),
  *   - optionally the other dissipation terms of Sect. 3.3.3: the signal-velocity viscosity
  *     (Eqs. pvsig, vsig), the Balsara limiter, per-particle alpha with its time derivative
  *     (Eq. alphaswitch) and the artificial conductivity with per-particle alpha^u.
@@ -101,7 +102,14 @@ typedef struct {
     int sph;                   /* 1: compute SPH density and forces for the gas */
     int adaptive_softening;    /* 1: eps solved with correction terms; 0: eps fixed as given */
     int use_tc_gradient;       /* 1: Thomas-Couchman gradient in the SPH force and du/dt */
-    int periodic_mask;         /* bit a set: axis a periodic (SPH only; gravity must be off) */
+    int periodic_mask;         /* bit a set: axis a periodic.  SPH: any axes (nearest image).  With
+                                  gravity only 7, a cube (equal lengths): periodic gravity by the
+                                  Ewald method (Sect. 4.3) -- nearest images plus the replicas'
+                                  correction, tabulated on a 65^3 octant grid and interpolated
+                                  trilinearly, for every pair and every far node's monopole; the
+                                  potential includes the zero-mean periodic term and the particle's
+                                  own replicas; a node is taken at one image only if its box lies
+                                  inside the cube of side L around the particle */
     float periodic_lo[3], periodic_hi[3];
     int precision;             /* EVOL_FP32_PLAIN or EVOL_FP32_MIXED */
     int leaf_size;             /* a cube is split while it holds more than leaf_size particles

@@ -39,7 +39,7 @@ void free_all(evol_ctx *c)
     evol_dev &d = c->d;
     void *ptrs[] = {d.pos, d.vel, d.grav, d.hydro, d.snd, d.vah, d.orig, d.inv, d.divv_h, d.divv_e, d.mumax, d.dt, d.time, d.len_h, d.len_eps, d.nh, d.omega,
                     d.diss, d.curlv_h, d.vsig, d.lapu, d.dalpha, d.dalpha_u, d.tb, d.te, d.bact, d.pred_tau,
-                    d.pers, d.actf, d.acts, d.act, d.nbmin, d.bt,
+                    d.pers, d.actf, d.acts, d.act, d.nbmin, d.bt, d.ewald,
                     d.zeta, d.rho, d.neps, d.ups, d.X, d.acc, d.dudt, d.keys_a, d.keys_b, d.vals_a, d.vals_b,
                     d.hist, d.lcp, d.cnt, d.base, d.scan_part, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
                     d.nnch, d.narrive, d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nM64, d.nC64, d.nQ64, d.nBmin,
@@ -71,7 +71,14 @@ int check_args(evol_ctx *c, const evol_particles *p, const evol_params *prm)
     if (prm->precision != EVOL_FP32_PLAIN && prm->precision != EVOL_FP32_MIXED) return EVOL_EINVAL;
     if (prm->gravity) {
         if (!p->eps) return EVOL_EINVAL;
-        if (prm->periodic_mask) return EVOL_EINVAL;          // no Ewald summation: periodic gravity unsupported
+        // periodic gravity (Ewald): a cube periodic on all three axes
+        if (prm->periodic_mask) {
+            if (prm->periodic_mask != 7) return EVOL_EINVAL;
+            const float L = prm->periodic_hi[0] - prm->periodic_lo[0];
+            if (!(L > 0.f) || prm->periodic_hi[1] - prm->periodic_lo[1] != L ||
+                prm->periodic_hi[2] - prm->periodic_lo[2] != L)
+                return EVOL_EINVAL;
+        }
         if (prm->adaptive_softening && !(prm->n_nei_grav > 0.f)) return EVOL_EINVAL;
     }
     if (prm->sph && p->n_gas > 0) {
@@ -232,6 +239,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.tb, n); rc |= dalloc(&d.te, n); rc |= dalloc(&d.bact, n); rc |= dalloc(&d.pred_tau, n);
     rc |= dalloc(&d.pers, 7 * n); rc |= dalloc(&d.actf, n); rc |= dalloc(&d.acts, n + 1); rc |= dalloc(&d.act, n);
     rc |= dalloc(&d.nbmin, n); rc |= dalloc(&d.bt, 8);
+    rc |= dalloc(&d.ewald, (int64_t)EVOL_EWALD_M * EVOL_EWALD_M * EVOL_EWALD_M);
     if (!rc && cudaMallocHost((void **)&c->h_bt, 8 * sizeof(unsigned long long)) != cudaSuccess) rc = EVOL_ENOMEM;
     rc |= dalloc(&d.dt, 4); rc |= dalloc(&d.time, 1);
     rc |= dalloc(&d.keys_a, n); rc |= dalloc(&d.keys_b, n); rc |= dalloc(&d.vals_a, n); rc |= dalloc(&d.vals_b, n);
@@ -334,6 +342,7 @@ int evol_gravity(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_ou
     int rc = check_args(c, p, prm);
     if (rc || p->n == 0) return rc;
     if (!prm->gravity) return EVOL_EINVAL;
+    if (prm->periodic_mask == 7 && (rc = evol_ewald_prepare(c))) return set_err(c, rc);
     if ((rc = ensure_tree(c, p, prm))) return set_err(c, rc);
     if (prm->adaptive_softening)
         if ((rc = evol_launch_lengths(c, p, prm, 1))) return set_err(c, rc);
@@ -365,6 +374,10 @@ static int run_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol
 {
     evol_outputs zero{};
     if (!out) out = &zero;
+    if (prm->gravity && prm->periodic_mask == 7) {
+        int erc = evol_ewald_prepare(c);
+        if (erc) return set_err(c, erc);
+    }
     uint64_t sig = 1469598103934665603ull;
     sig = fnv(sig, &c->nsys, sizeof c->nsys);
     sig = fnv(sig, p, sizeof *p);

@@ -48,6 +48,7 @@ struct evol_dev {
     int32_t *actf, *acts, *act;     // sorted: active flags, their exclusive scan (+ total), the list
     unsigned *nbmin;                // sorted: smallest active-neighbour step (wake-up)
     unsigned long long *bt;         // [0] t_sys [1] t_next (ticks); [2..5] run counts
+    float4 *ewald;                  // periodic gravity: correction table (f, g) for L = 1
     float *dt;               // integrator scalars: [0] time step, [1] criterion minimum (as bits)
     double *time;            // integrator time
     float *dudt;             // sorted
@@ -136,6 +137,7 @@ struct evol_ctx {
     cudaGraphExec_t bins_exec;       // one system step of evol_run_bins
     uint64_t bins_sig;
     unsigned long long *h_bt;        // pinned host copy of the system time
+    int ewald_ready;                 // the Ewald table has been computed
 };
 
 // ---- host-side launch helpers (defined in evol_api.cu / tree.cu / walks) ------------------
@@ -149,6 +151,7 @@ int evol_launch_integrator_step(evol_ctx *c, const evol_particles *p, const evol
                                 int stage);
 int evol_launch_bins(evol_ctx *c, const evol_particles *p, const evol_params *prm, const evol_bins *bp, int stage);
 int evol_launch_active_list(evol_ctx *c, int n);
+int evol_ewald_prepare(evol_ctx *c);
 
 #define EVOL_UNPERM_LENGTHS 1
 #define EVOL_UNPERM_DENSITY 2
@@ -244,6 +247,34 @@ __device__ __forceinline__ float evol_wrap(float d, float len, int periodic)
     return periodic ? d - len * rintf(d / len) : d;
 }
 
+// ---- periodic gravity (Ewald, Sect. 4.3) ----------------------------------------------------
+// Correction table for a cube of side 1: (f_x, f_y, f_z, g) at the grid points (i, j, k) / (2 N) of the
+// octant [0, 1/2]^3, 0 <= i, j, k <= N; entry ((i M + j) M + k), M = N + 1.
+#define EVOL_EWALD_N 64
+#define EVOL_EWALD_M (EVOL_EWALD_N + 1)
+
+// Trilinear interpolation for a nearest-image offset (dx, dy, dz); sc = 2 N / L.  Returns f (odd in
+// its own coordinate, even in the others) and g, for L = 1: the caller scales f by 1/L^2, g by 1/L.
+__device__ __forceinline__ float4 evol_ewald_lookup(const float4 *__restrict__ tab, float dx, float dy, float dz,
+                                                    float sc)
+{
+    const float nm1 = (float)(EVOL_EWALD_N - 1);
+    const float ux = fabsf(dx) * sc, uy = fabsf(dy) * sc, uz = fabsf(dz) * sc;
+    const int i = (int)fminf(floorf(ux), nm1), j = (int)fminf(floorf(uy), nm1), k = (int)fminf(floorf(uz), nm1);
+    const float tx = ux - (float)i, ty = uy - (float)j, tz = uz - (float)k;
+    const int M = EVOL_EWALD_M;
+    const float4 *b = tab + ((i * M + j) * M + k);
+    const float4 c000 = b[0], c001 = b[1], c010 = b[M], c011 = b[M + 1];
+    const float4 c100 = b[M * M], c101 = b[M * M + 1], c110 = b[M * M + M], c111 = b[M * M + M + 1];
+    auto lerp4 = [](float4 a, float4 c, float t) {
+        return make_float4(fmaf(t, c.x - a.x, a.x), fmaf(t, c.y - a.y, a.y), fmaf(t, c.z - a.z, a.z),
+                           fmaf(t, c.w - a.w, a.w));
+    };
+    const float4 v = lerp4(lerp4(lerp4(c000, c001, tz), lerp4(c010, c011, tz), ty),
+                           lerp4(lerp4(c100, c101, tz), lerp4(c110, c111, tz), ty), tx);
+    return make_float4(dx < 0.f ? -v.x : v.x, dy < 0.f ? -v.y : v.y, dz < 0.f ? -v.z : v.z, v.w);
+}
+
 // Walk parameters passed by value to kernels.
 struct evol_kparams {
     float theta, G, gamma, alpha, beta;
@@ -261,6 +292,10 @@ struct evol_kparams {
     // positions, ascending; its length at d.acts[n]); the force walk also records, per SPH
     // neighbour, the smallest step (ticks) of an active particle next to it (wake-up)
     int active, wake;
+    // periodic gravity (Ewald): cube side, 2 N / L for the table lookup, the table (L = 1)
+    int ewald;
+    float ewald_L, ewald_sc;
+    const float4 *ewald_tab;
     // dissipation variants (Sect. 3.3.3); diss = any of them on
     int diss, visc_form, balsara, var_alpha, conduction, cond_vsig, cond_source;
     float alpha_min, alpha_tau, alpha_source, alpha_u_min;

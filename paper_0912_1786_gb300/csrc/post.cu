@@ -679,3 +679,77 @@ int evol_launch_bins(evol_ctx *c, const evol_particles *p, const evol_params *pr
     }
     return evol_cuda_ok(cudaGetLastError());
 }
+
+// ---- periodic gravity: the Ewald correction table (Sect. 4.3) ----------------------------------
+namespace {
+
+// One grid point of the table for a cube of side 1 (w = 2): the correction f of the acceleration
+// by the replicas beyond the nearest image and its zero-mean potential g,
+//   f(x) = x/|x|^3 - sum_{|n|<5} (x - n)/r_n^3 (erfc(w r_n) + 2 w r_n/sqrt(pi) e^{-w^2 r_n^2})
+//          - 2 sum_{0<|h|<5} h/h^2 e^{-pi^2 h^2/w^2} sin(2 pi h.x),
+//   g(x) = 1/|x| - sum_n erfc(w r_n)/r_n - 1/pi sum_h e^{-pi^2 h^2/w^2}/h^2 cos(2 pi h.x) + pi/w^2,
+// in FP64 (the n = 0 terms combined with the direct ones, by series near x = 0).
+__global__ void k_ewald_table(float4 *tab)
+{
+    const int N = EVOL_EWALD_N, M = EVOL_EWALD_M;
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= M * M * M) return;
+    const int k = id % M, j = (id / M) % M, i = id / (M * M);
+    const double x[3] = {0.5 * i / N, 0.5 * j / N, 0.5 * k / N};
+    const double w = 2.0, pi = 3.14159265358979323846, sqpi = sqrt(pi);
+    double F[3] = {0.0, 0.0, 0.0}, g = 0.0;
+    for (int a = -4; a <= 4; ++a)
+        for (int b = -4; b <= 4; ++b)
+            for (int c = -4; c <= 4; ++c) {
+                const int n2 = a * a + b * b + c * c;
+                if (n2 >= 25) continue;
+                const double d[3] = {x[0] - a, x[1] - b, x[2] - c};
+                const double rn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                const double z = w * rn;
+                if (n2 == 0) {
+                    if (z < 1e-3) {
+                        const double z2 = z * z;
+                        const double k3 = 4.0 / (3.0 * sqpi) * w * w * w * (1.0 - 0.6 * z2);
+                        for (int q = 0; q < 3; ++q) F[q] += x[q] * k3;
+                        g += 2.0 * w / sqpi * (1.0 - z2 / 3.0);
+                    } else {
+                        const double kk = (erf(z) - 2.0 * z / sqpi * exp(-z * z)) / (rn * rn * rn);
+                        for (int q = 0; q < 3; ++q) F[q] += x[q] * kk;
+                        g += erf(z) / rn;
+                    }
+                    continue;
+                }
+                const double kk = (erfc(z) + 2.0 * z / sqpi * exp(-z * z)) / (rn * rn * rn);
+                for (int q = 0; q < 3; ++q) F[q] -= d[q] * kk;
+                g -= erfc(z) / rn;
+            }
+    for (int a = -4; a <= 4; ++a)
+        for (int b = -4; b <= 4; ++b)
+            for (int c = -4; c <= 4; ++c) {
+                const int h2 = a * a + b * b + c * c;
+                if (h2 == 0 || h2 >= 25) continue;
+                const double e = exp(-pi * pi * h2 / (w * w));
+                const double ph = 2.0 * pi * (a * x[0] + b * x[1] + c * x[2]);
+                const double ks = 2.0 * e / h2 * sin(ph);
+                F[0] -= ks * a;
+                F[1] -= ks * b;
+                F[2] -= ks * c;
+                g -= e / (pi * h2) * cos(ph);
+            }
+    g += pi / (w * w);
+    tab[id] = make_float4((float)F[0], (float)F[1], (float)F[2], (float)g);
+}
+
+}  // namespace
+
+// Build the Ewald table once per context (outside any stream capture: the entry points call this
+// before recording their graphs).
+int evol_ewald_prepare(evol_ctx *c)
+{
+    if (c->ewald_ready) return EVOL_OK;
+    const int cnt = EVOL_EWALD_M * EVOL_EWALD_M * EVOL_EWALD_M;
+    k_ewald_table<<<(cnt + 127) / 128, 128, 0, c->stream>>>(c->d.ewald);
+    if (cudaGetLastError() != cudaSuccess) return EVOL_ECUDA;
+    c->ewald_ready = 1;
+    return EVOL_OK;
+}

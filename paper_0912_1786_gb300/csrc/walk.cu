@@ -216,8 +216,8 @@ struct DissSmem<false> {
 // (the production form) and the SPH-only walk fit five blocks per SM (at most 102 registers), the
 // mixed gravity + SPH walk and the walks with the dissipation variants (DISS) four (128
 // registers), the gravity-only walks and the mixed DISS walks three; the check-mode variants one.
-template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS>
-__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (MIXED && DISS) ? 3 : ((GRAV && MIXED) || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS, bool EWALD>
+__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SPH) || (MIXED && DISS)) ? 3 : ((GRAV && MIXED) || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
     __shared__ DissSmem<DISS> ds;
@@ -227,8 +227,11 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
     // individual time steps: groups of 32 consecutive entries of the active list
     const int nlist = kp.active ? d.acts[n] : n;
     const int ngroups = (nlist + 31) >> 5;
-    // periodic axes come only with SPH alone (periodic gravity is rejected by the entry points)
-    const int pm = (SPH && !GRAV) ? kp.periodic_mask : 0;
+    // periodic axes: SPH alone, or gravity in a periodic cube (EWALD: nearest images plus the
+    // tabulated correction of the replicas, Sect. 4.3); pmg: the periodic axes of the gravity tests
+    const int pm = ((SPH && !GRAV) || EWALD) ? kp.periodic_mask : 0;
+    const int pmg = EWALD ? kp.periodic_mask : 0;
+    const float halfL = 0.5f * kp.ewald_L, iL = EWALD ? 1.f / kp.ewald_L : 0.f;
     const float plen0 = kp.plen[0], plen1 = kp.plen[1], plen2 = kp.plen[2];
     const float inv_pi = 1.f / EVOL_PI_F;
 
@@ -312,6 +315,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
             const f32x2 PX = pk2(pi.x, pi.x), PY = pk2(pi.y, pi.y), PZ = pk2(pi.z, pi.z);
             const f32x2 KM25 = pk2(-2.5f, -2.5f), KM05 = pk2(-0.5f, -0.5f);
             f32x2 fax = 0ull, fay = 0ull, faz = 0ull, fpot = 0ull;      // +0.0f in both halves
+            float4 ew = make_float4(0.f, 0.f, 0.f, 0.f);                // Ewald corrections (x M)
             for (int e = 0; e < padded; e += TRIP) {
 #pragma unroll
                 for (int u = 0; u < EVOL_FAR_UNROLL; ++u) {
@@ -320,7 +324,26 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                     const ulonglong2 *F = reinterpret_cast<const ulonglong2 *>(sm.fpair[w][pp]);
                     const ulonglong2 v0 = F[0], v1 = F[1], v2 = F[2], v3 = F[3], v4 = F[4];
                     // v0 = (x, y), v1 = (z, -M), v2 = (Qxx, Qyy), v3 = (Qzz, Qxy), v4 = (Qxz, Qyz)
-                    const f32x2 dx = sub2(PX, v0.x), dy = sub2(PY, v0.y), dz = sub2(PZ, v1.x);
+                    f32x2 dx = sub2(PX, v0.x), dy = sub2(PY, v0.y), dz = sub2(PZ, v1.x);
+                    if constexpr (EWALD) {
+                        // nearest image of the centre of mass, and the node's replicas beyond it
+                        // (monopole: its mass at the centre of mass)
+                        dx = pk2(evol_wrap(lo2(dx), plen0, pmg & 1), evol_wrap(hi2(dx), plen0, pmg & 1));
+                        dy = pk2(evol_wrap(lo2(dy), plen1, pmg & 2), evol_wrap(hi2(dy), plen1, pmg & 2));
+                        dz = pk2(evol_wrap(lo2(dz), plen2, pmg & 4), evol_wrap(hi2(dz), plen2, pmg & 4));
+                        if ((mk.x >> lane) & 1u) {
+                            const float4 c = evol_ewald_lookup(kp.ewald_tab, lo2(dx), lo2(dy), lo2(dz), kp.ewald_sc);
+                            const float Mn = -lo2(v1.y);
+                            ew.x = fmaf(Mn, c.x, ew.x); ew.y = fmaf(Mn, c.y, ew.y);
+                            ew.z = fmaf(Mn, c.z, ew.z); ew.w = fmaf(Mn, c.w, ew.w);
+                        }
+                        if ((mk.y >> lane) & 1u) {
+                            const float4 c = evol_ewald_lookup(kp.ewald_tab, hi2(dx), hi2(dy), hi2(dz), kp.ewald_sc);
+                            const float Mn = -hi2(v1.y);
+                            ew.x = fmaf(Mn, c.x, ew.x); ew.y = fmaf(Mn, c.y, ew.y);
+                            ew.z = fmaf(Mn, c.z, ew.z); ew.w = fmaf(Mn, c.w, ew.w);
+                        }
+                    }
                     const f32x2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
                     const float r0 = ((mk.x >> lane) & 1u) ? rsqrtf(lo2(d2)) : 0.f;
                     const float r1 = ((mk.y >> lane) & 1u) ? rsqrtf(hi2(d2)) : 0.f;
@@ -343,6 +366,13 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
             acc.ay += lo2(fay) + hi2(fay);
             acc.az += lo2(faz) + hi2(faz);
             acc.pot += lo2(fpot) + hi2(fpot);
+            if constexpr (EWALD) {
+                // the table is for a cube of side 1: f scales as 1/L^2, g as 1/L
+                acc.ax += ew.x * iL * iL;
+                acc.ay += ew.y * iL * iL;
+                acc.az += ew.z * iL * iL;
+                acc.pot += ew.w * iL;
+            }
             fold();
             nfar = 0;
             __syncwarp();
@@ -388,6 +418,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
             {
                 const f32x2 PX = pk2(pi.x, pi.x), PY = pk2(pi.y, pi.y), PZ = pk2(pi.z, pi.z);
                 f32x2 nax = 0ull, nay = 0ull, naz = 0ull, npot = 0ull;
+                float4 ewn = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int q = 0; q < (nnear + 1) >> 1; ++q) {
                     const uint2 mk = *reinterpret_cast<const uint2 *>(&sm.near_mask[w][2 * q]);
                     const ulonglong2 *F = reinterpret_cast<const ulonglong2 *>(sm.npair[w][q]);
@@ -401,6 +432,21 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                     const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
                     const float ra = lo2(r2), rb = hi2(r2);
                     const bool mine_a = (mk.x >> lane) & 1u, mine_b = (mk.y >> lane) & 1u;
+                    if constexpr (EWALD) {
+                        // every pair, softened or not: the replicas of j beyond its nearest image
+                        if (mine_a) {
+                            const float4 c = evol_ewald_lookup(kp.ewald_tab, lo2(dx), lo2(dy), lo2(dz), kp.ewald_sc);
+                            const float mj = lo2(v1.y);
+                            ewn.x = fmaf(mj, c.x, ewn.x); ewn.y = fmaf(mj, c.y, ewn.y);
+                            ewn.z = fmaf(mj, c.z, ewn.z); ewn.w = fmaf(mj, c.w, ewn.w);
+                        }
+                        if (mine_b) {
+                            const float4 c = evol_ewald_lookup(kp.ewald_tab, hi2(dx), hi2(dy), hi2(dz), kp.ewald_sc);
+                            const float mj = hi2(v1.y);
+                            ewn.x = fmaf(mj, c.x, ewn.x); ewn.y = fmaf(mj, c.y, ewn.y);
+                            ewn.z = fmaf(mj, c.z, ewn.z); ewn.w = fmaf(mj, c.w, ewn.w);
+                        }
+                    }
                     if (CHECK) cpp += (mine_a ? 1 : 0) + (mine_b ? 1 : 0);
                     bool mark_a = false, mark_b = false;
                     if (GRAV) {
@@ -429,6 +475,12 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                     acc.ay -= lo2(nay) + hi2(nay);
                     acc.az -= lo2(naz) + hi2(naz);
                     acc.pot -= lo2(npot) + hi2(npot);
+                }
+                if constexpr (EWALD) {
+                    acc.ax += ewn.x * iL * iL;
+                    acc.ay += ewn.y * iL * iL;
+                    acc.az += ewn.z * iL * iL;
+                    acc.pot += ewn.w * iL;
                 }
             }
             // Pass 2: the marked pairs of each lane.  Every lane of the warp runs this loop; lanes past
@@ -657,8 +709,15 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                 }
                 bool acc_all = bnear2 > rup * rup * (1.f + TAU);
                 bool open_all = bfar2 < rlo * rlo * (1.f - TAU);
+                if (EWALD) {
+                    // a node is taken whole at one image only inside the cube of side L around
+                    // each particle: |r_i - box centre| + half width < L/2 on every axis
+                    acc_all = acc_all && dx + gwx + C.x < halfL * (1.f - TAU) && dy + gwy + C.y < halfL * (1.f - TAU) &&
+                              dz + gwz + C.z < halfL * (1.f - TAU);
+                }
                 if (GRAV) {
-                    const float ax = fabsf(A.x - gcx), ay = fabsf(A.y - gcy), az = fabsf(A.z - gcz);
+                    const float ax = fabsf(evol_wrap(A.x - gcx, plen0, pmg & 1)), ay = fabsf(evol_wrap(A.y - gcy, plen1, pmg & 2)),
+                                az = fabsf(evol_wrap(A.z - gcz, plen2, pmg & 4));
                     const float mx = fmaxf(ax - gwx, 0.f), my = fmaxf(ay - gwy, 0.f), mz = fmaxf(az - gwz, 0.f);
                     const float Mx = ax + gwx, My = ay + gwy, Mz = az + gwz;
                     acc_all = acc_all && (mx * mx + my * my + mz * mz > A.w * (1.f + TAU));
@@ -692,17 +751,19 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                 if ((Mk >> lane) & 1u) {
                     const float4 B = sm.bB[w][kk];
                     const float4 C = sm.bC[w][kk];
-                    float ex = fabsf(evol_wrap(pi.x - B.x, plen0, pm & 1)) - C.x;
-                    float ey = fabsf(evol_wrap(pi.y - B.y, plen1, pm & 2)) - C.y;
-                    float ez = fabsf(evol_wrap(pi.z - B.z, plen2, pm & 4)) - C.z;
-                    ex = fmaxf(ex, 0.f); ey = fmaxf(ey, 0.f); ez = fmaxf(ez, 0.f);
+                    const float qx = fabsf(evol_wrap(pi.x - B.x, plen0, pm & 1));
+                    const float qy = fabsf(evol_wrap(pi.y - B.y, plen1, pm & 2));
+                    const float qz = fabsf(evol_wrap(pi.z - B.z, plen2, pm & 4));
+                    const float ex = fmaxf(qx - C.x, 0.f), ey = fmaxf(qy - C.y, 0.f), ez = fmaxf(qz - C.z, 0.f);
                     const float bd2 = ex * ex + ey * ey + ez * ez;
                     float R = GRAV ? fmaxf(two_eps_i, C.w) : 0.f;
                     if (SPH && gas_i && B.w >= 0.f) R = fmaxf(R, fmaxf(two_h_i, B.w));
                     far = bd2 > R * R;
+                    if (EWALD) far = far && qx + C.x < halfL && qy + C.y < halfL && qz + C.z < halfL;
                     if (GRAV && far) {
                         const float4 A = sm.bA[w][kk];
-                        const float dx = pi.x - A.x, dy = pi.y - A.y, dz = pi.z - A.z;
+                        const float dx = evol_wrap(pi.x - A.x, plen0, pmg & 1), dy = evol_wrap(pi.y - A.y, plen1, pmg & 2),
+                                    dz = evol_wrap(pi.z - A.z, plen2, pmg & 4);
                         far = dx * dx + dy * dy + dz * dz > A.w;
                     }
                 }
@@ -834,7 +895,9 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
                 ax = (float)(G * tax);
                 ay = (float)(G * tay);
                 az = (float)(G * taz);
-                pot = (float)(G * (tpot - 1.4 * (double)pi.w * (double)ie_i));
+                double self_img = 0.0;
+                if (EWALD) self_img = (double)pi.w * (double)kp.ewald_tab[0].w * (double)iL;   // own replicas
+                pot = (float)(G * (tpot - 1.4 * (double)pi.w * (double)ie_i + self_img));
             }
             ax += (float)thx;
             ay += (float)thy;
@@ -894,43 +957,55 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (GRAV && !SPH) ? 3 : (
     }
 }
 
-template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS>
+template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS, bool EWALD>
 void launch_walk(evol_ctx *c, const evol_kparams &kp)
 {
     static int blocks_per_sm = -1;
     if (blocks_per_sm < 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walk<GRAV, SPH, MIXED, CHECK, DISS>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walk<GRAV, SPH, MIXED, CHECK, DISS, EWALD>,
                                                       WK_THREADS, 0);
         if (blocks_per_sm < 1) blocks_per_sm = 1;
         if (blocks_per_sm > 8) blocks_per_sm = 8;          // stack slots exist for 32 warps per SM
     }
     unsigned long long *q = c->d.counters + 4;
     cudaMemsetAsync(q, 0, sizeof(unsigned long long), c->stream);
-    k_walk<GRAV, SPH, MIXED, CHECK, DISS><<<c->num_sms * blocks_per_sm, WK_THREADS, 0, c->stream>>>(c->d, kp, q);
+    k_walk<GRAV, SPH, MIXED, CHECK, DISS, EWALD><<<c->num_sms * blocks_per_sm, WK_THREADS, 0, c->stream>>>(c->d, kp, q);
 }
 
-template <bool GRAV, bool SPH, bool DISS>
+template <bool GRAV, bool SPH, bool DISS, bool EWALD>
 void launch_walk_pcd(evol_ctx *c, const evol_kparams &kp, bool mixed, bool check)
 {
     if (mixed) {
-        if (check) launch_walk<GRAV, SPH, true, true, DISS>(c, kp);
-        else launch_walk<GRAV, SPH, true, false, DISS>(c, kp);
+        if (check) launch_walk<GRAV, SPH, true, true, DISS, EWALD>(c, kp);
+        else launch_walk<GRAV, SPH, true, false, DISS, EWALD>(c, kp);
     } else {
-        if (check) launch_walk<GRAV, SPH, false, true, DISS>(c, kp);
-        else launch_walk<GRAV, SPH, false, false, DISS>(c, kp);
+        if (check) launch_walk<GRAV, SPH, false, true, DISS, EWALD>(c, kp);
+        else launch_walk<GRAV, SPH, false, false, DISS, EWALD>(c, kp);
     }
+}
+
+template <bool GRAV, bool SPH, bool EWALD>
+void launch_walk_pce(evol_ctx *c, const evol_kparams &kp, bool mixed, bool check)
+{
+    if constexpr (SPH) {
+        if (kp.diss) {
+            launch_walk_pcd<GRAV, SPH, true, EWALD>(c, kp, mixed, check);
+            return;
+        }
+    }
+    launch_walk_pcd<GRAV, SPH, false, EWALD>(c, kp, mixed, check);
 }
 
 template <bool GRAV, bool SPH>
 void launch_walk_pc(evol_ctx *c, const evol_kparams &kp, bool mixed, bool check)
 {
-    if constexpr (SPH) {
-        if (kp.diss) {
-            launch_walk_pcd<GRAV, SPH, true>(c, kp, mixed, check);
+    if constexpr (GRAV) {
+        if (kp.ewald) {
+            launch_walk_pce<GRAV, SPH, true>(c, kp, mixed, check);
             return;
         }
     }
-    launch_walk_pcd<GRAV, SPH, false>(c, kp, mixed, check);
+    launch_walk_pce<GRAV, SPH, false>(c, kp, mixed, check);
 }
 
 }  // namespace
@@ -953,6 +1028,12 @@ int evol_launch_walk(evol_ctx *c, const evol_particles *p, const evol_params *pr
     kp.stack_stride = (int)c->wstack_cap;
     kp.active = c->bins_active;
     kp.wake = c->bins_active && do_sph && c->d.nbmin != nullptr && c->bins_wake;
+    kp.ewald = do_grav && prm->periodic_mask == 7;
+    if (kp.ewald) {
+        kp.ewald_L = prm->periodic_hi[0] - prm->periodic_lo[0];
+        kp.ewald_sc = 2.f * EVOL_EWALD_N / kp.ewald_L;
+        kp.ewald_tab = c->d.ewald;
+    }
     kp.diss = do_sph && evol_diss_on(prm);
     kp.visc_form = prm->visc_form;
     kp.balsara = prm->balsara;
