@@ -427,6 +427,82 @@ def other_forms(torch, dev, stream, E, DeviceSet, w, steps, precision_used, leaf
 DISSIPATION_ALL = dict(visc_form=1, balsara=1, variable_alpha=1, conduction=1)
 
 
+def ewald_block(torch, dev, stream, E, DeviceSet, n, steps):
+    """Periodic gravity (Sect. 4.3): the same particles (a clustered periodic box, gravity only,
+    adaptive softening) once with the Ewald correction and once without periodicity; particles/s,
+    walk time and far-node interactions of each, and their ratio (the paper: the interpolation
+    almost doubles the tree time)."""
+    import dataclasses
+    from paper_0912_1786_gb300 import workloads as W
+    wp = W.periodic_box(n, seed=6)
+    wo = W.Workload(wp.name, wp.x, wp.y, wp.z, wp.vx, wp.vy, wp.vz, wp.m, wp.u, wp.h, wp.eps, n_gas=0,
+                    params=dataclasses.replace(wp.params, periodic_mask=0))
+    out = {"input": f"periodic_box n={n} (half uniform, half three clumps), gravity only, adaptive eps (32)"}
+    for name, ww in (("ewald", wp), ("open", wo)):
+        ds = DeviceSet(ww, device=str(dev))
+        ctx = E.evol_create(ww.n, stream.cuda_stream)
+        try:
+            run = lambda: (ds.reset_lengths(), E.evol_step(ctx, ds.particles, ds.params, ds.outputs))
+            for _ in range(2):
+                run()
+            E.evol_sync(ctx)
+            ms, walks = 0.0, []
+            for _ in range(steps):
+                ms += time_steps(torch, dev, stream, run, 1)
+                walks.append(E.evol_get_timings(ctx)[3])
+            E.evol_sync(ctx)
+            cnt = E.evol_get_counters(ctx)
+            out[name] = {"particles_per_s": ww.n * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                         "walk_ms": statistics.mean(walks), "far_interactions": int(cnt[0]),
+                         "pair_interactions": int(cnt[1])}
+        finally:
+            E.evol_destroy(ctx)
+    out["walk_time_ratio"] = out["ewald"]["walk_ms"] / out["open"]["walk_ms"]
+    return out
+
+
+def bins_block(torch, dev, stream, E, DeviceSet, n):
+    """Individual power-of-two time steps (Sect. 4.2.1) on an Evrard sphere with a hot core (a wide
+    spread of Courant steps): one largest step of evol_run_bins against the same span taken by the
+    global step at the finest step in use, estimated as (system steps + 1) force steps of all
+    particles."""
+    from paper_0912_1786_gb300 import workloads as W
+    w = W.hot_core(W.evrard_sphere(n, seed=21, sigma_v=0.05))
+    ds = DeviceSet(w, device=str(dev))
+    ctx = E.evol_create(w.n, stream.cuda_stream)
+    K, dt_max = 10, 0.0625
+    try:
+        b = E.make_bins(K, 4.0, eta_acc=0.1, eta_courant=0.2, eta_u=0.2, dt_max=dt_max, predicted_velocity=1,
+                        predict_lengths=0)
+        E.evol_run_bins(ctx, ds.particles, ds.params, b, ds.outputs, 1)           # graph recording
+        E.evol_sync(ctx)
+        # the same arrays (the recorded graph holds their addresses) back at the start
+        for k, a in w.arrays().items():
+            t = ds.inp[k]
+            t.copy_(torch.from_numpy(np.ascontiguousarray(a[: t.numel()], np.float32)).to(t.device))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, st = E.evol_run_bins(ctx, ds.particles, ds.params, b, ds.outputs, 1)
+        torch.cuda.synchronize(dev)
+        t_bins = time.perf_counter() - t0
+        E.evol_sync(ctx)
+        # one force step of every particle, the unit of the global-step estimate
+        ds3 = DeviceSet(w, device=str(dev))
+        run = lambda: (ds3.reset_lengths(), E.evol_step(ctx, ds3.particles, ds3.params, ds3.outputs))
+        run()
+        E.evol_sync(ctx)
+        ms_step = time_steps(torch, dev, stream, run, 3) / 3
+    finally:
+        E.evol_destroy(ctx)
+    glob = (st[0] + 1) * ms_step / 1e3
+    return {"input": f"evrard_sphere n={n} with a hot core (u x (1 + 30 exp(-(r/0.2)^2))), sigma_v 0.05",
+            "max_bin": K, "dt_max": dt_max, "wake_factor": 4.0,
+            "system_steps": st[0], "particle_evaluations": st[1], "wakeups": st[2], "criteria_below_tick": st[3],
+            "wall_s": t_bins, "evaluations_per_s": st[1] / t_bins,
+            "global_step_estimate_s": glob, "speedup_vs_global_step": glob / t_bins,
+            "note": "wall time includes one host synchronisation per system step"}
+
+
 def dissipation_form(torch, dev, stream, E, DeviceSet, w, steps, leaf, ostate, sample=2000):
     """The dissipation variants (signal-velocity viscosity, Balsara limiter, variable alpha,
     conductivity) on the same particles with seeded velocities (sigma 0.1, so that the viscosity
@@ -516,6 +592,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the periodic-gravity and individual-step blocks")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--leaf", type=int, default=0, help="fixed leaf size (skips the autotune)")
     ap.add_argument("--ref-budget", type=float, default=20.0)
@@ -672,6 +749,7 @@ def main():
     accuracy = None
     ostate = None
     diss_block = None
+    extras = None
     if not args.no_forms:
         g_main = gpu_check_step(E, ctx, ds, offsets)
         rates, results = other_forms(torch, dev, stream, E, DeviceSet, w, max(2, min(args.steps, 5)), prec,
@@ -701,6 +779,10 @@ def main():
         if w.params.sph and w.n_gas > 0 and offsets is None and rank == 0 and world == 1:
             diss_block = dissipation_form(torch, dev, stream, E, DeviceSet, w, max(2, min(args.steps, 5)),
                                           int(ds.params.leaf_size), ostate)
+    if not args.no_extras and rank == 0 and world == 1 and offsets is None and args.kdk_steps == 0:
+        # periodic gravity (Sect. 4.3) and individual time steps (Sect. 4.2.1) at 2^20 particles
+        extras = {"ewald": ewald_block(torch, dev, stream, E, DeviceSet, 1 << 20, 3),
+                  "individual_steps": bins_block(torch, dev, stream, E, DeviceSet, 1 << 20)}
 
     # ---- roofline of the dominant kernel (the force walk) ----
     far, pp, sph, soft = float(cnt[0]), float(cnt[1]), float(cnt[2]), float(cnt[8])
@@ -757,6 +839,7 @@ def main():
                 "forms_particles_per_s": forms,
                 "forms_accuracy": accuracy,
                 "dissipation_variants": diss_block,
+                "periodic_and_individual_steps": extras,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": None}
         lps = launches_per_step(w)

@@ -108,8 +108,9 @@ typedef struct {
                                   correction, tabulated on a 65^3 octant grid and interpolated
                                   trilinearly, for every pair and every far node's monopole; the
                                   potential includes the zero-mean periodic term and the particle's
-                                  own replicas; a node is taken at one image only if its box lies
-                                  inside the cube of side L around the particle */
+                                  own replicas; a node is taken at the nearest image of its centre
+                                  of mass (direct + correction is periodic: any image serves), and
+                                  nodes of side above L/8 are opened; not with evol_step_batched */
     float periodic_lo[3], periodic_hi[3];
     int precision;             /* EVOL_FP32_PLAIN or EVOL_FP32_MIXED */
     int leaf_size;             /* a cube is split while it holds more than leaf_size particles

@@ -719,6 +719,7 @@ int orc_divv(const orc_tree *t, int mode, const double *L, const double *nsum, c
 /* ------------------------------------------------------------------------------------ */
 
 #define ORC_EWALD_N 64           /* table intervals per axis over the octant [0, L/2] */
+#define ORC_EWALD_LMAX 0.125    /* nodes of side above this fraction of L are opened */
 
 /* Ewald correction for a unit mass in a periodic cube of side L (Sect. 4.3, the series of
  * Hernquist et al. 1991 and Springel 2001 as printed), x = r_i - r_j (nearest image):
@@ -1087,18 +1088,14 @@ static int orc_accept(const orc_tree *t, const orc_params *pr, const orc_period 
         double ropen = (pr->theta > 0) ? t->l[id] / pr->theta + t->delta[id] : INFINITY;
         orc_margin(res, d, ropen);
         far = far && (d > ropen);
-        if (pr->ewald_L > 0) {
-            /* periodic gravity: the node is taken whole at one image only if its particle box
-             * lies inside the cube of side L centred on the particle (every particle of the node
-             * then has its nearest image in that box): |r_i - box centre|_a + half width_a < L/2 */
-            for (int a = 0; a < 3; ++a) {
-                double bc = 0.5 * (t->bmin[3 * id + a] + t->bmax[3 * id + a]);
-                double bw = 0.5 * (t->bmax[3 * id + a] - t->bmin[3 * id + a]);
-                double e = fabs(orc_wrap(pp, a, p[a] - bc)) + bw;
-                orc_margin(res, e, 0.5 * pr->ewald_L);
-                far = far && (e < 0.5 * pr->ewald_L);
-            }
-        }
+        /* Periodic gravity: the node is taken at the nearest image of its centre of mass, whatever
+         * images its particles' own nearest ones are: the direct force of the node there plus the
+         * correction of its replicas is the full periodic force of its mass, and that force is
+         * periodic, so any one image serves.  The correction is taken for the node's mass at the
+         * centre of mass; its error grows as (l/L)^2.  Reading: nodes of side l > L/8 are opened
+         * (the paper states no rule; with it the tree error at theta = 0.5 stays near the
+         * non-periodic one). */
+        if (pr->ewald_L > 0) far = far && (t->l[id] <= ORC_EWALD_LMAX * pr->ewald_L);
     }
     return far;
 }

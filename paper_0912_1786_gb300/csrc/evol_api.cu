@@ -461,6 +461,7 @@ int evol_step_batched(evol_ctx *c, const int64_t *sys_offsets, int nsys, evol_pa
     int rc = check_args(c, p, prm);
     if (rc) return rc;
     if (!sys_offsets || nsys < 1 || nsys > c->nsys_cap) return EVOL_EINVAL;
+    if (prm->gravity && prm->periodic_mask) return EVOL_EINVAL;     // periodic gravity: one system
     if (sys_offsets[0] != 0 || sys_offsets[nsys] != p->n) return EVOL_EINVAL;
     for (int k = 0; k < nsys; ++k)
         if (sys_offsets[k + 1] < sys_offsets[k]) return EVOL_EINVAL;

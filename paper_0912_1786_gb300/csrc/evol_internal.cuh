@@ -253,28 +253,6 @@ __device__ __forceinline__ float evol_wrap(float d, float len, int periodic)
 #define EVOL_EWALD_N 64
 #define EVOL_EWALD_M (EVOL_EWALD_N + 1)
 
-// Trilinear interpolation for a nearest-image offset (dx, dy, dz); sc = 2 N / L.  Returns f (odd in
-// its own coordinate, even in the others) and g, for L = 1: the caller scales f by 1/L^2, g by 1/L.
-__device__ __forceinline__ float4 evol_ewald_lookup(const float4 *__restrict__ tab, float dx, float dy, float dz,
-                                                    float sc)
-{
-    const float nm1 = (float)(EVOL_EWALD_N - 1);
-    const float ux = fabsf(dx) * sc, uy = fabsf(dy) * sc, uz = fabsf(dz) * sc;
-    const int i = (int)fminf(floorf(ux), nm1), j = (int)fminf(floorf(uy), nm1), k = (int)fminf(floorf(uz), nm1);
-    const float tx = ux - (float)i, ty = uy - (float)j, tz = uz - (float)k;
-    const int M = EVOL_EWALD_M;
-    const float4 *b = tab + ((i * M + j) * M + k);
-    const float4 c000 = b[0], c001 = b[1], c010 = b[M], c011 = b[M + 1];
-    const float4 c100 = b[M * M], c101 = b[M * M + 1], c110 = b[M * M + M], c111 = b[M * M + M + 1];
-    auto lerp4 = [](float4 a, float4 c, float t) {
-        return make_float4(fmaf(t, c.x - a.x, a.x), fmaf(t, c.y - a.y, a.y), fmaf(t, c.z - a.z, a.z),
-                           fmaf(t, c.w - a.w, a.w));
-    };
-    const float4 v = lerp4(lerp4(lerp4(c000, c001, tz), lerp4(c010, c011, tz), ty),
-                           lerp4(lerp4(c100, c101, tz), lerp4(c110, c111, tz), ty), tx);
-    return make_float4(dx < 0.f ? -v.x : v.x, dy < 0.f ? -v.y : v.y, dz < 0.f ? -v.z : v.z, v.w);
-}
-
 // Walk parameters passed by value to kernels.
 struct evol_kparams {
     float theta, G, gamma, alpha, beta;

@@ -159,6 +159,36 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
     return r;
 }
 
+// Periodic gravity: trilinear interpolation in the Ewald table (Sect. 4.3).  f is odd in its own
+// coordinate and even in the others, g is even, so the table holds the octant [0, L/2]^3 only; the
+// four components are interpolated as two packed pairs, (f_x, f_y) and (f_z, g), and the caller
+// applies the octant signs.  sc = 2 N / L.
+struct Ew2 {
+    f32x2 xy, zw;
+};
+__device__ __forceinline__ Ew2 ewald_lookup2(const float4 *__restrict__ tab, float dx, float dy, float dz, float sc)
+{
+    const int M = EVOL_EWALD_M;
+    const float nm1 = (float)(EVOL_EWALD_N - 1);
+    const float ux = fabsf(dx) * sc, uy = fabsf(dy) * sc, uz = fabsf(dz) * sc;
+    // the cell, clamped in float before the conversion (fminf returns nm1 for a NaN offset), so that
+    // every index stays inside the table; truncation is the floor for the non-negative values
+    const int i = __float2int_rz(fminf(ux, nm1)), j = __float2int_rz(fminf(uy, nm1)), k = __float2int_rz(fminf(uz, nm1));
+    const float tx = ux - (float)i, ty = uy - (float)j, tz = uz - (float)k;
+    const ulonglong2 *b = reinterpret_cast<const ulonglong2 *>(tab + ((i * M + j) * M + k));
+    const ulonglong2 c000 = b[0], c001 = b[1], c010 = b[M], c011 = b[M + 1];
+    const ulonglong2 c100 = b[M * M], c101 = b[M * M + 1], c110 = b[M * M + M], c111 = b[M * M + M + 1];
+    const f32x2 TZ = pk2(tz, tz), TY = pk2(ty, ty), TX = pk2(tx, tx);
+    auto L = [](f32x2 a, f32x2 c, f32x2 t) { return fma2(t, sub2(c, a), a); };
+    const f32x2 a0 = L(c000.x, c001.x, TZ), b0 = L(c000.y, c001.y, TZ);
+    const f32x2 a1 = L(c010.x, c011.x, TZ), b1 = L(c010.y, c011.y, TZ);
+    const f32x2 a2 = L(c100.x, c101.x, TZ), b2 = L(c100.y, c101.y, TZ);
+    const f32x2 a3 = L(c110.x, c111.x, TZ), b3 = L(c110.y, c111.y, TZ);
+    const f32x2 e0 = L(a0, a1, TY), g0 = L(b0, b1, TY), e1 = L(a2, a3, TY), g1 = L(b2, b3, TY);
+    return Ew2{L(e0, e1, TX), L(g0, g1, TX)};
+}
+
+
 // Per-particle sums of one flush (a block of at most FARCAP far nodes or NEARCAP near entries).
 struct Acc {
     float ax = 0.f, ay = 0.f, az = 0.f, pot = 0.f;      // gravity (without G)
@@ -214,10 +244,11 @@ struct DissSmem<false> {
 
 // Register budgets, chosen so that no variant spills to local memory: the plain gravity + SPH walk
 // (the production form) and the SPH-only walk fit five blocks per SM (at most 102 registers), the
-// mixed gravity + SPH walk and the walks with the dissipation variants (DISS) four (128
-// registers), the gravity-only walks and the mixed DISS walks three; the check-mode variants one.
+// mixed gravity + SPH walk, the walks with the dissipation variants (DISS) and the plain
+// gravity-only periodic (EWALD) walk four (128 registers), the other gravity-only, periodic and
+// mixed DISS walks three; the check-mode variants one.
 template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS, bool EWALD>
-__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SPH) || (MIXED && DISS)) ? 3 : ((GRAV && MIXED) || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIXED) ? 4 : (EWALD || (GRAV && !SPH) || (MIXED && DISS)) ? 3 : ((GRAV && MIXED) || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
     __shared__ DissSmem<DISS> ds;
@@ -231,7 +262,8 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
     // tabulated correction of the replicas, Sect. 4.3); pmg: the periodic axes of the gravity tests
     const int pm = ((SPH && !GRAV) || EWALD) ? kp.periodic_mask : 0;
     const int pmg = EWALD ? kp.periodic_mask : 0;
-    const float halfL = 0.5f * kp.ewald_L, iL = EWALD ? 1.f / kp.ewald_L : 0.f;
+    const float iL = EWALD ? 1.f / kp.ewald_L : 0.f;
+    const float side0 = EWALD ? d.fcube[3] : 0.f;     // root cube side (periodic gravity: one system)
     const float plen0 = kp.plen[0], plen1 = kp.plen[1], plen2 = kp.plen[2];
     const float inv_pi = 1.f / EVOL_PI_F;
 
@@ -315,7 +347,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
             const f32x2 PX = pk2(pi.x, pi.x), PY = pk2(pi.y, pi.y), PZ = pk2(pi.z, pi.z);
             const f32x2 KM25 = pk2(-2.5f, -2.5f), KM05 = pk2(-0.5f, -0.5f);
             f32x2 fax = 0ull, fay = 0ull, faz = 0ull, fpot = 0ull;      // +0.0f in both halves
-            float4 ew = make_float4(0.f, 0.f, 0.f, 0.f);                // Ewald corrections (x M)
+            f32x2 ewxy = 0ull, ewzw = 0ull;                             // Ewald corrections (x M)
             for (int e = 0; e < padded; e += TRIP) {
 #pragma unroll
                 for (int u = 0; u < EVOL_FAR_UNROLL; ++u) {
@@ -332,16 +364,19 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
                         dy = pk2(evol_wrap(lo2(dy), plen1, pmg & 2), evol_wrap(hi2(dy), plen1, pmg & 2));
                         dz = pk2(evol_wrap(lo2(dz), plen2, pmg & 4), evol_wrap(hi2(dz), plen2, pmg & 4));
                         if ((mk.x >> lane) & 1u) {
-                            const float4 c = evol_ewald_lookup(kp.ewald_tab, lo2(dx), lo2(dy), lo2(dz), kp.ewald_sc);
+                            const float ex = lo2(dx), ey = lo2(dy), ez = lo2(dz);
+                            const Ew2 c = ewald_lookup2(kp.ewald_tab, ex, ey, ez, kp.ewald_sc);
+                            // octant signs folded into the mass: f_a odd in its own coordinate
                             const float Mn = -lo2(v1.y);
-                            ew.x = fmaf(Mn, c.x, ew.x); ew.y = fmaf(Mn, c.y, ew.y);
-                            ew.z = fmaf(Mn, c.z, ew.z); ew.w = fmaf(Mn, c.w, ew.w);
+                            ewxy = fma2(pk2(ex < 0.f ? -Mn : Mn, ey < 0.f ? -Mn : Mn), c.xy, ewxy);
+                            ewzw = fma2(pk2(ez < 0.f ? -Mn : Mn, Mn), c.zw, ewzw);
                         }
                         if ((mk.y >> lane) & 1u) {
-                            const float4 c = evol_ewald_lookup(kp.ewald_tab, hi2(dx), hi2(dy), hi2(dz), kp.ewald_sc);
+                            const float ex = hi2(dx), ey = hi2(dy), ez = hi2(dz);
+                            const Ew2 c = ewald_lookup2(kp.ewald_tab, ex, ey, ez, kp.ewald_sc);
                             const float Mn = -hi2(v1.y);
-                            ew.x = fmaf(Mn, c.x, ew.x); ew.y = fmaf(Mn, c.y, ew.y);
-                            ew.z = fmaf(Mn, c.z, ew.z); ew.w = fmaf(Mn, c.w, ew.w);
+                            ewxy = fma2(pk2(ex < 0.f ? -Mn : Mn, ey < 0.f ? -Mn : Mn), c.xy, ewxy);
+                            ewzw = fma2(pk2(ez < 0.f ? -Mn : Mn, Mn), c.zw, ewzw);
                         }
                     }
                     const f32x2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
@@ -368,10 +403,10 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
             acc.pot += lo2(fpot) + hi2(fpot);
             if constexpr (EWALD) {
                 // the table is for a cube of side 1: f scales as 1/L^2, g as 1/L
-                acc.ax += ew.x * iL * iL;
-                acc.ay += ew.y * iL * iL;
-                acc.az += ew.z * iL * iL;
-                acc.pot += ew.w * iL;
+                acc.ax += lo2(ewxy) * iL * iL;
+                acc.ay += hi2(ewxy) * iL * iL;
+                acc.az += lo2(ewzw) * iL * iL;
+                acc.pot += hi2(ewzw) * iL;
             }
             fold();
             nfar = 0;
@@ -418,7 +453,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
             {
                 const f32x2 PX = pk2(pi.x, pi.x), PY = pk2(pi.y, pi.y), PZ = pk2(pi.z, pi.z);
                 f32x2 nax = 0ull, nay = 0ull, naz = 0ull, npot = 0ull;
-                float4 ewn = make_float4(0.f, 0.f, 0.f, 0.f);
+                f32x2 ewnxy = 0ull, ewnzw = 0ull;
                 for (int q = 0; q < (nnear + 1) >> 1; ++q) {
                     const uint2 mk = *reinterpret_cast<const uint2 *>(&sm.near_mask[w][2 * q]);
                     const ulonglong2 *F = reinterpret_cast<const ulonglong2 *>(sm.npair[w][q]);
@@ -435,16 +470,18 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
                     if constexpr (EWALD) {
                         // every pair, softened or not: the replicas of j beyond its nearest image
                         if (mine_a) {
-                            const float4 c = evol_ewald_lookup(kp.ewald_tab, lo2(dx), lo2(dy), lo2(dz), kp.ewald_sc);
+                            const float ex = lo2(dx), ey = lo2(dy), ez = lo2(dz);
+                            const Ew2 c = ewald_lookup2(kp.ewald_tab, ex, ey, ez, kp.ewald_sc);
                             const float mj = lo2(v1.y);
-                            ewn.x = fmaf(mj, c.x, ewn.x); ewn.y = fmaf(mj, c.y, ewn.y);
-                            ewn.z = fmaf(mj, c.z, ewn.z); ewn.w = fmaf(mj, c.w, ewn.w);
+                            ewnxy = fma2(pk2(ex < 0.f ? -mj : mj, ey < 0.f ? -mj : mj), c.xy, ewnxy);
+                            ewnzw = fma2(pk2(ez < 0.f ? -mj : mj, mj), c.zw, ewnzw);
                         }
                         if (mine_b) {
-                            const float4 c = evol_ewald_lookup(kp.ewald_tab, hi2(dx), hi2(dy), hi2(dz), kp.ewald_sc);
+                            const float ex = hi2(dx), ey = hi2(dy), ez = hi2(dz);
+                            const Ew2 c = ewald_lookup2(kp.ewald_tab, ex, ey, ez, kp.ewald_sc);
                             const float mj = hi2(v1.y);
-                            ewn.x = fmaf(mj, c.x, ewn.x); ewn.y = fmaf(mj, c.y, ewn.y);
-                            ewn.z = fmaf(mj, c.z, ewn.z); ewn.w = fmaf(mj, c.w, ewn.w);
+                            ewnxy = fma2(pk2(ex < 0.f ? -mj : mj, ey < 0.f ? -mj : mj), c.xy, ewnxy);
+                            ewnzw = fma2(pk2(ez < 0.f ? -mj : mj, mj), c.zw, ewnzw);
                         }
                     }
                     if (CHECK) cpp += (mine_a ? 1 : 0) + (mine_b ? 1 : 0);
@@ -477,10 +514,10 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
                     acc.pot -= lo2(npot) + hi2(npot);
                 }
                 if constexpr (EWALD) {
-                    acc.ax += ewn.x * iL * iL;
-                    acc.ay += ewn.y * iL * iL;
-                    acc.az += ewn.z * iL * iL;
-                    acc.pot += ewn.w * iL;
+                    acc.ax += lo2(ewnxy) * iL * iL;
+                    acc.ay += hi2(ewnxy) * iL * iL;
+                    acc.az += lo2(ewnzw) * iL * iL;
+                    acc.pot += hi2(ewnzw) * iL;
                 }
             }
             // Pass 2: the marked pairs of each lane.  Every lane of the warp runs this loop; lanes past
@@ -709,11 +746,11 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
                 }
                 bool acc_all = bnear2 > rup * rup * (1.f + TAU);
                 bool open_all = bfar2 < rlo * rlo * (1.f - TAU);
-                if (EWALD) {
-                    // a node is taken whole at one image only inside the cube of side L around
-                    // each particle: |r_i - box centre| + half width < L/2 on every axis
-                    acc_all = acc_all && dx + gwx + C.x < halfL * (1.f - TAU) && dy + gwy + C.y < halfL * (1.f - TAU) &&
-                              dz + gwz + C.z < halfL * (1.f - TAU);
+                if (EWALD && !(ldexpf(side0, -(I.x & 0xff)) <= 0.125f * kp.ewald_L)) {
+                    // periodic gravity: nodes of side above L/8 are always opened (their replicas'
+                    // correction is taken as a monopole, whose error grows as (l/L)^2)
+                    acc_all = false;
+                    open_all = true;
                 }
                 if (GRAV) {
                     const float ax = fabsf(evol_wrap(A.x - gcx, plen0, pmg & 1)), ay = fabsf(evol_wrap(A.y - gcy, plen1, pmg & 2)),
@@ -759,7 +796,6 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
                     float R = GRAV ? fmaxf(two_eps_i, C.w) : 0.f;
                     if (SPH && gas_i && B.w >= 0.f) R = fmaxf(R, fmaxf(two_h_i, B.w));
                     far = bd2 > R * R;
-                    if (EWALD) far = far && qx + C.x < halfL && qy + C.y < halfL && qz + C.z < halfL;
                     if (GRAV && far) {
                         const float4 A = sm.bA[w][kk];
                         const float dx = evol_wrap(pi.x - A.x, plen0, pmg & 1), dy = evol_wrap(pi.y - A.y, plen1, pmg & 2),

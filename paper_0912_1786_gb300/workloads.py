@@ -240,6 +240,36 @@ def ensemble(nsys: int = 64, seed: int = 5, log2_min: float = 10.0, log2_max: fl
     return w
 
 
+def periodic_box(n: int = 1 << 20, seed: int = 6, L: float = 1.0, n_gas: int = 0, sigma_v: float = 0.0,
+                 params: Params | None = None) -> Workload:
+    """Particles in the periodic cube [0, L)^3 (Sect. 4.3): half uniform, half in three Gaussian clumps
+    (dispersion 0.05 L, wrapped), equal masses summing to 1, optional gas (the first n_gas) with
+    u = 0.5 and isotropic velocities of dispersion sigma_v."""
+    rng = np.random.default_rng(seed)
+    P = rng.uniform(0.0, L, (n, 3))
+    k = n // 2
+    centres = rng.uniform(0.1, 0.9, (3, 3)) * L
+    P[:k] = np.mod(centres[rng.integers(0, 3, k)] + rng.normal(0, 0.05 * L, (k, 3)), L)
+    v = rng.normal(0, sigma_v, (n, 3)) if sigma_v > 0 else np.zeros((n, 3))
+    p = params or Params(theta=0.5, gravity=1, sph=1 if n_gas else 0, adaptive_softening=1, n_nei_grav=32.0,
+                         n_nei_sph=40.0, leaf_size=8, periodic_mask=7, periodic_lo=(0.0, 0.0, 0.0),
+                         periodic_hi=(L, L, L))
+    guess = _length_guess(np.full(n, n / L ** 3), 32.0)
+    x, y, z, vx, vy, vz, m, uu, h, eps = _f32(P[:, 0], P[:, 1], P[:, 2], v[:, 0], v[:, 1], v[:, 2],
+                                              np.full(n, 1.0 / n), np.full(n, 0.5), guess, guess)
+    return Workload("periodic_box", x, y, z, vx, vy, vz, m, uu, h, eps, n_gas=n_gas, params=p)
+
+
+def hot_core(w: Workload, factor: float = 30.0, radius: float = 0.2) -> Workload:
+    """A copy of a gas sphere whose internal energy is raised near the centre,
+    u (1 + factor exp(-(r/radius)^2)): a wide spread of Courant steps (individual time steps)."""
+    import copy
+    out = copy.copy(w)
+    r = np.sqrt(w.x.astype(np.float64) ** 2 + w.y.astype(np.float64) ** 2 + w.z.astype(np.float64) ** 2)
+    out.u = np.ascontiguousarray(w.u * (1.0 + factor * np.exp(-(r / radius) ** 2)), F32)
+    return out
+
+
 def with_dissipation(w: Workload, seed: int = 7, alpha=(0.05, 1.5), alpha_u=(0.0, 1.0), u_spread: float = 0.5,
                      sigma_v: float = 0.0, **params) -> Workload:
     """A copy of `w` with the per-particle inputs of the dissipation variants: alpha_i and alpha^u_i
