@@ -394,7 +394,10 @@ __device__ int gather_from_list(const evol_dev &d, const evol_kparams &kp, const
     return cnt;
 }
 
-template <int MODE>
+// Variants: STD the standard scheme (mode 0), ACT the active list of individual time steps, CURL
+// |curl v| in the last evaluation (mode 0); each a template parameter, so that the default solve's
+// code carries none of them.
+template <int MODE, bool STD, bool ACT, bool CURL>
 __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ LenSmem sm;
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
     const int stack_cap = 2 * kp.stack_cap;
     const int n = kp.n;
     // individual time steps: items of SUB consecutive entries of the active list
-    const int nlist = kp.active ? d.acts[n] : n;
+    const int nlist = ACT ? d.acts[n] : n;
     const int ngroups = (nlist + SUB - 1) / SUB;   // the queue hands out SUB particles at a time
     const float eta = MODE == 0 ? kp.eta_h : kp.eta_e;
     const float eta3 = eta * eta * eta;
@@ -422,7 +425,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
         if (g >= ngroups) break;
         const int e = g * SUB + lane;                 // lanes 0 .. SUB-1 hold the particles
         const bool valid = lane < SUB && e < nlist;
-        const int s = kp.active ? (valid ? d.act[e] : 0) : e;
+        const int s = ACT ? (valid ? d.act[e] : 0) : e;
         const float4 pi4 = valid ? d.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
         const bool gas_i = valid && d.orig[s] < kp.n_gas;
         const bool act = MODE == 0 ? gas_i : valid;
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
             auto give_up = [&](int code) {
                 if (lane == 0) evol_flag(d.err, code);
                 if (lane == t) {
-                    const int si = s;                  // lane t holds particle t
+                    const int si = ACT ? s : g * SUB + t;   // lane t holds particle t
                     const float qnan = __int_as_float(0x7fc00000);
                     if (MODE == 0) {
                         d.len_h[si] = L;
@@ -554,7 +557,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         continue;
                     }
                 }
-                if (MODE == 0 && kp.standard && status == ST_ACTIVE) {
+                if (MODE == 0 && STD && status == ST_ACTIVE) {
                     // standard scheme: widen the ball until it holds N + 1 gas particles, then h
                     // from the N-th and (N+1)-th distances (every particle closer than the
                     // (N+1)-th is in the list: the list holds the whole ball)
@@ -590,7 +593,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                 } else {
                     // the neighbours' masses (and, for the continuity equation, positions and
                     // velocities) are read from the sorted particle state
-                    const int st = __shfl_sync(0xffffffffu, s, t);
+                    const int st = ACT ? __shfl_sync(0xffffffffu, s, t) : g * SUB + t;
                     const float4 vi = kp.want_divv ? d.vel[st] : make_float4(0.f, 0.f, 0.f, 0.f);
                     for (int e = lane; e < cnt; e += 32) {
                         const float2 rj = nb[e];
@@ -614,7 +617,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                             const float dy = evol_wrap(py - pj.y, kp.plen[1], kp.periodic_mask & 2);
                             const float dz = evol_wrap(pz - pj.z, kp.plen[2], kp.periodic_mask & 4);
                             S5 += ((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz) / rj.x * dw;
-                            if (MODE == 0 && kp.want_curl) {
+                            if (MODE == 0 && CURL) {
                                 // (v_i - v_j) x (r_i - r_j) / r  w'(u)
                                 const float ux = vi.x - vj.x, uy = vi.y - vj.y, uz = vi.z - vj.z;
                                 const float q = dw / rj.x;
@@ -633,7 +636,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         S3 += __shfl_xor_sync(0xffffffffu, S3, o);
                         if (MODE == 0) S4 += __shfl_xor_sync(0xffffffffu, S4, o);
                         if (kp.want_divv) S5 += __shfl_xor_sync(0xffffffffu, S5, o);
-                        if (MODE == 0 && kp.want_curl) {
+                        if (MODE == 0 && CURL) {
                             S6x += __shfl_xor_sync(0xffffffffu, S6x, o);
                             S6y += __shfl_xor_sync(0xffffffffu, S6y, o);
                             S6z += __shfl_xor_sync(0xffffffffu, S6z, o);
@@ -647,7 +650,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                     S3 = __shfl_sync(0xffffffffu, S3, 0);
                     if (MODE == 0) S4 = __shfl_sync(0xffffffffu, S4, 0);
                     if (kp.want_divv) S5 = __shfl_sync(0xffffffffu, S5, 0);
-                    if (MODE == 0 && kp.want_curl) {
+                    if (MODE == 0 && CURL) {
                         S6x = __shfl_sync(0xffffffffu, S6x, 0);
                         S6y = __shfl_sync(0xffffffffu, S6y, 0);
                         S6z = __shfl_sync(0xffffffffu, S6z, 0);
@@ -656,14 +659,14 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                 const float Smw = S3, Smuw = S4;
                 if (status == ST_LAST) {
                     if (lane == t) {
-                        const int si = s;                  // lane t holds particle t
+                        const int si = ACT ? s : g * SUB + t;   // lane t holds particle t
                         const float nsum = Sw * inv_pi * Linv * Linv * Linv;
                         if (MODE == 0) {
                             d.len_h[si] = L;
                             d.nh[si] = nsum;
                             d.rho[si] = Smw * inv_pi * Linv * Linv * Linv;
-                            d.omega[si] = kp.standard ? 1.f : -Suw / (3.f * Sw);
-                            d.zeta[si] = kp.standard ? 0.f : (3.f * Smw + Smuw) / (3.f * Sw);
+                            d.omega[si] = STD ? 1.f : -Suw / (3.f * Sw);
+                            d.zeta[si] = STD ? 0.f : (3.f * Smw + Smuw) / (3.f * Sw);
                         } else {
                             d.len_eps[si] = L;
                             d.neps[si] = nsum;
@@ -673,11 +676,11 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         // div v = -1/(n C) sum_j (v_i - v_j).grad_i W = 3 S5 / (L Suw), C = Upsilon
                         // or Omega* = -Suw/(3 Sw), n = Sw/(pi L^3), grad W = r_ij/r w'(u)/(pi L^4)
                         // (the standard scheme takes C = 1: div v = -S5 / (L Sw))
-                        const bool stdc = MODE == 0 && kp.standard;
+                        const bool stdc = MODE == 0 && STD;
                         if (kp.want_divv)
                             (MODE == 0 ? d.divv_h : d.divv_e)[si] = stdc ? -S5 / (L * Sw) : 3.f * S5 / (L * Suw);
                         // |curl v| = |1/(n C) sum_j (v_i - v_j) x grad_i W| = 3 |S6| / (L |Suw|)
-                        if (MODE == 0 && kp.want_curl) {
+                        if (MODE == 0 && CURL) {
                             const float s6 = sqrtf(S6x * S6x + S6y * S6y + S6z * S6z);
                             d.curlv_h[si] = stdc ? s6 / (L * Sw) : 3.f * s6 / (L * fabsf(Suw));
                         }
@@ -749,10 +752,20 @@ int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params 
     unsigned long long *q = c->d.counters + (mode == 0 ? 5 : 6);
     cudaMemsetAsync(q, 0, sizeof(unsigned long long), c->stream);
     int blocks = (int)(c->cand_slots / LW_WARPS);
-    if (mode == 0)
-        k_lengths<0><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q);
-    else
-        k_lengths<1><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q);
+    // variant = standard scheme | active list << 1 | curl << 2
+    const int var = (kp.standard ? 1 : 0) | (kp.active ? 2 : 0) | (kp.want_curl ? 4 : 0);
+    switch (mode == 0 ? var : 8 + (kp.active ? 1 : 0)) {
+    case 0: k_lengths<0, false, false, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
+    case 1: k_lengths<0, true, false, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
+    case 2: k_lengths<0, false, true, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
+    case 3: k_lengths<0, true, true, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
+    case 4: k_lengths<0, false, false, true><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
+    case 5: k_lengths<0, true, false, true><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
+    case 6: k_lengths<0, false, true, true><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
+    case 7: k_lengths<0, true, true, true><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
+    case 8: k_lengths<1, false, false, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
+    default: k_lengths<1, false, true, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
+    }
     return evol_cuda_ok(cudaGetLastError());
 }
 
