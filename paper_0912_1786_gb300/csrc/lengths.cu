@@ -12,7 +12,7 @@
 // neighbours found are appended, as (distance, mass) pairs, to a shared-memory list.
 // On that list the particle solves
 //     F(L) = L^3 n(L) - eta^3 = 0,   n(L) = sum_j W(r_ij, L)  (self term included)
-// by Newton steps kept inside a bisection bracket, gathering again when 2L leaves the gathered
+// by Newton steps in L^3 kept inside a bisection bracket, gathering again when 2L leaves the gathered
 // radius.  F is non-decreasing in L, so the root is unique.  With w(u) = pi L^3 W the sums are
 // dimensionless:
 //     F = Sw/pi - eta^3,  F' = -Suw/(pi L),  Sw = sum w(u),  Suw = sum u w'(u).
@@ -43,7 +43,11 @@ constexpr int GCAP = 192;             // leaves in a group walk's list
 constexpr int MAX_ITERS = 60;
 constexpr int MAX_WALKS = 24;
 constexpr float SEARCH_MARGIN = 1.1f;
-constexpr float CONV_TOL = 1e-6f;     // relative step below which one last evaluation is taken
+// Relative step below which one last evaluation is taken: a Newton step that small leaves an
+// error of the order of its square (the iteration converges quadratically), far below FP32
+// resolution; a bisection step must be smaller, as it halves the error only.
+constexpr float NEWTON_TOL = 1e-4f;
+constexpr float CONV_TOL = 1e-6f;
 
 enum { ST_DONE = 0, ST_ACTIVE = 1, ST_LAST = 2 };
 
@@ -76,14 +80,14 @@ __device__ __forceinline__ float kth_distance(const float2 *nb, int cnt, int k, 
 // Particles of the listed leaves against the particle at (px, py, pz), 32 at a time across
 // leaves: those within R2 (gas only in mode 0) are appended to the neighbour list.  Returns the
 // new count (entries beyond PCAP are counted but not stored).
-template <int MODE>
+template <int MODE, bool PER>
 __device__ __forceinline__ int gather_listed(const evol_dev &d, const evol_kparams &kp, const int *hb, const int *hs,
                                              int nh, float2 *nb, int cnt, float px, float py, float pz, float R2,
                                              int lane)
 {
     const unsigned ltmask = (1u << lane) - 1u;
     const float p0 = kp.plen[0], p1 = kp.plen[1], p2 = kp.plen[2];
-    const int pm = kp.periodic_mask;
+    const int pm = PER ? kp.periodic_mask : 0;   // PER: periodic axes present
     const int total = hb[nh];
     constexpr int U = 1;              // chunks whose loads are issued together (more costs occupancy)
     // the listed leaf holding the chunk's first flattened index; leaves are never empty, so the
@@ -137,14 +141,14 @@ __device__ __forceinline__ int gather_listed(const evol_dev &d, const evol_kpara
 // particle box comes within the radius; the leaves reached are listed (HCAP at a time) and their
 // particles gathered into the neighbour list.  Returns the neighbour count, or -1 when the walk
 // had to stop (corrupt tree or stack overflow; the error word is set).
-template <int MODE>
+template <int MODE, bool PER>
 __device__ int gather_ball(const evol_dev &d, const evol_kparams &kp, int *hb, int *hs, float2 *nb, int lane,
                            int *stk, int stack_cap, long long pop_cap, int root, float px, float py, float pz,
                            float R2)
 {
     const unsigned ltmask = (1u << lane) - 1u;
     const float p0 = kp.plen[0], p1 = kp.plen[1], p2 = kp.plen[2];
-    const int pm = kp.periodic_mask;
+    const int pm = PER ? kp.periodic_mask : 0;   // PER: periodic axes present
     if (lane == 0) {
         stk[0] = root;
         hb[0] = 0;
@@ -184,7 +188,7 @@ __device__ int gather_ball(const evol_dev &d, const evol_kparams &kp, int *hb, i
         if (nl) {
             if (nh + nl > HCAP) {
                 __syncwarp();
-                cnt = gather_listed<MODE>(d, kp, hb, hs, nh, nb, cnt, px, py, pz, R2, lane);
+                cnt = gather_listed<MODE, PER>(d, kp, hb, hs, nh, nb, cnt, px, py, pz, R2, lane);
                 __syncwarp();
                 nh = 0;
             }
@@ -238,7 +242,7 @@ __device__ int gather_ball(const evol_dev &d, const evol_kparams &kp, int *hb, i
         top += total;
         __syncwarp();
     }
-    if (nh) cnt = gather_listed<MODE>(d, kp, hb, hs, nh, nb, cnt, px, py, pz, R2, lane);
+    if (nh) cnt = gather_listed<MODE, PER>(d, kp, hb, hs, nh, nb, cnt, px, py, pz, R2, lane);
     __syncwarp();
     return cnt;
 }
@@ -247,14 +251,14 @@ __device__ int gather_ball(const evol_dev &d, const evol_kparams &kp, int *hb, i
 // leaves only in mode 0), from one root per system present among the `seed` lanes.  The
 // leaves go to the group list; returns their number, GCAP + 1 when they do not fit, or -1 when
 // the walk had to stop (corrupt tree or stack overflow; the error word is set).
-template <int MODE>
+template <int MODE, bool PER>
 __device__ int collect_leaves(const evol_dev &d, const evol_kparams &kp, float4 *gc, float4 *gh, int2 *gr, int lane,
                               int *stk, int stack_cap, long long pop_cap, float cx, float cy, float cz, float hx,
                               float hy, float hz, float R2, int myroot, bool seed)
 {
     const unsigned ltmask = (1u << lane) - 1u;
     const float p0 = kp.plen[0], p1 = kp.plen[1], p2 = kp.plen[2];
-    const int pm = kp.periodic_mask;
+    const int pm = PER ? kp.periodic_mask : 0;   // PER: periodic axes present
     int top = 0;
     {
         const unsigned peers = __match_any_sync(0xffffffffu, seed ? myroot : -1);
@@ -340,14 +344,14 @@ __device__ int collect_leaves(const evol_dev &d, const evol_kparams &kp, float4 
 
 // A particle's gather from its group list: the listed leaves of its own system (particle range
 // inside [sbeg, send)) whose box comes within sqrt(R2) of (px, py, pz), then their particles.
-template <int MODE>
+template <int MODE, bool PER>
 __device__ int gather_from_list(const evol_dev &d, const evol_kparams &kp, const float4 *gc, const float4 *gh,
                                 const int2 *gr, int nleaf, int *hb, int *hs, float2 *nb, int lane, float px, float py,
                                 float pz, float R2, int sbeg, int send)
 {
     const unsigned ltmask = (1u << lane) - 1u;
     const float p0 = kp.plen[0], p1 = kp.plen[1], p2 = kp.plen[2];
-    const int pm = kp.periodic_mask;
+    const int pm = PER ? kp.periodic_mask : 0;   // PER: periodic axes present
     int cnt = 0, nh = 0;
     for (int base = 0; base < nleaf; base += 32) {
         const int l = base + lane;
@@ -366,7 +370,7 @@ __device__ int gather_from_list(const evol_dev &d, const evol_kparams &kp, const
         if (nl) {
             if (nh + nl > HCAP) {
                 __syncwarp();
-                cnt = gather_listed<MODE>(d, kp, hb, hs, nh, nb, cnt, px, py, pz, R2, lane);
+                cnt = gather_listed<MODE, PER>(d, kp, hb, hs, nh, nb, cnt, px, py, pz, R2, lane);
                 __syncwarp();
                 nh = 0;
             }
@@ -389,15 +393,15 @@ __device__ int gather_from_list(const evol_dev &d, const evol_kparams &kp, const
             __syncwarp();
         }
     }
-    if (nh) cnt = gather_listed<MODE>(d, kp, hb, hs, nh, nb, cnt, px, py, pz, R2, lane);
+    if (nh) cnt = gather_listed<MODE, PER>(d, kp, hb, hs, nh, nb, cnt, px, py, pz, R2, lane);
     __syncwarp();
     return cnt;
 }
 
 // Variants: STD the standard scheme (mode 0), ACT the active list of individual time steps, CURL
-// |curl v| in the last evaluation (mode 0); each a template parameter, so that the default solve's
-// code carries none of them.
-template <int MODE, bool STD, bool ACT, bool CURL>
+// |curl v| in the last evaluation (mode 0), PER periodic axes; each a template parameter, so that
+// the default solve's code carries none of them.
+template <int MODE, bool STD, bool ACT, bool CURL, bool PER>
 __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ LenSmem sm;
@@ -466,7 +470,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
               gz1 = fmaxf(gz1, __shfl_xor_sync(0xffffffffu, gz1, o));
               Rg = fmaxf(Rg, __shfl_xor_sync(0xffffffffu, Rg, o));
           }
-          const int nleaf = collect_leaves<MODE>(d, kp, sm.gc[w], sm.gh[w], sm.gr[w], lane, stk, stack_cap, pop_cap,
+          const int nleaf = collect_leaves<MODE, PER>(d, kp, sm.gc[w], sm.gh[w], sm.gr[w], lane, stk, stack_cap, pop_cap,
                                                  0.5f * (gx0 + gx1), 0.5f * (gy0 + gy1), 0.5f * (gz0 + gz1),
                                                  0.5f * (gx1 - gx0), 0.5f * (gy1 - gy0), 0.5f * (gz1 - gz0), Rg * Rg,
                                                  root, insub);
@@ -528,11 +532,11 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                     __syncwarp();
                     if (glist && Rc <= Rg) {
                         if (lane == 0) ++lc[0];
-                        cnt = gather_from_list<MODE>(d, kp, sm.gc[w], sm.gh[w], sm.gr[w], nleaf, sm.hb[w], sm.hs[w], nb,
+                        cnt = gather_from_list<MODE, PER>(d, kp, sm.gc[w], sm.gh[w], sm.gr[w], nleaf, sm.hb[w], sm.hs[w], nb,
                                                      lane, px, py, pz, R2, sb, se);
                     } else {
                         if (lane == 0) ++lc[1];
-                        cnt = gather_ball<MODE>(d, kp, sm.hb[w], sm.hs[w], nb, lane, stk, stack_cap, pop_cap, rt, px,
+                        cnt = gather_ball<MODE, PER>(d, kp, sm.hb[w], sm.hs[w], nb, lane, stk, stack_cap, pop_cap, rt, px,
                                                 py, pz, R2);
                     }
                     if (cnt < 0) {
@@ -554,6 +558,7 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         }
                         L = Ln;
                         stale = true;
+                        status = ST_ACTIVE;                    // a converged length is solved again
                         continue;
                     }
                 }
@@ -613,9 +618,10 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                         if (kp.want_divv && rj.x > 0.f) {
                             // (v_i - v_j).(r_i - r_j) / r  w'(u)  (Sect. 2.1, continuity equation)
                             const float4 vj = d.vel[j];
-                            const float dx = evol_wrap(px - pj.x, kp.plen[0], kp.periodic_mask & 1);
-                            const float dy = evol_wrap(py - pj.y, kp.plen[1], kp.periodic_mask & 2);
-                            const float dz = evol_wrap(pz - pj.z, kp.plen[2], kp.periodic_mask & 4);
+                            const int pmk = PER ? kp.periodic_mask : 0;
+                            const float dx = evol_wrap(px - pj.x, kp.plen[0], pmk & 1);
+                            const float dy = evol_wrap(py - pj.y, kp.plen[1], pmk & 2);
+                            const float dz = evol_wrap(pz - pj.z, kp.plen[2], pmk & 4);
                             S5 += ((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz) / rj.x * dw;
                             if (MODE == 0 && CURL) {
                                 // (v_i - v_j) x (r_i - r_j) / r  w'(u)
@@ -692,19 +698,36 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
                     if (F < 0.f) lo = L;
                     if (F > 0.f) hi = L;
                     float Ln;
+                    bool newton = false;
                     if (F == 0.f) {
                         Ln = L;
                     } else {
-                        // Newton step, F' = -Suw/(pi L); bisection where it leaves the bracket
-                        const float Fp = -Suw * inv_pi * Linv;
-                        Ln = Fp > 0.f ? L - F / Fp : (hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L);
-                        // below the root with no upper bracket yet, F' counts only the few neighbours
-                        // inside the kernel and the step can overshoot by orders of magnitude: grow by
-                        // at most a factor 2 until the root is bracketed
-                        if (hi == INFINITY) Ln = fminf(Ln, 2.f * L);
-                        if (!(Ln > lo && Ln < hi)) Ln = hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L;
+                        // Newton step in y = L^3, on which F = n y - eta^3 depends almost linearly
+                        // (n varies slowly with L): dF/dy = F'/(3 L^2) with F' = -Suw/(pi L), so
+                        // y' = y (1 + 3 pi F / Suw); bisection where it leaves the bracket
+                        const float q = 1.f + 3.f * EVOL_PI_F * F / Suw;
+                        newton = Suw < 0.f && q > 0.f;
+                        Ln = newton ? L * cbrtf(q) : (hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L);
+                        if (newton && fabsf(Ln - L) <= NEWTON_TOL * L) {
+                            // converged: a step this small goes towards the root (F' > 0), and one
+                            // below FP32 resolution leaves L on the bracket's end
+                            if (Ln < lo || Ln > hi) Ln = L;
+                        } else {
+                            // below the root with no upper bracket yet, F' counts only the few
+                            // neighbours inside the kernel and the step can overshoot by orders of
+                            // magnitude: grow by at most a factor 2 until the root is bracketed
+                            if (hi == INFINITY && Ln > 2.f * L) {
+                                Ln = 2.f * L;
+                                newton = false;
+                            }
+                            if (!(Ln > lo && Ln < hi)) {
+                                Ln = hi < INFINITY ? 0.5f * (lo + hi) : 2.f * L;
+                                newton = false;
+                            }
+                        }
                     }
-                    const bool conv = fabsf(Ln - L) <= CONV_TOL * L || (hi < INFINITY && hi - lo <= 1e-7f * hi);
+                    const bool conv = fabsf(Ln - L) <= (newton ? NEWTON_TOL : CONV_TOL) * L ||
+                                      (hi < INFINITY && hi - lo <= 1e-7f * hi);
                     L = Ln;
                     if (conv) status = ST_LAST;
                     if (iters >= MAX_ITERS) {
@@ -752,20 +775,36 @@ int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params 
     unsigned long long *q = c->d.counters + (mode == 0 ? 5 : 6);
     cudaMemsetAsync(q, 0, sizeof(unsigned long long), c->stream);
     int blocks = (int)(c->cand_slots / LW_WARPS);
-    // variant = standard scheme | active list << 1 | curl << 2
-    const int var = (kp.standard ? 1 : 0) | (kp.active ? 2 : 0) | (kp.want_curl ? 4 : 0);
-    switch (mode == 0 ? var : 8 + (kp.active ? 1 : 0)) {
-    case 0: k_lengths<0, false, false, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
-    case 1: k_lengths<0, true, false, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
-    case 2: k_lengths<0, false, true, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
-    case 3: k_lengths<0, true, true, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
-    case 4: k_lengths<0, false, false, true><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
-    case 5: k_lengths<0, true, false, true><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
-    case 6: k_lengths<0, false, true, true><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
-    case 7: k_lengths<0, true, true, true><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
-    case 8: k_lengths<1, false, false, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
-    default: k_lengths<1, false, true, false><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break;
+    // variant = standard scheme | active list << 1 | curl << 2 | periodic << 3 (mode 0);
+    // 16 + active list | periodic << 1 (mode 1)
+    const int per = prm->periodic_mask ? 1 : 0;
+    const int var = mode == 0 ? ((kp.standard ? 1 : 0) | (kp.active ? 2 : 0) | (kp.want_curl ? 4 : 0) | (per << 3))
+                              : 16 + ((kp.active ? 1 : 0) | (per << 1));
+#define EVOL_LEN(M, S, A, C, P) \
+    k_lengths<M, S, A, C, P><<<blocks, LW_THREADS, 0, c->stream>>>(c->d, kp, q); break
+    switch (var) {
+    case 0: EVOL_LEN(0, false, false, false, false);
+    case 1: EVOL_LEN(0, true, false, false, false);
+    case 2: EVOL_LEN(0, false, true, false, false);
+    case 3: EVOL_LEN(0, true, true, false, false);
+    case 4: EVOL_LEN(0, false, false, true, false);
+    case 5: EVOL_LEN(0, true, false, true, false);
+    case 6: EVOL_LEN(0, false, true, true, false);
+    case 7: EVOL_LEN(0, true, true, true, false);
+    case 8: EVOL_LEN(0, false, false, false, true);
+    case 9: EVOL_LEN(0, true, false, false, true);
+    case 10: EVOL_LEN(0, false, true, false, true);
+    case 11: EVOL_LEN(0, true, true, false, true);
+    case 12: EVOL_LEN(0, false, false, true, true);
+    case 13: EVOL_LEN(0, true, false, true, true);
+    case 14: EVOL_LEN(0, false, true, true, true);
+    case 15: EVOL_LEN(0, true, true, true, true);
+    case 16: EVOL_LEN(1, false, false, false, false);
+    case 17: EVOL_LEN(1, false, true, false, false);
+    case 18: EVOL_LEN(1, false, false, false, true);
+    default: EVOL_LEN(1, false, true, false, true);
     }
+#undef EVOL_LEN
     return evol_cuda_ok(cudaGetLastError());
 }
 

@@ -316,3 +316,12 @@ def test_length_solve_from_poor_guesses(scale):
     w.h[:] = (w.h * scale).astype(np.float32)
     w.eps[:] = (w.eps * scale).astype(np.float32)
     _compare(w)
+
+
+@pytest.mark.parametrize("n_nei", [60.0, 110.0])
+def test_paper_neighbour_numbers(n_nei):
+    # the paper's recommended range 60 <= N_nei <= 110 (Sect. 2.1): lists of that many neighbours
+    # take the length solve's one-warp-per-particle form
+    w = W.evrard_sphere(8192, seed=7, sigma_v=0.1,
+                        params=W.Params(theta=0.5, n_nei_sph=n_nei, n_nei_grav=n_nei, leaf_size=16))
+    _compare(w)
