@@ -109,6 +109,22 @@ __device__ __forceinline__ float tc_over_u_u(float u, float iu)
 // 1/x from the hardware reciprocal (about 1 ulp), for operands of the pair loop
 __device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.f, x); }
 
+// Position of the k-th (0-based) set bit of m (k < popc(m)), by halving with population counts.
+__device__ __forceinline__ int nth_bit(unsigned m, int k)
+{
+    int p = 0;
+#pragma unroll
+    for (int h = 16; h > 0; h >>= 1) {
+        const int c = __popc(m & ((1u << h) - 1u));
+        if (k >= c) {
+            k -= c;
+            m >>= h;
+            p += h;
+        }
+    }
+    return p;
+}
+
 // Packed two-wide FP32 arithmetic (add/mul/fma .rn.f32x2): one instruction computes the same
 // operation, rounded the same way, on two independent FP32 values held in a 64-bit register.
 // The far-node loop evaluates two accepted nodes per lane with it, which halves the issue slots
@@ -242,16 +258,28 @@ template <>
 struct DissSmem<false> {
 };
 
+// Check mode: each lane's SPH neighbour count and set hash, accumulated by whichever lane
+// evaluates the pair (integer sums, so the order does not matter).
+template <bool CHECK>
+struct CheckSmem {
+    int cs[WK_WARPS][32];
+    unsigned long long hs[WK_WARPS][32];
+};
+template <>
+struct CheckSmem<false> {
+};
+
 // Register budgets, chosen so that no variant spills to local memory: the plain gravity + SPH walk
-// (the production form) and the SPH-only walk fit five blocks per SM (at most 102 registers), the
-// mixed gravity + SPH walk, the walks with the dissipation variants (DISS) and the plain
+// (the production form) and the plain SPH-only walk fit five blocks per SM (at most 102
+// registers), the mixed walks, the walks with the dissipation variants (DISS) and the plain
 // gravity-only periodic (EWALD) walk four (128 registers), the other gravity-only, periodic and
 // mixed DISS walks three; the check-mode variants one.
 template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS, bool EWALD>
-__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIXED) ? 4 : (EWALD || (GRAV && !SPH) || (MIXED && DISS)) ? 3 : ((GRAV && MIXED) || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIXED) ? 4 : (EWALD || (GRAV && !SPH) || (MIXED && DISS)) ? 3 : (MIXED || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
     __shared__ DissSmem<DISS> ds;
+    __shared__ CheckSmem<CHECK> cks;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int n = kp.n;
@@ -281,13 +309,10 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
         // this lane's hydro operands (v, P/rho^2, c, rho, 1/h, zeta/Omega*) are read where they are
         // used, in the SPH pass, which keeps them out of the traversal's live registers
         const float4 g0 = valid ? d.grav[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float xu_i = g0.y;                   // X/Upsilon (adaptive-softening correction)
         const bool gas_i = SPH && valid && g0.z > 0.f;
         const bool active = valid && (GRAV || gas_i);
         const float ie_i = g0.x, two_eps_i = GRAV && active ? 2.f / g0.x : 0.f;
         const float two_h_i = gas_i ? 2.f * g0.z : 0.f;
-        const float inv_mi = valid ? 1.f / pi.w : 0.f;
-        const float eps_i = GRAV && valid ? 1.f / ie_i : 0.f;
         // squared near radii of the pair tests: softened gravity inside max(E_i, E_j), SPH inside
         // max(H_i, H_j) when both are gas (H = -1 marks a particle that is not)
         const float E_i = two_eps_i * two_eps_i;
@@ -295,8 +320,8 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
 
         Acc acc;
         Totals<MIXED> tot;
-        unsigned long long hfar = 0, hnear = 0, hsph = 0;
-        int cfar = 0, cpp = 0, csph = 0;
+        unsigned long long hfar = 0, hnear = 0;
+        int cfar = 0, cpp = 0;
         // interaction counts of this lane (one group's counts fit 32 bits)
         unsigned wfar = 0, wpp = 0, wsph = 0, wsoft = 0;
         // per-group counts kept by lane 0 in shared memory: lane slots issued (32 per entry or per
@@ -308,6 +333,10 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
         if constexpr (DISS) {
             ds.vs[w][lane] = 0.f;
             ds.lap[w][lane] = 0.f;
+        }
+        if constexpr (CHECK) {
+            cks.cs[w][lane] = 0;
+            cks.hs[w][lane] = 0ull;
         }
         __syncwarp();
 
@@ -447,8 +476,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
             // there (Eqs. softforce, softphi) and the correction term vanishes with dW/dr; it is summed
             // here (as +m/r^3 d and +m/r, subtracted at the end).  Pairs inside that distance, and gas
             // pairs inside 2 max(h_i, h_j), are marked per lane (bit t of sbits) and evaluated in
-            // pass 2, each lane taking its own marked pairs, so that the warp runs the softened and
-            // SPH terms about as often as its busiest lane has such pairs.
+            // pass 2, where the warp's marked pairs are shared out 32 at a time.
             unsigned long long sbits = 0ull;
             {
                 const f32x2 PX = pk2(pi.x, pi.x), PY = pk2(pi.y, pi.y), PZ = pk2(pi.z, pi.z);
@@ -520,65 +548,104 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                     acc.pot += hi2(ewnzw) * iL;
                 }
             }
-            // Pass 2: the marked pairs of each lane.  Every lane of the warp runs this loop; lanes past
-            // the end of the particle array have no marks and read nothing.
-            if (__any_sync(0xffffffffu, sbits != 0ull)) {
-                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 gi = (SPH && valid) ? d.grav[s] : z4;
-                const float4 hi = (SPH && valid) ? d.hydro[s] : z4;
-                const float4 si = (SPH && valid) ? d.snd[s] : z4;
-                const float4 di = (DISS && gas_i) ? d.diss[s] : z4;
-                // wake-up: this particle's step (ticks), recorded at each SPH neighbour
-                unsigned Li = 0u;
-                if (kp.wake && gas_i) {
-                    const int ji = d.orig[s];
-                    Li = (unsigned)(d.te[ji] - d.tb[ji]);
+            // Pass 2: the marked pairs, shared out over the warp.  The marks are enumerated lane by
+            // lane (each lane's in entry order) and taken 32 at a time, item k of a batch by lane k,
+            // which reads its pair's owner (the lane whose particle is i) from the sorted state.  The
+            // items of one owner are consecutive: a segmented scan sums each batch's results per
+            // owner, and the owner adds the total; maxima go to shared memory as atomic maxima (the
+            // values are non-negative, so their bit patterns order like the floats).
+            {
+                const int nm = __popcll(sbits);
+                int incl = nm;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
                 }
-                while (__any_sync(0xffffffffu, sbits != 0ull)) {
+                const int excl = incl - nm;               // this lane's first item
+                const int nitems = __shfl_sync(0xffffffffu, incl, 31);
+                const unsigned sb_lo = (unsigned)sbits, sb_hi = (unsigned)(sbits >> 32);
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                // this lane's operands as an owner, formed once per flush and handed to the items by
+                // shuffles (as at the top of the group: 1/eps, eps, X/Upsilon, h, zeta/Omega*, 1/m)
+                const float4 gl = (nitems > 0 && valid) ? d.grav[s] : z4;
+                const float eps_l = GRAV && valid ? 1.f / gl.x : 0.f;
+                const float inv_ml = valid ? 1.f / pi.w : 0.f;
+                for (int base = 0; base < nitems; base += 32) {
                     if (lane == 0) wc[2] += 32u;
-                    if (sbits) {
-                        const int t = __ffsll((long long)sbits) - 1;
-                        sbits &= sbits - 1ull;
+                    const int item = base + lane;
+                    // the owner: the last lane whose items start at or before this one
+                    int o = 0;
+#pragma unroll
+                    for (int st = 16; st > 0; st >>= 1) {
+                        const int ex = __shfl_sync(0xffffffffu, excl, o + st);
+                        if (ex <= item) o += st;
+                    }
+                    const unsigned olo = __shfl_sync(0xffffffffu, sb_lo, o);
+                    const unsigned ohi = __shfl_sync(0xffffffffu, sb_hi, o);
+                    const int k = item - __shfl_sync(0xffffffffu, excl, o);    // the owner's k-th mark
+                    const int so = __shfl_sync(0xffffffffu, s, o);
+                    // the owner's operands
+                    const float4 po = make_float4(__shfl_sync(0xffffffffu, pi.x, o), __shfl_sync(0xffffffffu, pi.y, o),
+                                                  __shfl_sync(0xffffffffu, pi.z, o), 0.f);
+                    const float4 go = make_float4(__shfl_sync(0xffffffffu, gl.x, o), __shfl_sync(0xffffffffu, gl.y, o),
+                                                  __shfl_sync(0xffffffffu, gl.z, o), __shfl_sync(0xffffffffu, gl.w, o));
+                    const float E_o = __shfl_sync(0xffffffffu, E_i, o), H_o = __shfl_sync(0xffffffffu, H_i, o);
+                    const float eps_o = __shfl_sync(0xffffffffu, eps_l, o);
+                    const float inv_mo = __shfl_sync(0xffffffffu, inv_ml, o);
+                    const float ie_o = go.x, xu_o = go.y;
+                    float sum[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    if (item < nitems) {
+                        const int nlo = __popc(olo);
+                        const int t = k < nlo ? nth_bit(olo, k) : 32 + nth_bit(ohi, k - nlo);
                         const float *f = sm.npair[w][t >> 1] + (t & 1);
                         const float mj = f[6], Ej = f[8], Hj = f[10];
-                        const float dx = evol_wrap(pi.x - f[0], plen0, pm & 1);
-                        const float dy = evol_wrap(pi.y - f[2], plen1, pm & 2);
-                        const float dz = evol_wrap(pi.z - f[4], plen2, pm & 4);
+                        const float dx = evol_wrap(po.x - f[0], plen0, pm & 1);
+                        const float dy = evol_wrap(po.y - f[2], plen1, pm & 2);
+                        const float dz = evol_wrap(po.z - f[4], plen2, pm & 4);
                         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));     // as in pass 1
                         // r and 1/r from one reciprocal square root (coincident particles: both 0)
                         const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
                         const float r = r2 * rinv;
                         const float4 gj = sm.ng[w][t];
-                        if (GRAV && r2 < fmaxf(E_i, Ej)) {              // the same test as pass 1
+                        if (GRAV && r2 < fmaxf(E_o, Ej)) {              // the same test as pass 1
                             ++wsoft;
                             // symmetrised softened pair force and potential (App. B), each side
                             // softened where u < 2 and Newtonian beyond
-                            const float ui = r * ie_i, uj = r * gj.x;
-                            const float iui = rinv * eps_i, iuj = rinv * rcp_fast(gj.x);
+                            const float ui = r * ie_o, uj = r * gj.x;
+                            const float iui = rinv * eps_o, iuj = rinv * rcp_fast(gj.x);
                             const float rinv3 = rinv * rinv * rinv;
-                            const float fi = ui < 2.f ? gsoft_over_r_u(ui, iui) * ie_i * ie_i * ie_i : rinv3;
+                            const float fi = ui < 2.f ? gsoft_over_r_u(ui, iui) * ie_o * ie_o * ie_o : rinv3;
                             const float fj = uj < 2.f ? gsoft_over_r_u(uj, iuj) * gj.x * gj.x * gj.x : rinv3;
                             float fg = -0.5f * mj * (fi + fj);
-                            acc.pot += mj * (ui < 2.f ? phisoft_u(ui, iui) * ie_i : -rinv);
+                            sum[3] = mj * (ui < 2.f ? phisoft_u(ui, iui) * ie_o : -rinv);
                             if (kp.adaptive) {
                                 // adaptive-softening correction (Eq. dLgravdr, mass-weighted reading)
-                                const float ie2 = ie_i * ie_i, je2 = gj.x * gj.x;
-                                const float ci = ui < 2.f ? xu_i * dw_over_u_u(ui, iui) * ie2 * ie2 * ie_i : 0.f;
+                                const float ie2 = ie_o * ie_o, je2 = gj.x * gj.x;
+                                const float ci = ui < 2.f ? xu_o * dw_over_u_u(ui, iui) * ie2 * ie2 * ie_o : 0.f;
                                 const float cj = uj < 2.f ? gj.y * dw_over_u_u(uj, iuj) * je2 * je2 * gj.x : 0.f;
-                                fg += -0.5f * inv_pi * (ci + mj * inv_mi * cj);
+                                fg += -0.5f * inv_pi * (ci + mj * inv_mo * cj);
                             }
-                            acc.ax += fg * dx;
-                            acc.ay += fg * dy;
-                            acc.az += fg * dz;
+                            sum[0] = fg * dx;
+                            sum[1] = fg * dy;
+                            sum[2] = fg * dz;
                         }
-                        if (SPH && fminf(H_i, Hj) >= 0.f && r2 < fmaxf(H_i, Hj)) {   // as in pass 1
+                        if (SPH && fminf(H_o, Hj) >= 0.f && r2 < fmaxf(H_o, Hj)) {   // as in pass 1
                             ++wsph;
-                            if (CHECK) {
-                                ++csph;
-                                hsph += evol_mix64((unsigned long long)sm.norig[w][t]);
+                            if constexpr (CHECK) {
+                                atomicAdd(&cks.cs[w][o], 1);
+                                atomicAdd(&cks.hs[w][o], evol_mix64((unsigned long long)sm.norig[w][t]));
                             }
-                            if (kp.wake) atomicMin(&d.nbmin[sm.near_j[w][t]], Li);
+                            if (kp.wake) {
+                                // wake-up: the owner's step (ticks), recorded at its SPH neighbour
+                                const int jo = d.orig[so];
+                                atomicMin(&d.nbmin[sm.near_j[w][t]], (unsigned)(d.te[jo] - d.tb[jo]));
+                            }
                             if (r2 > 0.f) {
+                                const float4 gi = go;
+                                const float4 hi = d.hydro[so];
+                                const float4 si = d.snd[so];
+                                const float4 di = DISS ? d.diss[so] : z4;
                                 const float4 hj = sm.nh[w][t];
                                 const float4 sj = sm.ns[w][t];
                                 const float ihi = si.z, ihj = sj.z;
@@ -588,7 +655,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                                 const float kgi = (kp.use_tc ? tc_over_u_u(uhi, iuhi) : dw_over_u_u(uhi, iuhi)) * ihi2 * ihi2 * ihi * inv_pi;
                                 const float kgj = (kp.use_tc ? tc_over_u_u(uhj, iuhj) : dw_over_u_u(uhj, iuhj)) * ihj2 * ihj2 * ihj * inv_pi;
                                 const float fi = 1.f + gi.w * rcp_fast(mj);       // 1 + zeta_i / (m_j Omega*_i)
-                                const float fj = 1.f + gj.w * inv_mi;             // 1 + zeta_j / (m_i Omega*_j)
+                                const float fj = 1.f + gj.w * inv_mo;             // 1 + zeta_j / (m_i Omega*_j)
                                 const float vx = hi.x - hj.x, vy = hi.y - hj.y, vz = hi.z - hj.z;
                                 const float vr = vx * dx + vy * dy + vz * dz;
                                 float visc = 0.f;
@@ -600,12 +667,12 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                                     dj = ds.nd[w][t];
                                     wij = vr * rinv;
                                     vsig = si.x + sj.x - fminf(wij, 0.f);
-                                    ds.vs[w][lane] = fmaxf(ds.vs[w][lane], vsig);
+                                    atomicMax(reinterpret_cast<int *>(&ds.vs[w][o]), __float_as_int(vsig));
                                 }
                                 if (vr < 0.f) {
                                     const float hb = 0.5f * (gi.z + gj.z);
                                     const float mu = hb * vr * rcp_fast(r2 + 0.01f * hb * hb);
-                                    sm.mum[w][lane] = fmaxf(sm.mum[w][lane], -mu);    // |mu| (vr < 0)
+                                    atomicMax(reinterpret_cast<int *>(&sm.mum[w][o]), __float_as_int(-mu));   // |mu|
                                     const float cb = 0.5f * (si.x + sj.x);
                                     const float rb = 0.5f * (si.y + sj.y);
                                     if constexpr (!DISS) {
@@ -624,10 +691,10 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                                 const float gbar = 0.5f * (kgi * fi + kgj * fj);
                                 const float pterm_i = hi.w * fi * kgi;
                                 const float sc = -mj * (pterm_i + hj.w * fj * kgj + visc * gbar);
-                                acc.hx += sc * dx;
-                                acc.hy += sc * dy;
-                                acc.hz += sc * dz;
-                                acc.du += mj * (pterm_i + 0.5f * visc * gbar) * vr;
+                                sum[4] = sc * dx;
+                                sum[5] = sc * dy;
+                                sum[6] = sc * dz;
+                                sum[7] = mj * (pterm_i + 0.5f * visc * gbar) * vr;
                                 if constexpr (DISS) {
                                     if (kp.conduction) {
                                         // artificial conductivity: du_i/dt += m_j Pi^u_ij |gradbar W_ij| with
@@ -639,12 +706,48 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                                                              ? sqrtf(fabsf(si.w - sj.w) * irb)
                                                              : vsig;
                                         const float ag = fabsf(gbar);
-                                        acc.du -= mj * (0.5f * (di.w + dj.w)) * vu * duij * irb * ag * r;
-                                        ds.lap[w][lane] += 2.f * mj * duij * rcp_fast(sj.y) * ag;
+                                        sum[7] -= mj * (0.5f * (di.w + dj.w)) * vu * duij * irb * ag * r;
+                                        sum[8] = 2.f * mj * duij * rcp_fast(sj.y) * ag;
                                     }
                                 }
                             }
                         }
+                    }
+                    // segmented inclusive scan over the batch: a segment starts where the owner changes
+                    const int oprev = __shfl_up_sync(0xffffffffu, o, 1);     // every lane takes part
+                    int head = (lane == 0 || oprev != o) ? 1 : 0;
+#pragma unroll
+                    for (int dd = 1; dd < 32; dd <<= 1) {
+                        const int hu = __shfl_up_sync(0xffffffffu, head, dd);
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) {
+                            if ((q < 4 && !GRAV) || (q >= 4 && q < 8 && !SPH) || (q == 8 && !DISS)) continue;
+                            const float vu = __shfl_up_sync(0xffffffffu, sum[q], dd);
+                            if (lane >= dd && !head) sum[q] += vu;
+                        }
+                        if (lane >= dd) head |= hu;
+                    }
+                    // each owner takes its segment's total from the segment's last item
+                    const bool mine = nm > 0 && excl < base + 32 && excl + nm > base;
+                    const int tail = (min(excl + nm, base + 32) - 1 - base) & 31;
+                    float tot_[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        tot_[q] = 0.f;
+                        if ((q < 4 && !GRAV) || (q >= 4 && q < 8 && !SPH) || (q == 8 && !DISS)) continue;
+                        const float tv = __shfl_sync(0xffffffffu, sum[q], tail);
+                        if (mine) tot_[q] = tv;
+                    }
+                    if (mine) {
+                        acc.ax += tot_[0];
+                        acc.ay += tot_[1];
+                        acc.az += tot_[2];
+                        acc.pot += tot_[3];
+                        acc.hx += tot_[4];
+                        acc.hy += tot_[5];
+                        acc.hz += tot_[6];
+                        acc.du += tot_[7];
+                        if constexpr (DISS) ds.lap[w][lane] += tot_[8];
                     }
                 }
             }
@@ -965,13 +1068,13 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                     }
                 }
             }
-            if (CHECK) {
+            if constexpr (CHECK) {
                 d.hash3[3 * s + 0] = hfar;
                 d.hash3[3 * s + 1] = hnear;
-                d.hash3[3 * s + 2] = hsph;
+                d.hash3[3 * s + 2] = cks.hs[w][lane];
                 d.cnt3[3 * s + 0] = cfar;
                 d.cnt3[3 * s + 1] = cpp;
-                d.cnt3[3 * s + 2] = csph;
+                d.cnt3[3 * s + 2] = cks.cs[w][lane];
             }
         }
         // interaction counters, per lane: summed over the warp
