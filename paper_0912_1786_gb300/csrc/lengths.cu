@@ -400,9 +400,10 @@ __device__ int gather_from_list(const evol_dev &d, const evol_kparams &kp, const
 
 // Variants: STD the standard scheme (mode 0), ACT the active list of individual time steps, CURL
 // |curl v| in the last evaluation (mode 0), PER periodic axes; each a template parameter, so that
-// the default solve's code carries none of them.
+// the default solve's code carries none of them.  Five blocks per SM (at most 102 registers); the
+// curl variants, which need more registers, four.
 template <int MODE, bool STD, bool ACT, bool CURL, bool PER>
-__global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__global__ void __launch_bounds__(LW_THREADS, CURL ? 4 : 5) k_lengths(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ LenSmem sm;
     const int lane = threadIdx.x & 31;
@@ -453,9 +454,11 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
         __syncwarp();
         bool broken = false;
 
-        do {                                           // one group walk for the SUB particles
-          const unsigned subm = todo0;
-          // one walk for the SUB particles: their box and largest search radius
+        // one group walk for the SUB particles; where their leaves do not fit one list, walks for
+        // the first half of them and then for the rest
+        unsigned pending = todo0, subm = todo0;
+        while (pending && !broken) {
+          // the walk's particles: their box and largest search radius
           const bool insub = (subm >> lane) & 1u;
           float gx0 = insub ? pi4.x : INFINITY, gy0 = insub ? pi4.y : INFINITY, gz0 = insub ? pi4.z : INFINITY;
           float gx1 = insub ? pi4.x : -INFINITY, gy1 = insub ? pi4.y : -INFINITY, gz1 = insub ? pi4.z : -INFINITY;
@@ -480,6 +483,12 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
           }
           const bool glist = nleaf <= GCAP;
           if (lane == 0 && !glist) ++lc[3];
+          if (!glist && __popc(subm) > 1) {
+              unsigned upper = subm;                  // subm less its lowest popc/2 particles
+              for (int q = __popc(subm) / 2; q > 0; --q) upper &= upper - 1u;
+              subm &= ~upper;
+              continue;
+          }
           unsigned todo = subm;
           while (todo && !broken) {
             const int t = __ffs(todo) - 1;
@@ -743,7 +752,9 @@ __global__ void __launch_bounds__(LW_THREADS, 5) k_lengths(evol_dev d, evol_kpar
             }
             iters_total += iters;
           }
-        } while (0);
+          pending &= ~subm;
+          subm = pending;
+        }
         if (lane == 0) {
             atomicAdd(&d.counters[3], (unsigned long long)iters_total);
             unsigned long long *c4 = d.counters + (MODE == 1 ? 16 : 20);
