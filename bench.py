@@ -58,12 +58,10 @@ def _hbm_peak():
 
 
 HBM_PEAK_GBS = _hbm_peak()
-# DRAM bytes (read + written) of one force-walk launch from an ncu capture of the same build and
-# command, keyed by (workload, leaf size); empty until a capture of the current walk is recorded.
 # DRAM bytes per launch of the production walk (dram__bytes_read.sum + dram__bytes_write.sum of a
 # one-pass ncu capture of the full-size workload at that leaf size); other workloads and leaf sizes
 # report null
-WALK_TRAFFIC = {("c3", 16): 433.0e6 + 119.4e6, ("c3", 24): 385.1e6 + 107.5e6, ("c3", 32): 364.3e6 + 106.3e6}
+WALK_TRAFFIC = {("c3", 16): 430.9e6 + 118.0e6, ("c3", 24): 384.7e6 + 106.4e6, ("c3", 32): 363.8e6 + 104.8e6}
 
 
 def log(*a):
