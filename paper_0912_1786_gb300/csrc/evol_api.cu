@@ -39,7 +39,7 @@ void free_all(evol_ctx *c)
     evol_dev &d = c->d;
     void *ptrs[] = {d.pos, d.vel, d.grav, d.hydro, d.snd, d.vah, d.orig, d.inv, d.divv_h, d.divv_e, d.mumax, d.dt, d.time, d.len_h, d.len_eps, d.nh, d.omega,
                     d.diss, d.curlv_h, d.vsig, d.lapu, d.dalpha, d.dalpha_u, d.tb, d.te, d.bact, d.pred_tau,
-                    d.pers, d.actf, d.acts, d.act, d.nbmin, d.bt, d.ewald,
+                    d.pers, d.actf, d.acts, d.act, d.sg_acc, d.sg_front, d.sg_info, d.nbmin, d.bt, d.ewald,
                     d.zeta, d.rho, d.neps, d.ups, d.X, d.acc, d.dudt, d.keys_a, d.keys_b, d.vals_a, d.vals_b,
                     d.hist, d.lcp, d.cnt, d.base, d.scan_part, d.nbeg, d.nend, d.nlev, d.nnext, d.nparent,
                     d.nnch, d.narrive, d.nA, d.nB, d.nC, d.nQ0, d.nQ1, d.nM64, d.nC64, d.nQ64, d.nBmin,
@@ -238,6 +238,11 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.dalpha, n); rc |= dalloc(&d.dalpha_u, n);
     rc |= dalloc(&d.tb, n); rc |= dalloc(&d.te, n); rc |= dalloc(&d.bact, n); rc |= dalloc(&d.pred_tau, n);
     rc |= dalloc(&d.pers, 7 * n); rc |= dalloc(&d.actf, n); rc |= dalloc(&d.acts, n + 1); rc |= dalloc(&d.act, n);
+    {
+        const int64_t nsg = n / 256 + 2;        // super-groups of the force walk
+        rc |= dalloc(&d.sg_acc, nsg * EVOL_SG_ACAP); rc |= dalloc(&d.sg_front, nsg * EVOL_SG_FCAP);
+        rc |= dalloc(&d.sg_info, nsg);
+    }
     rc |= dalloc(&d.nbmin, n); rc |= dalloc(&d.bt, 8);
     rc |= dalloc(&d.ewald, (int64_t)EVOL_EWALD_M * EVOL_EWALD_M * EVOL_EWALD_M);
     if (!rc && cudaMallocHost((void **)&c->h_bt, 8 * sizeof(unsigned long long)) != cudaSuccess) rc = EVOL_ENOMEM;

@@ -46,6 +46,11 @@ struct evol_dev {
     float *pred_tau;                // t_now - (tb + te)/2 (time units): prediction of v and u
     float *pers;                    // last evaluation: rho, Omega*, zeta, Upsilon, X, div v, |curl v| (7 x cap)
     int32_t *actf, *acts, *act;     // sorted: active flags, their exclusive scan (+ total), the list
+    // force walk: per super-group (8 groups of 32 list entries) the nodes its bounds accept for all
+    // its particles (EVOL_SG_ACAP each), the frontier its groups start from (EVOL_SG_FCAP each), and
+    // their counts (-1: walk from the root)
+    int32_t *sg_acc, *sg_front;
+    int2 *sg_info;
     unsigned *nbmin;                // sorted: smallest active-neighbour step (wake-up)
     unsigned long long *bt;         // [0] t_sys [1] t_next (ticks); [2..5] run counts
     float4 *ewald;                  // periodic gravity: correction table (f, g) for L = 1
@@ -247,6 +252,10 @@ __device__ __forceinline__ float evol_wrap(float d, float len, int periodic)
     return periodic ? d - len * rintf(d / len) : d;
 }
 
+// ---- force-walk super-groups: list capacities per super-group --------------------------------
+#define EVOL_SG_ACAP 3072
+#define EVOL_SG_FCAP 768
+
 // ---- periodic gravity (Ewald, Sect. 4.3) ----------------------------------------------------
 // Correction table for a cube of side 1: (f_x, f_y, f_z, g) at the grid points (i, j, k) / (2 N) of the
 // octant [0, 1/2]^3, 0 <= i, j, k <= N; entry ((i M + j) M + k), M = N + 1.
@@ -270,6 +279,7 @@ struct evol_kparams {
     // positions, ascending; its length at d.acts[n]); the force walk also records, per SPH
     // neighbour, the smallest step (ticks) of an active particle next to it (wake-up)
     int active, wake;
+    int super;               // the force walk's groups start from their super-group's lists
     // periodic gravity (Ewald): cube side, 2 N / L for the table lookup, the table (L = 1)
     int ewald;
     float ewald_L, ewald_sc;

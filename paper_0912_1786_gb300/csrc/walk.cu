@@ -35,6 +35,7 @@ constexpr int WK_THREADS = 128;
 constexpr int WK_WARPS = WK_THREADS / 32;
 constexpr int FARCAP = 64;
 constexpr int NEARCAP = 64;
+constexpr int SG_GROUPS = 8;      // groups per super-group (see k_super)
 
 constexpr float TAU = 1e-5f;      // safety margin of the group-level bounds
 
@@ -271,11 +272,10 @@ struct CheckSmem<false> {
 
 // Register budgets, chosen so that no variant spills to local memory: the plain gravity + SPH walk
 // (the production form) and the plain SPH-only walk fit five blocks per SM (at most 102
-// registers), the mixed walks, the walks with the dissipation variants (DISS) and the plain
-// gravity-only periodic (EWALD) walk four (128 registers), the other gravity-only, periodic and
-// mixed DISS walks three; the check-mode variants one.
+// registers), the mixed walks and the walks with the dissipation variants (DISS) four (128
+// registers), the gravity-only, periodic and mixed DISS walks three; the check-mode variants one.
 template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS, bool EWALD>
-__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIXED) ? 4 : (EWALD || (GRAV && !SPH) || (MIXED && DISS)) ? 3 : (MIXED || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SPH) || (MIXED && DISS)) ? 3 : (MIXED || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
     __shared__ DissSmem<DISS> ds;
@@ -788,9 +788,23 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
         __syncwarp();
 
         int2 *stk = d.wstack + (size_t)(blockIdx.x * WK_WARPS + w) * kp.stack_stride;
-        // one stack entry per system present in the group: its root with the mask of its lanes
         int top = 0;
-        {
+        // nodes accepted for all by the super-group, taken 32 at a time before the stack: [apos, aend)
+        const int *alist = d.sg_acc;
+        int apos = 0, aend = 0;
+        const int2 sgi = kp.super ? d.sg_info[g / SG_GROUPS] : make_int2(-1, -1);
+        if (sgi.x >= 0 && sgi.y <= kp.stack_cap) {
+            // the super-group's lists (k_super), with the mask of every active lane: its frontier on
+            // the stack, the nodes it accepted for all as batches that skip the node tests (they
+            // count only as far nodes, and as accepted nodes in check mode)
+            const size_t sgb = (size_t)(g / SG_GROUPS);
+            for (int k = lane; k < sgi.y; k += 32)
+                stk[k] = make_int2(d.sg_front[sgb * EVOL_SG_FCAP + k], (int)rootmask);
+            top = sgi.y;
+            alist = d.sg_acc + sgb * EVOL_SG_ACAP;
+            aend = (GRAV || CHECK) ? sgi.x : 0;
+        } else {
+            // one stack entry per system present in the group: its root with the mask of its lanes
             const int myroot = active ? d.sys_root[d.sys_sorted[s]] : -1;
             const unsigned peers = __match_any_sync(0xffffffffu, myroot);
             const bool leader = active && (__ffs(peers) - 1) == lane;
@@ -803,7 +817,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
         // tree: stop, flag it and report where
         long long pops = 0;
         const long long pop_cap = 2ll * (long long)(*d.nnodes) + 64;
-        while (top > 0) {
+        while (top > 0 || apos < aend) {
             if (++pops > pop_cap) {
                 if (lane == 0) {
                     evol_flag(d.err, EVOL_ETIMEOUT);
@@ -811,20 +825,36 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                 }
                 break;
             }
-            const int k = min(top, 32);
-            top -= k;
             int node = -1;
             unsigned M = 0;
-            if (lane < k) {
-                const int2 e = stk[top + lane];
-                node = e.x;
-                M = (unsigned)e.y;
+            const bool pre = apos < aend;    // a batch of the super-group's accepted nodes
+            int k;
+            if (pre) {
+                k = min(aend - apos, 32);
+                if (lane < k) {
+                    node = alist[apos + lane];
+                    M = rootmask;
+                }
+                apos += k;
+            } else {
+                k = min(top, 32);
+                top -= k;
+                if (lane < k) {
+                    const int2 e = stk[top + lane];
+                    node = e.x;
+                    M = (unsigned)e.y;
+                }
             }
             __syncwarp();
             int4 I = make_int4(0, 0, 0, 0);
             int cls = 0;                     // 0 none, 1 accept all, 2 open all, 3 mixed
             unsigned Ak = 0, Ok = 0;
-            if (lane < k) {
+            if (pre) {
+                if (lane < k) {
+                    cls = 1;
+                    Ak = M;
+                }
+            } else if (lane < k) {
                 I = d.nI[node];
                 const float4 B = d.nB[node];
                 const float4 C = d.nC[node];
@@ -985,6 +1015,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                 }
             }
             // opened internal nodes: push their children with the open mask
+            if (pre) continue;               // nothing opened
             const bool io = Ok != 0u && !isleaf;
             int nch = 0;
             int ch[8];
@@ -1096,6 +1127,197 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
     }
 }
 
+// Super-groups: 8 consecutive groups (256 consecutive entries of the particle list) walk the top of
+// the tree once for all 8.  A node that the super-group's bounds accept for every one of its
+// particles is accepted by each particle's own test (the bounds hold with the same margin as the
+// group bounds, and a group's particles are a subset), and every particle reaches it (each of its
+// ancestors was opened for all of them); such nodes are listed once and go to each group's far
+// list with the mask of all its lanes.  Nodes the bounds leave undecided, and the leaves they open
+// for all, form the frontier from which each group's own traversal starts.  A super-group with
+// particles of more than one system, or whose lists do not fit, is marked, and its groups walk
+// from the root.
+template <bool GRAV, bool SPH, bool EWALD>
+__global__ void __launch_bounds__(32, 16) k_super(evol_dev d, evol_kparams kp, int nsg)
+{
+    const int lane = threadIdx.x;
+    const int n = kp.n;
+    const int nlist = kp.active ? d.acts[n] : n;
+    const int pm = ((SPH && !GRAV) || EWALD) ? kp.periodic_mask : 0;
+    const int pmg = EWALD ? kp.periodic_mask : 0;
+    const float plen0 = kp.plen[0], plen1 = kp.plen[1], plen2 = kp.plen[2];
+    const float side0 = EWALD ? d.fcube[3] : 0.f;
+    int *stk = reinterpret_cast<int *>(d.wstack + (size_t)blockIdx.x * kp.stack_stride);
+    const int stack_cap = 2 * kp.stack_cap;
+    const unsigned ltmask = (1u << lane) - 1u;
+    const long long pop_cap = 2ll * (long long)(*d.nnodes) + 64;
+    for (int sg = blockIdx.x; sg < nsg; sg += gridDim.x) {
+        // bounds over the super-group's active particles (as the group bounds of the walk)
+        float gx0 = INFINITY, gy0 = INFINITY, gz0 = INFINITY, gx1 = -INFINITY, gy1 = -INFINITY, gz1 = -INFINITY;
+        float emax = 0.f, emin = INFINITY, hmax = -1.f, hmin = INFINITY;
+        int rmin = 0x7fffffff, rmax = -1;
+        bool all_gas = true;
+#pragma unroll 1
+        for (int q = 0; q < 32 * SG_GROUPS; q += 32) {
+            const int e = sg * 32 * SG_GROUPS + q + lane;
+            if (e >= nlist) continue;
+            const int s = kp.active ? d.act[e] : e;
+            const float4 p = d.pos[s];
+            const float4 g0 = d.grav[s];
+            const bool gas = SPH && g0.z > 0.f;
+            if (!(GRAV || gas)) continue;           // not active in this walk
+            gx0 = fminf(gx0, p.x); gy0 = fminf(gy0, p.y); gz0 = fminf(gz0, p.z);
+            gx1 = fmaxf(gx1, p.x); gy1 = fmaxf(gy1, p.y); gz1 = fmaxf(gz1, p.z);
+            if (GRAV) {
+                const float te = 2.f / g0.x;
+                emax = fmaxf(emax, te);
+                emin = fminf(emin, te);
+            }
+            if (gas) {
+                hmax = fmaxf(hmax, 2.f * g0.z);
+                hmin = fminf(hmin, 2.f * g0.z);
+            } else {
+                all_gas = false;
+            }
+            const int r = d.sys_root[d.sys_sorted[s]];
+            rmin = min(rmin, r);
+            rmax = max(rmax, r);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            gx0 = fminf(gx0, __shfl_xor_sync(0xffffffffu, gx0, o));
+            gy0 = fminf(gy0, __shfl_xor_sync(0xffffffffu, gy0, o));
+            gz0 = fminf(gz0, __shfl_xor_sync(0xffffffffu, gz0, o));
+            gx1 = fmaxf(gx1, __shfl_xor_sync(0xffffffffu, gx1, o));
+            gy1 = fmaxf(gy1, __shfl_xor_sync(0xffffffffu, gy1, o));
+            gz1 = fmaxf(gz1, __shfl_xor_sync(0xffffffffu, gz1, o));
+            emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+            emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+            hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+            hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
+            rmin = min(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+            rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        }
+        all_gas = SPH && __all_sync(0xffffffffu, all_gas);
+        if (!GRAV) emin = 0.f;
+        int2 info = make_int2(-1, -1);
+        if (rmax >= 0 && rmin == rmax) {
+            const float gcx = 0.5f * (gx0 + gx1), gcy = 0.5f * (gy0 + gy1), gcz = 0.5f * (gz0 + gz1);
+            const float gwx = 0.5f * (gx1 - gx0), gwy = 0.5f * (gy1 - gy0), gwz = 0.5f * (gz1 - gz0);
+            int *acc = d.sg_acc + (size_t)sg * EVOL_SG_ACAP;
+            int *front = d.sg_front + (size_t)sg * EVOL_SG_FCAP;
+            int na = 0, nf = 0, top = 1;
+            bool ok = true;
+            if (lane == 0) stk[0] = rmin;
+            __syncwarp();
+            long long pops = 0;
+            while (top > 0) {
+                if (++pops > pop_cap) {
+                    ok = false;
+                    break;
+                }
+                const int k = min(top, 32);
+                top -= k;
+                const int node = lane < k ? stk[top + lane] : -1;
+                __syncwarp();
+                int cls = 0;                 // 0 none, 1 accept all, 2 open all, 3 mixed
+                bool leaf = false;
+                int4 I = make_int4(0, 0, 0, 0);
+                if (lane < k) {
+                    I = d.nI[node];
+                    const float4 B = d.nB[node];
+                    const float4 C = d.nC[node];
+                    const float4 A = GRAV ? d.nA[node] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float dx = fabsf(evol_wrap(B.x - gcx, plen0, pm & 1));
+                    const float dy = fabsf(evol_wrap(B.y - gcy, plen1, pm & 2));
+                    const float dz = fabsf(evol_wrap(B.z - gcz, plen2, pm & 4));
+                    const float nx = fmaxf(dx - (C.x + gwx), 0.f), ny = fmaxf(dy - (C.y + gwy), 0.f),
+                                nz = fmaxf(dz - (C.z + gwz), 0.f);
+                    const float fx = fmaxf(dx + gwx - C.x, 0.f), fy = fmaxf(dy + gwy - C.y, 0.f),
+                                fz = fmaxf(dz + gwz - C.z, 0.f);
+                    const float bnear2 = nx * nx + ny * ny + nz * nz, bfar2 = fx * fx + fy * fy + fz * fz;
+                    float rup = GRAV ? fmaxf(emax, C.w) : 0.f;
+                    float rlo = GRAV ? fmaxf(emin, C.w) : 0.f;
+                    if (SPH && B.w >= 0.f && hmax >= 0.f) {
+                        rup = fmaxf(rup, fmaxf(hmax, B.w));
+                        if (all_gas) rlo = fmaxf(rlo, fmaxf(hmin, B.w));
+                    }
+                    bool acc_all = bnear2 > rup * rup * (1.f + TAU);
+                    bool open_all = bfar2 < rlo * rlo * (1.f - TAU);
+                    if (EWALD && !(ldexpf(side0, -(I.x & 0xff)) <= 0.125f * kp.ewald_L)) {
+                        acc_all = false;
+                        open_all = true;
+                    }
+                    if (GRAV) {
+                        const float ax = fabsf(evol_wrap(A.x - gcx, plen0, pmg & 1)), ay = fabsf(evol_wrap(A.y - gcy, plen1, pmg & 2)),
+                                    az = fabsf(evol_wrap(A.z - gcz, plen2, pmg & 4));
+                        const float mx = fmaxf(ax - gwx, 0.f), my = fmaxf(ay - gwy, 0.f), mz = fmaxf(az - gwz, 0.f);
+                        const float Mx = ax + gwx, My = ay + gwy, Mz = az + gwz;
+                        acc_all = acc_all && (mx * mx + my * my + mz * mz > A.w * (1.f + TAU));
+                        open_all = open_all || (Mx * Mx + My * My + Mz * Mz < A.w * (1.f - TAU));
+                    }
+                    cls = acc_all ? 1 : (open_all ? 2 : 3);
+                    leaf = (I.x >> 8) & 1;
+                }
+                // accepted for all: listed (far nodes of the gravity walks; the SPH-only walks read
+                // them only in check mode, which records every accepted node)
+                const unsigned am = __ballot_sync(0xffffffffu, cls == 1);
+                if (am) {
+                    if (na + __popc(am) > EVOL_SG_ACAP) {
+                        ok = false;
+                        break;
+                    }
+                    if (cls == 1) acc[na + __popc(am & ltmask)] = node;
+                    na += __popc(am);
+                }
+                // undecided, or a leaf opened for all: the groups' frontier
+                const bool fr = cls == 3 || (cls == 2 && leaf);
+                const unsigned fm = __ballot_sync(0xffffffffu, fr);
+                if (fm) {
+                    if (nf + __popc(fm) > EVOL_SG_FCAP) {
+                        ok = false;
+                        break;
+                    }
+                    if (fr) front[nf + __popc(fm & ltmask)] = node;
+                    nf += __popc(fm);
+                }
+                // internal nodes opened for all: push their children
+                const bool io = cls == 2 && !leaf;
+                int nch = 0;
+                int ch[8];
+                if (io) {
+                    const int4 K0 = d.nK0[node], K1 = d.nK1[node];
+                    ch[0] = K0.x; ch[1] = K0.y; ch[2] = K0.z; ch[3] = K0.w;
+                    ch[4] = K1.x; ch[5] = K1.y; ch[6] = K1.z; ch[7] = K1.w;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) nch += ch[u] >= 0 ? 1 : 0;
+                }
+                int incl = nch;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                if (top + total > stack_cap) {
+                    ok = false;
+                    break;
+                }
+                if (io) {
+                    const int pos = top + incl - nch;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (u < nch) stk[pos + u] = ch[u];
+                }
+                top += total;
+                __syncwarp();
+            }
+            if (ok) info = make_int2(na, nf);
+        }
+        if (lane == 0) d.sg_info[sg] = info;
+        __syncwarp();
+    }
+}
+
 template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS, bool EWALD>
 void launch_walk(evol_ctx *c, const evol_kparams &kp)
 {
@@ -1126,6 +1348,9 @@ void launch_walk_pcd(evol_ctx *c, const evol_kparams &kp, bool mixed, bool check
 template <bool GRAV, bool SPH, bool EWALD>
 void launch_walk_pce(evol_ctx *c, const evol_kparams &kp, bool mixed, bool check)
 {
+    // the super-groups' top-of-tree walk first (one warp per block, 16 blocks per SM)
+    const int nsg = (kp.n + 32 * SG_GROUPS - 1) / (32 * SG_GROUPS);
+    if (kp.super && nsg > 0) k_super<GRAV, SPH, EWALD><<<c->num_sms * 16, 32, 0, c->stream>>>(c->d, kp, nsg);
     if constexpr (SPH) {
         if (kp.diss) {
             launch_walk_pcd<GRAV, SPH, true, EWALD>(c, kp, mixed, check);
@@ -1184,6 +1409,7 @@ int evol_launch_walk(evol_ctx *c, const evol_particles *p, const evol_params *pr
     kp.alpha_tau = prm->alpha_tau;
     kp.alpha_source = prm->alpha_source;
     kp.alpha_u_min = prm->alpha_u_min;
+    kp.super = 1;
     bool mixed = prm->precision == EVOL_FP32_MIXED;
     bool check = c->check_mode != 0;
     if (do_grav && do_sph) launch_walk_pc<true, true>(c, kp, mixed, check);
