@@ -61,7 +61,7 @@ HBM_PEAK_GBS = _hbm_peak()
 # DRAM bytes per launch of the production walk (dram__bytes_read.sum + dram__bytes_write.sum of a
 # one-pass ncu capture of the full-size workload at that leaf size); other workloads and leaf sizes
 # report null
-WALK_TRAFFIC = {("c3", 16): 430.9e6 + 118.0e6, ("c3", 24): 384.7e6 + 106.4e6, ("c3", 32): 363.8e6 + 104.8e6}
+WALK_TRAFFIC = {("c3", 16): 499.2e6 + 100.6e6, ("c3", 24): 455.0e6 + 95.5e6, ("c3", 32): 432.2e6 + 93.0e6}
 
 
 def log(*a):

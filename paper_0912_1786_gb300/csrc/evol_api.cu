@@ -239,7 +239,7 @@ int evol_create(evol_ctx **out, int64_t max_n, void *stream)
     rc |= dalloc(&d.tb, n); rc |= dalloc(&d.te, n); rc |= dalloc(&d.bact, n); rc |= dalloc(&d.pred_tau, n);
     rc |= dalloc(&d.pers, 7 * n); rc |= dalloc(&d.actf, n); rc |= dalloc(&d.acts, n + 1); rc |= dalloc(&d.act, n);
     {
-        const int64_t nsg = n / 256 + 2;        // super-groups of the force walk
+        const int64_t nsg = n / (32 * EVOL_SG_GROUPS) + 2;     // super-groups of the force walk
         rc |= dalloc(&d.sg_acc, nsg * EVOL_SG_ACAP); rc |= dalloc(&d.sg_front, nsg * EVOL_SG_FCAP);
         rc |= dalloc(&d.sg_info, nsg);
     }

@@ -252,7 +252,8 @@ __device__ __forceinline__ float evol_wrap(float d, float len, int periodic)
     return periodic ? d - len * rintf(d / len) : d;
 }
 
-// ---- force-walk super-groups: list capacities per super-group --------------------------------
+// ---- force-walk super-groups: groups of 32 list entries per super-group, list capacities -----
+#define EVOL_SG_GROUPS 8
 #define EVOL_SG_ACAP 3072
 #define EVOL_SG_FCAP 768
 

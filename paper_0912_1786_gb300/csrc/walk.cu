@@ -35,7 +35,7 @@ constexpr int WK_THREADS = 128;
 constexpr int WK_WARPS = WK_THREADS / 32;
 constexpr int FARCAP = 64;
 constexpr int NEARCAP = 64;
-constexpr int SG_GROUPS = 8;      // groups per super-group (see k_super)
+constexpr int SG_GROUPS = EVOL_SG_GROUPS;   // groups per super-group (see k_super)
 
 constexpr float TAU = 1e-5f;      // safety margin of the group-level bounds
 
@@ -908,8 +908,8 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
             }
             __syncwarp();
             // mixed nodes: every lane in the mask applies its own test
-            unsigned mm = __ballot_sync(0xffffffffu, cls == 3);
-            if (lane == 0) {
+            unsigned mm = pre ? 0u : __ballot_sync(0xffffffffu, cls == 3);
+            if (lane == 0 && !pre) {
                 wc[3] += (unsigned)k;
                 wc[4] += (unsigned)__popc(mm);
             }
@@ -967,6 +967,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
                 }
                 nfar += cnt;
             }
+            if (pre) continue;               // nothing opened
             // opened leaves: their particles go to the near list
             const bool isleaf = (I.x >> 8) & 1;
             unsigned lm = __ballot_sync(0xffffffffu, Ok != 0u && isleaf);
@@ -1015,7 +1016,6 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
                 }
             }
             // opened internal nodes: push their children with the open mask
-            if (pre) continue;               // nothing opened
             const bool io = Ok != 0u && !isleaf;
             int nch = 0;
             int ch[8];
