@@ -272,10 +272,11 @@ struct CheckSmem<false> {
 
 // Register budgets, chosen so that no variant spills to local memory: the plain gravity + SPH walk
 // (the production form) and the plain SPH-only walk fit five blocks per SM (at most 102
-// registers), the mixed walks and the walks with the dissipation variants (DISS) four (128
-// registers), the gravity-only, periodic and mixed DISS walks three; the check-mode variants one.
+// registers), the mixed walks, the walks with the dissipation variants (DISS) and the plain
+// gravity-only periodic (EWALD) walk four (128 registers), the other gravity-only, periodic and
+// mixed DISS walks three; the check-mode variants one.
 template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS, bool EWALD>
-__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SPH) || (MIXED && DISS)) ? 3 : (MIXED || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIXED) ? 4 : (EWALD || (GRAV && !SPH) || (MIXED && DISS)) ? 3 : (MIXED || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
     __shared__ DissSmem<DISS> ds;
@@ -792,7 +793,9 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD || (GRAV && !SP
         // nodes accepted for all by the super-group, taken 32 at a time before the stack: [apos, aend)
         const int *alist = d.sg_acc;
         int apos = 0, aend = 0;
-        const int2 sgi = kp.super ? d.sg_info[g / SG_GROUPS] : make_int2(-1, -1);
+        // (not in the periodic gravity walk, which opens every node above L/8 and keeps its registers
+        // for the Ewald lookups)
+        const int2 sgi = (!EWALD && kp.super) ? d.sg_info[g / SG_GROUPS] : make_int2(-1, -1);
         if (sgi.x >= 0 && sgi.y <= kp.stack_cap) {
             // the super-group's lists (k_super), with the mask of every active lane: its frontier on
             // the stack, the nodes it accepted for all as batches that skip the node tests (they
@@ -1350,7 +1353,7 @@ void launch_walk_pce(evol_ctx *c, const evol_kparams &kp, bool mixed, bool check
 {
     // the super-groups' top-of-tree walk first (one warp per block, 16 blocks per SM)
     const int nsg = (kp.n + 32 * SG_GROUPS - 1) / (32 * SG_GROUPS);
-    if (kp.super && nsg > 0) k_super<GRAV, SPH, EWALD><<<c->num_sms * 16, 32, 0, c->stream>>>(c->d, kp, nsg);
+    if (!EWALD && kp.super && nsg > 0) k_super<GRAV, SPH, EWALD><<<c->num_sms * 16, 32, 0, c->stream>>>(c->d, kp, nsg);
     if constexpr (SPH) {
         if (kp.diss) {
             launch_walk_pcd<GRAV, SPH, true, EWALD>(c, kp, mixed, check);
