@@ -640,7 +640,12 @@ def main():
     elif not args.no_autotune and w.sys_offsets is None:
         best, ms = E.evol_autotune(ctx, ds.particles, ds.params, ds.outputs, candidates=[12, 16, 24, 32, 48], reps=3)
         ds.params.leaf_size = best
-        autotune = {"leaf_size": best, "median_ms_by_leaf": ms}
+        # then the length solves' group size at that leaf size
+        bg, msg = E.evol_autotune_length_group(ctx, ds.particles, ds.params, ds.outputs, candidates=[8, 16, 32],
+                                               reps=3)
+        ds.params.length_group = bg
+        autotune = {"leaf_size": best, "median_ms_by_leaf": ms, "length_group": bg,
+                    "median_ms_by_length_group": msg}
 
     offsets = [int(v) for v in w.sys_offsets] if w.sys_offsets is not None else None
 
@@ -824,8 +829,9 @@ def main():
                 "precision": args.precision, "data": "synthetic",
                 "config": {"workload": wname, "n": w.n, "n_gas": w.n_gas, "theta": w.params.theta,
                            "n_nei": w.params.n_nei_sph, "leaf_size": int(ds.params.leaf_size),
+                           "length_group": int(ds.params.length_group) or 8,
                            "kdk_steps_per_bench_step": args.kdk_steps or None,
-                "autotune": autotune,
+                           "autotune": autotune,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "working set > L2 (inputs 40 B/particle x 3.1M + tree), no flush"},
                 "phase_ms": {"build": ph[0], "eps_solve": ph[1], "h_solve": ph[2], "walk": ph[3], "total": ph[4]},

@@ -137,6 +137,9 @@ typedef struct {
     float alpha_u_min;         /* paper: 0 */
     int sph_scheme;            /* EVOL_SPH_LAGRANGIAN (0) or EVOL_SPH_STANDARD; the standard scheme
                                   needs 1 <= n_nei_sph (rounded) <= 335 */
+    int length_group;          /* particles per group walk of the length solves (they share one
+                                  tree walk listing the leaves near them): 0 = 8, or 1..32.
+                                  Changes cost, not the definition. */
 } evol_params;
 
 /* Outputs, caller order.  Any pointer may be NULL (not written). */
@@ -287,6 +290,12 @@ int evol_step_host(evol_ctx *ctx, evol_particles *p_host, const evol_params *prm
  * values again; out receives the last run's results.  Synchronous. */
 int evol_autotune(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outputs *out,
                   const int *candidates, int ncand, int reps, int *best_leaf, float *ms_out);
+
+/* The same autotuner for the length solves' group size (prm->length_group), at the parameters
+ * given (leaf size included): candidates in 1..32 (NULL: {4, 8, 16, 32}); *best receives the fastest,
+ * ms_out (may be NULL) each candidate's median step time.  Same timing protocol as evol_autotune. */
+int evol_autotune_length_group(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outputs *out,
+                               const int *candidates, int ncand, int reps, int *best, float *ms_out);
 
 /* Wait for the context stream and return the first device-side error recorded since the
  * previous evol_sync (then clear it), or EVOL_OK. */

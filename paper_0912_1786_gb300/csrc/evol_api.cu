@@ -95,6 +95,7 @@ int check_args(evol_ctx *c, const evol_particles *p, const evol_params *prm)
     if (prm->balsara && !(prm->balsara_eta >= 0.f)) return EVOL_EINVAL;
     if ((prm->variable_alpha || prm->conduction) && !(prm->alpha_tau > 0.f)) return EVOL_EINVAL;
     if (prm->sph_scheme != EVOL_SPH_LAGRANGIAN && prm->sph_scheme != EVOL_SPH_STANDARD) return EVOL_EINVAL;
+    if (prm->length_group < 0 || prm->length_group > 32) return EVOL_EINVAL;
     if (prm->sph && prm->sph_scheme == EVOL_SPH_STANDARD) {
         const long nstd = lrintf(prm->n_nei_sph);
         if (nstd < 1 || nstd + 1 > evol_lengths_list_cap()) return EVOL_EINVAL;
@@ -177,6 +178,79 @@ int record_phase(evol_ctx *c, int k, evol_particles *p, const evol_params *prm, 
         break;
     }
     }
+    return rc;
+}
+
+}  // namespace
+
+namespace {
+// Times evol_step for each candidate value of one cost parameter (set(q, v) writes it into a copy
+// of the parameters) and returns the fastest; see evol_autotune for the protocol.
+template <typename Set>
+int tune_param(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out, const int *candidates,
+               int ncand, int reps, int *best_out, float *ms_out, Set set)
+{
+    int rc = EVOL_OK;
+    if (p->n == 0) {
+        *best_out = candidates[0];
+        return EVOL_OK;
+    }
+    // Every timed step starts from the caller's starting lengths, as a step of the caller's run
+    // does: they are kept in the host-step staging buffer and restored before each step (outside
+    // the timed interval).
+    const int64_t n = p->n, ng = p->n_gas;
+    float *save_h = c->stage, *save_e = c->stage + c->cap;
+    auto restore = [&]() {
+        if (p->h && ng > 0) cudaMemcpyAsync(p->h, save_h, ng * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+        if (p->eps) cudaMemcpyAsync(p->eps, save_e, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    };
+    if (p->h && ng > 0) cudaMemcpyAsync(save_h, p->h, ng * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    if (p->eps) cudaMemcpyAsync(save_e, p->eps, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return EVOL_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return EVOL_ECUDA;
+    }
+    float best = 3.0e38f;
+    int best_k = 0;
+    std::vector<float> t(reps);
+    // one untimed step first, so that the first candidate does not pay the clocks' ramp-up
+    {
+        evol_params q = *prm;
+        set(q, candidates[0]);
+        restore();
+        rc = evol_step(c, p, &q, out);
+        if (!rc) rc = evol_sync(c);
+    }
+    for (int k = 0; k < ncand && !rc; ++k) {
+        evol_params q = *prm;
+        set(q, candidates[k]);
+        restore();
+        if ((rc = evol_step(c, p, &q, out))) break;           // records the graphs for this leaf size
+        if ((rc = evol_sync(c))) break;
+        for (int r = 0; r < reps && !rc; ++r) {
+            restore();
+            cudaEventRecord(e0, c->stream);
+            rc = evol_step(c, p, &q, out);
+            cudaEventRecord(e1, c->stream);
+            if (!rc) rc = evol_sync(c);
+            if (!rc && cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess) rc = EVOL_ECUDA;
+        }
+        if (rc) break;
+        std::vector<float> srt(t);
+        std::sort(srt.begin(), srt.end());
+        const float med = (reps & 1) ? srt[reps / 2] : 0.5f * (srt[reps / 2 - 1] + srt[reps / 2]);
+        if (ms_out) ms_out[k] = med;
+        if (med < best) {
+            best = med;
+            best_k = k;
+        }
+    }
+    restore();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) *best_out = candidates[best_k];
     return rc;
 }
 
@@ -886,67 +960,25 @@ int evol_autotune(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_o
     }
     for (int k = 0; k < ncand; ++k)
         if (candidates[k] < 1 || candidates[k] > 64) return EVOL_EINVAL;
-    if (p->n == 0) {
-        *best_leaf = candidates[0];
-        return EVOL_OK;
+    return tune_param(c, p, prm, out, candidates, ncand, reps, best_leaf, ms_out,
+                      [](evol_params &q, int v) { q.leaf_size = v; });
+}
+
+int evol_autotune_length_group(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out,
+                               const int *candidates, int ncand, int reps, int *best, float *ms_out)
+{
+    static const int defaults[4] = {4, 8, 16, 32};
+    int rc = check_args(c, p, prm);
+    if (rc) return rc;
+    if (!best || reps < 1 || (candidates && ncand < 1)) return EVOL_EINVAL;
+    if (!candidates) {
+        candidates = defaults;
+        ncand = 4;
     }
-    // Every timed step starts from the caller's starting lengths, as a step of the caller's run
-    // does: they are kept in the host-step staging buffer and restored before each step (outside
-    // the timed interval).
-    const int64_t n = p->n, ng = p->n_gas;
-    float *save_h = c->stage, *save_e = c->stage + c->cap;
-    auto restore = [&]() {
-        if (p->h && ng > 0) cudaMemcpyAsync(p->h, save_h, ng * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
-        if (p->eps) cudaMemcpyAsync(p->eps, save_e, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
-    };
-    if (p->h && ng > 0) cudaMemcpyAsync(save_h, p->h, ng * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
-    if (p->eps) cudaMemcpyAsync(save_e, p->eps, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return EVOL_ECUDA;
-    if (cudaEventCreate(&e1) != cudaSuccess) {
-        cudaEventDestroy(e0);
-        return EVOL_ECUDA;
-    }
-    float best = 3.0e38f;
-    int best_k = 0;
-    std::vector<float> t(reps);
-    // one untimed step first, so that the first candidate does not pay the clocks' ramp-up
-    {
-        evol_params q = *prm;
-        q.leaf_size = candidates[0];
-        restore();
-        rc = evol_step(c, p, &q, out);
-        if (!rc) rc = evol_sync(c);
-    }
-    for (int k = 0; k < ncand && !rc; ++k) {
-        evol_params q = *prm;
-        q.leaf_size = candidates[k];
-        restore();
-        if ((rc = evol_step(c, p, &q, out))) break;           // records the graphs for this leaf size
-        if ((rc = evol_sync(c))) break;
-        for (int r = 0; r < reps && !rc; ++r) {
-            restore();
-            cudaEventRecord(e0, c->stream);
-            rc = evol_step(c, p, &q, out);
-            cudaEventRecord(e1, c->stream);
-            if (!rc) rc = evol_sync(c);
-            if (!rc && cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess) rc = EVOL_ECUDA;
-        }
-        if (rc) break;
-        std::vector<float> srt(t);
-        std::sort(srt.begin(), srt.end());
-        const float med = (reps & 1) ? srt[reps / 2] : 0.5f * (srt[reps / 2 - 1] + srt[reps / 2]);
-        if (ms_out) ms_out[k] = med;
-        if (med < best) {
-            best = med;
-            best_k = k;
-        }
-    }
-    restore();
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (!rc) *best_leaf = candidates[best_k];
-    return rc;
+    for (int k = 0; k < ncand; ++k)
+        if (candidates[k] < 1 || candidates[k] > 32) return EVOL_EINVAL;
+    return tune_param(c, p, prm, out, candidates, ncand, reps, best, ms_out,
+                      [](evol_params &q, int v) { q.length_group = v; });
 }
 
 int evol_sync(evol_ctx *c)

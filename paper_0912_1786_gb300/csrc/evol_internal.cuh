@@ -281,6 +281,7 @@ struct evol_kparams {
     // neighbour, the smallest step (ticks) of an active particle next to it (wake-up)
     int active, wake;
     int super;               // the force walk's groups start from their super-group's lists
+    int lsub;                // particles per group walk of the length solves (1..32)
     // periodic gravity (Ewald): cube side, 2 N / L for the table lookup, the table (L = 1)
     int ewald;
     float ewald_L, ewald_sc;

@@ -2,10 +2,11 @@
 // densitySPH, drhodr; Sect. 3.1 "gather" view with an enlarged search radius).
 //
 // Each particle i needs the particles within its search radius R_i = 2 L_i (1 + 0.1).  A warp
-// takes 8 consecutive particles in key order and solves them one after the other, all 32 lanes
-// on one particle.  For the 8 particles the warp first walks the tree once, popping up to 32
-// nodes at a time and opening those whose particle box comes within R_g = max R_i of the 8
-// particles' bounding box; the leaves reached are listed in shared memory.
+// takes SUB consecutive particles in key order (evol_params.length_group, 8 by default) and
+// solves them one after the other, all 32 lanes on one particle.  For the SUB particles the warp
+// first walks the tree once, popping up to 32 nodes at a time and opening those whose particle box
+// comes within R_g = max R_i of the particles' bounding box; the leaves reached are listed in
+// shared memory (where they do not fit, the walk is repeated for halves of the particles).
 // A particle then tests the listed leaves against its own ball, and the particles of the leaves
 // that pass, 32 at a time across leaves.  A particle whose radius grows beyond R_g, or whose
 // group list overflowed, walks the tree on its own (same walk, from the particle's root).  The
@@ -38,7 +39,7 @@ constexpr int LW_THREADS = 128;
 constexpr int LW_WARPS = LW_THREADS / 32;
 constexpr int HCAP = 96;              // leaves listed per pass of a particle's gather
 constexpr int PCAP = 336;             // neighbour entries of the particle being solved
-constexpr int SUB = 8;                // particles sharing one group walk
+constexpr int SUB_DEFAULT = 8;        // particles sharing one group walk (evol_params.length_group = 0)
 constexpr int GCAP = 192;             // leaves in a group walk's list
 constexpr int MAX_ITERS = 60;
 constexpr int MAX_WALKS = 24;
@@ -413,7 +414,8 @@ __global__ void __launch_bounds__(LW_THREADS, CURL ? 4 : 5) k_lengths(evol_dev d
     int *stk = reinterpret_cast<int *>(d.wstack + (size_t)wslot * kp.stack_stride);
     const int stack_cap = 2 * kp.stack_cap;
     const int n = kp.n;
-    // individual time steps: items of SUB consecutive entries of the active list
+    // items of SUB consecutive entries of the particle list (individual time steps: the active list)
+    const int SUB = kp.lsub;
     const int nlist = ACT ? d.acts[n] : n;
     const int ngroups = (nlist + SUB - 1) / SUB;   // the queue hands out SUB particles at a time
     const float eta = MODE == 0 ? kp.eta_h : kp.eta_e;
@@ -781,6 +783,7 @@ int evol_launch_lengths(evol_ctx *c, const evol_particles *p, const evol_params 
     kp.standard = mode == 0 && prm->sph_scheme == EVOL_SPH_STANDARD;
     kp.nstd = (int)lrintf(prm->n_nei_sph);
     kp.want_divv = c->want_divv || kp.want_curl;
+    kp.lsub = prm->length_group > 0 ? prm->length_group : SUB_DEFAULT;
     kp.stack_cap = (int)c->wstack_lim;
     kp.stack_stride = (int)c->wstack_cap;
     unsigned long long *q = c->d.counters + (mode == 0 ? 5 : 6);

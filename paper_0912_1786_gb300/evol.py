@@ -45,7 +45,8 @@ class EvolParams(C.Structure):
                 ("visc_form", C.c_int), ("balsara", C.c_int), ("balsara_eta", C.c_float),
                 ("variable_alpha", C.c_int), ("alpha_min", C.c_float), ("alpha_tau", C.c_float),
                 ("alpha_source", C.c_float), ("conduction", C.c_int), ("cond_vsig", C.c_int),
-                ("cond_source", C.c_int), ("alpha_u_min", C.c_float), ("sph_scheme", C.c_int)]
+                ("cond_source", C.c_int), ("alpha_u_min", C.c_float), ("sph_scheme", C.c_int),
+                ("length_group", C.c_int)]
 
 
 class EvolIntegrator(C.Structure):
@@ -85,8 +86,9 @@ def lib():
             getattr(L, name).argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs)]
         L.evol_step_batched.argtypes = [vp, C.POINTER(C.c_int64), C.c_int, pp(EvolParticles), pp(EvolParams),
                                          pp(EvolOutputs)]
-        L.evol_autotune.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs), C.POINTER(C.c_int),
-                                     C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
+        for name in ("evol_autotune", "evol_autotune_length_group"):
+            getattr(L, name).argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs), C.POINTER(C.c_int),
+                                         C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
         L.evol_kdk.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs), C.c_float, C.c_int]
         L.evol_run.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolIntegrator), pp(EvolOutputs), C.c_int,
                                pp(C.c_double), pp(C.c_float)]
@@ -147,7 +149,7 @@ def make_params(p) -> EvolParams:
     e.group_size = int(getattr(p, "group_size", 32))
     # dissipation variants (defaults: the paper's constants, every variant off)
     for k, d in (("visc_form", 0), ("balsara", 0), ("variable_alpha", 0), ("conduction", 0), ("cond_vsig", 0),
-                 ("cond_source", 0), ("sph_scheme", 0)):
+                 ("cond_source", 0), ("sph_scheme", 0), ("length_group", 0)):
         setattr(e, k, int(getattr(p, k, d)))
     for k, d in (("balsara_eta", 1e-4), ("alpha_min", 0.01), ("alpha_tau", 0.1), ("alpha_source", 0.75),
                  ("alpha_u_min", 0.0)):
@@ -228,6 +230,17 @@ def evol_autotune(ctx, particles, params, outputs, candidates=None, reps=3):
     best = C.c_int()
     _check(lib().evol_autotune(ctx, C.byref(particles), C.byref(params), C.byref(outputs), carr, len(cand),
                                int(reps), C.byref(best), ms), "evol_autotune")
+    return best.value, dict(zip(cand, list(ms)))
+
+
+def evol_autotune_length_group(ctx, particles, params, outputs, candidates=None, reps=3):
+    """Fastest group size of the length solves at these parameters; returns (best, {size: median ms})."""
+    cand = list(candidates) if candidates is not None else [4, 8, 16, 32]
+    carr = (C.c_int * len(cand))(*cand)
+    ms = (C.c_float * len(cand))()
+    best = C.c_int()
+    _check(lib().evol_autotune_length_group(ctx, C.byref(particles), C.byref(params), C.byref(outputs), carr,
+                                            len(cand), int(reps), C.byref(best), ms), "evol_autotune_length_group")
     return best.value, dict(zip(cand, list(ms)))
 
 

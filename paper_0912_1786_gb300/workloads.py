@@ -47,6 +47,7 @@ class Params:
     group_size: int = 32
     use_tc_gradient: int = 1
     sph_scheme: int = 0            # 0: n-h (Lagrangian) scheme; 1: standard scheme, N_nei inside 2h
+    length_group: int = 0          # particles per group walk of the length solves (0: 8)
     # dissipation variants (Sect. 3.3.3); all off is the standard Monaghan viscosity
     visc_form: int = 0             # 0: Monaghan alpha/beta form; 1: signal-velocity form
     balsara: int = 0               # 1: Balsara limiter on the viscosity

@@ -30,3 +30,38 @@ def test_autotune_returns_candidate_and_parity_holds():
     g = run_gpu(w, p, check=False)
     o = oracle.force_step(w, params=p)
     assert_tol("acc", acc(g), np.stack([o["ax"], o["ay"], o["az"]], 1), scale=o["aabs"])
+
+
+def test_length_group_autotune_returns_candidate_and_rejects_bad_sizes():
+    import torch
+    from paper_0912_1786_gb300 import build, evol as E
+    from paper_0912_1786_gb300.device import DeviceSet
+    build.build()
+    w = W.hernquist_gas(n_dm=1 << 14, n_gas=1 << 13, seed=3, params=W.Params(theta=0.5, leaf_size=16))
+    ds = DeviceSet(w)
+    ctx = E.evol_create(w.n, torch.cuda.current_stream().cuda_stream)
+    try:
+        best, ms = E.evol_autotune_length_group(ctx, ds.particles, ds.params, ds.outputs, candidates=[4, 8, 16],
+                                                reps=2)
+        ds.params.length_group = 33
+        with pytest.raises(E.EvolError) as ei:
+            E.evol_step(ctx, ds.particles, ds.params, ds.outputs)
+        assert ei.value.code == E.EVOL_EINVAL
+    finally:
+        E.evol_destroy(ctx)
+    assert best in (4, 8, 16)
+    assert all(v > 0 for v in ms.values())
+
+
+@pytest.mark.parametrize("lg", [1, 4, 16, 32])
+def test_length_group_changes_cost_not_results(lg):
+    # every group size gives the oracle's lengths, densities and forces
+    w = W.hernquist_gas(n_dm=1 << 13, n_gas=1 << 12, seed=8, params=W.Params(theta=0.5, leaf_size=16, length_group=lg))
+    o = oracle.force_step(w)
+    g = run_gpu(w, check=False)
+    assert g["status"] == 0
+    ng = w.n_gas
+    assert_tol("h", g["h"], o["h"][:ng])
+    assert_tol("rho", g["rho"], o["rho"][:ng])
+    assert_tol("eps", g["eps"], o["eps"])
+    assert_tol("acc", acc(g), np.stack([o["ax"], o["ay"], o["az"]], 1), scale=o["aabs"])
