@@ -68,8 +68,9 @@ extern "C" {
 
 /* ---- precision forms -------------------------------------------------------------- */
 #define EVOL_FP32_PLAIN  0   /* FP32 moments and FP32 accumulation of per-particle sums */
-#define EVOL_FP32_MIXED  1   /* FP64 multipole/centre-of-mass accumulation and FP64 totals of
-                                blocked FP32 partial sums; the walk arithmetic stays FP32 */
+#define EVOL_FP32_MIXED  1   /* FP64 multipole/centre-of-mass accumulation; the gravity totals
+                                compensated (TwoSum of blocked FP32 partial sums, read out in
+                                FP64); the walk arithmetic stays FP32 */
 
 typedef struct evol_ctx evol_ctx;   /* opaque; owns every device scratch buffer */
 

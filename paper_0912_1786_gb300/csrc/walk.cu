@@ -57,7 +57,6 @@ struct WalkSmem {
     float4 ng[WK_WARPS][NEARCAP];
     float4 nh[WK_WARPS][NEARCAP];
     float4 ns[WK_WARPS][NEARCAP];
-    int norig[WK_WARPS][NEARCAP];
     float4 gbox[WK_WARPS][3];     // group bounds: centre, 0 | half widths, 0 | emax, emin, hmax, hmin
     unsigned wc[WK_WARPS][8];     // per-group work counts kept by lane 0 (see the end of k_walk)
     float mum[WK_WARPS][32];      // largest |mu_ij| of each lane's particle (viscosity)
@@ -220,31 +219,23 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = (a - ap) + (b - bp);
 }
 
-// Mixed form: the per-particle totals over the flush blocks are compensated sums -- each block
-// sum is added with TwoSum and its rounding error kept in a separate compensation term -- so the
+// Mixed form: the gravity totals (acceleration and potential, sums over thousands of far nodes and
+// near particles) are compensated sums.  Each flush block's sum is added to the running FP32 total
+// with TwoSum and the rounding error of that addition kept in a separate compensation term, so the
 // totals carry the blocks' own FP32 rounding only (a few ulps of at most 64 terms), not that of
-// thousands of successive additions.
+// thousands of successive additions.  The hydro sums (about N_nei pair terms, one or two flushes)
+// gain nothing from compensation at this granularity and are summed as in the plain form.  The
+// running totals are the plain form's registers (parked in shared memory while the pair loop sums
+// a block in them); the compensation terms sit in shared memory (one per lane and component), which
+// keeps the mixed walk at the plain walk's register count and residency.
 template <bool MIXED>
-struct Totals {
-    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    __device__ __forceinline__ void add(const Acc &a)
-    {
-        const float v[8] = {a.ax, a.ay, a.az, a.pot, a.hx, a.hy, a.hz, a.du};
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            float t, e;
-            two_sum(s[k], v[k], t, e);
-            s[k] = t;
-            c[k] += e;
-        }
-    }
-    __device__ __forceinline__ double get(int k) const { return (double)s[k] + (double)c[k]; }
+struct MixSmem {
+    // [0, 4): compensation terms of ax, ay, az, pot; [4, 8): the running totals, parked here while
+    // the pair loop sums its flush block in their registers
+    float c[WK_WARPS][8][32];
 };
 template <>
-struct Totals<false> {
-    __device__ __forceinline__ void add(const Acc &) {}
-    __device__ __forceinline__ double get(int) const { return 0.0; }
+struct MixSmem<false> {
 };
 
 // Dissipation operands staged per near entry (alpha, Balsara f, u, alpha^u of the neighbour) and
@@ -265,22 +256,24 @@ template <bool CHECK>
 struct CheckSmem {
     int cs[WK_WARPS][32];
     unsigned long long hs[WK_WARPS][32];
+    int norig[WK_WARPS][NEARCAP];                 // original index of each near entry
 };
 template <>
 struct CheckSmem<false> {
 };
 
-// Register budgets, chosen so that no variant spills to local memory: the plain gravity + SPH walk
-// (the production form) and the plain SPH-only walk fit five blocks per SM (at most 102
-// registers), the mixed walks, the walks with the dissipation variants (DISS) and the plain
-// gravity-only periodic (EWALD) walk four (128 registers), the other gravity-only, periodic and
-// mixed DISS walks three; the check-mode variants one.
+// Register budgets, chosen so that no variant spills to local memory: the gravity + SPH walk (the
+// production form, plain or mixed) and the SPH-only walk fit five blocks per SM (at most 102
+// registers), the walks with the dissipation variants (DISS) and the plain gravity-only periodic
+// (EWALD) walk four (128 registers), the other gravity-only, periodic and mixed DISS walks three;
+// the check-mode variants one.
 template <bool GRAV, bool SPH, bool MIXED, bool CHECK, bool DISS, bool EWALD>
-__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIXED) ? 4 : (EWALD || (GRAV && !SPH) || (MIXED && DISS)) ? 3 : (MIXED || DISS) ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
+__global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIXED) ? 4 : (EWALD || (GRAV && !SPH) || (MIXED && DISS)) ? 3 : DISS ? 4 : EVOL_WALK_MINB) k_walk(evol_dev d, evol_kparams kp, unsigned long long *queue)
 {
     __shared__ WalkSmem sm;
     __shared__ DissSmem<DISS> ds;
     __shared__ CheckSmem<CHECK> cks;
+    __shared__ MixSmem<MIXED> mx;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int n = kp.n;
@@ -320,7 +313,6 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
         const float H_i = gas_i ? two_h_i * two_h_i : -1.f;
 
         Acc acc;
-        Totals<MIXED> tot;
         unsigned long long hfar = 0, hnear = 0;
         int cfar = 0, cpp = 0;
         // interaction counts of this lane (one group's counts fit 32 bits)
@@ -339,12 +331,22 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
             cks.cs[w][lane] = 0;
             cks.hs[w][lane] = 0ull;
         }
+        if constexpr (MIXED) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) mx.c[w][k][lane] = 0.f;
+        }
         __syncwarp();
 
-        auto fold = [&]() {
-            if (MIXED) {
-                tot.add(acc);
-                acc = Acc();
+        // adds a block sum b to gravity component k of this lane's total (compensated in the mixed
+        // form)
+        auto add_to = [&](float &total, int k, float b) {
+            if constexpr (MIXED) {
+                float t, e;
+                two_sum(total, b, t, e);
+                total = t;
+                mx.c[w][k][lane] += e;
+            } else {
+                total += b;
             }
         };
 
@@ -427,18 +429,17 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                     fpot = fma2(v1.y, rinv, fma2(mul2(dqd, KM05), r5, fpot));
                 }
             }
-            acc.ax += lo2(fax) + hi2(fax);
-            acc.ay += lo2(fay) + hi2(fay);
-            acc.az += lo2(faz) + hi2(faz);
-            acc.pot += lo2(fpot) + hi2(fpot);
+            add_to(acc.ax, 0, lo2(fax) + hi2(fax));
+            add_to(acc.ay, 1, lo2(fay) + hi2(fay));
+            add_to(acc.az, 2, lo2(faz) + hi2(faz));
+            add_to(acc.pot, 3, lo2(fpot) + hi2(fpot));
             if constexpr (EWALD) {
                 // the table is for a cube of side 1: f scales as 1/L^2, g as 1/L
-                acc.ax += lo2(ewxy) * iL * iL;
-                acc.ay += hi2(ewxy) * iL * iL;
-                acc.az += lo2(ewzw) * iL * iL;
-                acc.pot += hi2(ewzw) * iL;
+                add_to(acc.ax, 0, lo2(ewxy) * iL * iL);
+                add_to(acc.ay, 1, hi2(ewxy) * iL * iL);
+                add_to(acc.az, 2, lo2(ewzw) * iL * iL);
+                add_to(acc.pot, 3, hi2(ewzw) * iL);
             }
-            fold();
             nfar = 0;
             __syncwarp();
         };
@@ -468,9 +469,17 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                     sm.ns[w][l] = d.snd[j];
                 }
                 if constexpr (DISS) ds.nd[w][l] = d.diss[j];     // read only for gas pairs
-                if (CHECK) sm.norig[w][l] = d.orig[j];
+                if constexpr (CHECK) cks.norig[w][l] = d.orig[j];
             }
             if (lane == 0) wc[1] += 32u * (unsigned)((nnear + 1) & ~1);
+            if constexpr (MIXED && GRAV) {
+                // park the running gravity totals; the pair loop sums this flush's block from zero
+                mx.c[w][4][lane] = acc.ax;
+                mx.c[w][5][lane] = acc.ay;
+                mx.c[w][6][lane] = acc.az;
+                mx.c[w][7][lane] = acc.pot;
+                acc.ax = acc.ay = acc.az = acc.pot = 0.f;
+            }
             __syncwarp();
             // Pass 1, every entry, two at a time in packed form.  A gravity pair farther apart than
             // 2 max(eps_i, eps_j) is Newtonian: both softened kernels equal their point-mass forms
@@ -635,7 +644,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                             ++wsph;
                             if constexpr (CHECK) {
                                 atomicAdd(&cks.cs[w][o], 1);
-                                atomicAdd(&cks.hs[w][o], evol_mix64((unsigned long long)sm.norig[w][t]));
+                                atomicAdd(&cks.hs[w][o], evol_mix64((unsigned long long)cks.norig[w][t]));
                             }
                             if (kp.wake) {
                                 // wake-up: the owner's step (ticks), recorded at its SPH neighbour
@@ -752,7 +761,21 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                     }
                 }
             }
-            fold();
+            if constexpr (MIXED && GRAV) {
+                // the block's sums into the parked totals, compensated
+                float b = acc.ax;
+                acc.ax = mx.c[w][4][lane];
+                add_to(acc.ax, 0, b);
+                b = acc.ay;
+                acc.ay = mx.c[w][5][lane];
+                add_to(acc.ay, 1, b);
+                b = acc.az;
+                acc.az = mx.c[w][6][lane];
+                add_to(acc.az, 2, b);
+                b = acc.pot;
+                acc.pot = mx.c[w][7][lane];
+                add_to(acc.pot, 3, b);
+            }
             nnear = 0;
             __syncwarp();
         };
@@ -1052,13 +1075,12 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
         if (GRAV && nfar) flush_far();
         if (nnear) flush_near();
 
-        double tax, tay, taz, tpot, thx, thy, thz, tdu;
-        if (MIXED) {
-            tax = tot.get(0); tay = tot.get(1); taz = tot.get(2); tpot = tot.get(3);
-            thx = tot.get(4); thy = tot.get(5); thz = tot.get(6); tdu = tot.get(7);
-        } else {
-            tax = acc.ax; tay = acc.ay; taz = acc.az; tpot = acc.pot;
-            thx = acc.hx; thy = acc.hy; thz = acc.hz; tdu = acc.du;
+        double tax = acc.ax, tay = acc.ay, taz = acc.az, tpot = acc.pot;
+        double thx = acc.hx, thy = acc.hy, thz = acc.hz, tdu = acc.du;
+        if constexpr (MIXED) {
+            // total = running sum + compensation, in FP64
+            tax += (double)mx.c[w][0][lane]; tay += (double)mx.c[w][1][lane];
+            taz += (double)mx.c[w][2][lane]; tpot += (double)mx.c[w][3][lane];
         }
         if (valid) {
             float ax = 0.f, ay = 0.f, az = 0.f, pot = 0.f;

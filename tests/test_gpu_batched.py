@@ -70,6 +70,50 @@ def test_batched_systems_match_oracle_per_system():
     assert nodes_seen == g["nodes"]["begin"].size
 
 
+@pytest.mark.slow
+def test_batched_fullsize_ensemble_sampled():
+    # the 64-sphere ensemble of the batched benchmark (N_k from 2^10 to 2^17, 1.76 M particles):
+    # every system's keys and nodes bit-exact, and a seeded sample of each system's particles
+    # against the oracle run on that system alone (all its lengths solved, forces on the sample)
+    w = W.ensemble(64, seed=5)
+    w.vx[:] = np.random.default_rng(7).normal(0, 0.1, w.n).astype(np.float32)
+    offs = [int(v) for v in w.sys_offsets]
+    assert max(np.diff(offs)) > 1 << 16
+    g = _run_batched(w, offs)
+    assert g["status"] == 0
+    nodes_seen = 0
+    cols = {k: ([], []) for k in ("acc", "rho", "h", "eps", "dudt")}
+    scales = {"acc": [], "dudt": []}
+    for k in range(len(offs) - 1):
+        b, e = offs[k], offs[k + 1]
+        ws = _sub(w, b, e)
+        idx = W.sample_indices(e - b, 48, seed=100 + k)
+        o = oracle.force_step(ws, idx=idx)
+        t = o["tree"]
+        assert np.array_equal(g["perm"][b:e] - b, t.perm())
+        assert np.array_equal(g["keys"][b:e], t.keys()[t.perm()])
+        on = t.nodes()
+        sl = slice(nodes_seen, nodes_seen + t.nnodes)
+        for key in ("begin", "end"):
+            assert np.array_equal(g["nodes"][key][sl] - b, on[key]), (k, key)
+        assert np.array_equal(g["nodes"]["level"][sl], on["level"])
+        assert np.array_equal(g["nodes"]["nchild"][sl], on["nchild"])
+        assert np.array_equal(g["nodes"]["next"][sl] - nodes_seen, on["next"])
+        nodes_seen += t.nnodes
+        gi = b + idx
+        cols["acc"][0].append(acc(g)[gi])
+        cols["acc"][1].append(np.stack([o["ax"], o["ay"], o["az"]], 1)[idx])
+        scales["acc"].append(o["aabs"][idx])
+        for q in ("rho", "h", "eps", "dudt"):
+            cols[q][0].append(g[q][gi])
+            cols[q][1].append(o[q][idx])
+        scales["dudt"].append(o["duabs"][idx])
+    assert nodes_seen == g["nodes"]["begin"].size
+    for q, (gv, ov) in cols.items():
+        sc = np.concatenate(scales[q]) if q in scales else None
+        assert_tol(q, np.concatenate(gv), np.concatenate(ov), scale=sc)
+
+
 def test_batch_of_one_equals_step():
     from gpu_common import run_gpu
     w = W.evrard_sphere(3000, seed=22, sigma_v=0.1)

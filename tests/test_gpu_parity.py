@@ -136,6 +136,22 @@ def test_c1_mixed_precision():
     _compare(w, precision=1)
 
 
+def test_mixed_form_closer_to_oracle_than_plain():
+    # the mixed form's FP64 moments and compensated gravity totals must show: on a halo whose
+    # particles sum about a thousand far nodes each, its median acceleration and potential errors
+    # are below the plain form's
+    w = W.hernquist_gas(n_dm=1 << 15, n_gas=1 << 14, seed=3)
+    o = oracle.force_step(w)
+    a_ref = np.stack([o["ax"], o["ay"], o["az"]], 1)
+    med = {}
+    for prec in (0, 1):
+        g = run_gpu(w, check=False, precision=prec)
+        assert g["status"] == 0
+        med[prec] = (rel_stats(acc(g), a_ref)[0], rel_stats(g["pot"], o["pot"])[0])
+    report({"quantity": "acc_pot_median_plain_vs_mixed", "plain": med[0], "mixed": med[1]})
+    assert med[1][0] < med[0][0] and med[1][1] < med[0][1]
+
+
 def test_c2_plummer_gravity_only():
     for th in (0.4, 0.8):
         w = W.plummer(1 << 15, seed=2, params=W.Params(theta=th, sph=0, n_nei_grav=32.0, leaf_size=8))
