@@ -61,7 +61,7 @@ HBM_PEAK_GBS = _hbm_peak()
 # DRAM bytes per launch of the production walk (dram__bytes_read.sum + dram__bytes_write.sum of a
 # one-pass ncu capture of the full-size workload at that leaf size); other workloads and leaf sizes
 # report null
-WALK_TRAFFIC = {("c3", 16): 499.2e6 + 100.6e6, ("c3", 24): 455.0e6 + 95.5e6, ("c3", 32): 432.2e6 + 93.0e6}
+WALK_TRAFFIC = {("c3", 16): 497.4e6 + 100.6e6, ("c3", 24): 453.7e6 + 94.8e6, ("c3", 32): 434.8e6 + 93.4e6}
 
 
 def log(*a):
@@ -368,7 +368,7 @@ def time_steps(torch, dev, stream, fn, steps):
     return t0.elapsed_time(t1)
 
 
-def other_forms(torch, dev, stream, E, DeviceSet, w, steps, precision_used, leaf):
+def other_forms(torch, dev, stream, E, DeviceSet, w, steps, precision_used, leaf, group=0):
     """Throughput of the other precision form (same workload) and, for an ensemble, of one
     launch per system; particles/s each.  Also returns each form's results (caller order, with
     interaction-set hashes for the precision form) for the accuracy comparison."""
@@ -376,6 +376,7 @@ def other_forms(torch, dev, stream, E, DeviceSet, w, steps, precision_used, leaf
     other = E.EVOL_FP32_MIXED if precision_used == E.EVOL_FP32_PLAIN else E.EVOL_FP32_PLAIN
     ds = DeviceSet(w, device=str(dev), precision=other)
     ds.params.leaf_size = leaf
+    ds.params.length_group = group
     ctx = E.evol_create(w.n, stream.cuda_stream)
     try:
         if w.sys_offsets is not None:
@@ -398,6 +399,7 @@ def other_forms(torch, dev, stream, E, DeviceSet, w, steps, precision_used, leaf
         from paper_0912_1786_gb300 import evol as E2
         ds = DeviceSet(w, device=str(dev), precision=precision_used)
         ds.params.leaf_size = leaf
+        ds.params.length_group = group
         offs = [int(v) for v in w.sys_offsets]
         ctxs, parts = [], []
         try:
@@ -635,9 +637,10 @@ def main():
     stream = torch.cuda.current_stream(dev)
     ctx = E.evol_create(w.n, stream.cuda_stream)
     autotune = None
+    offsets = [int(v) for v in w.sys_offsets] if w.sys_offsets is not None else None
     if args.leaf > 0:
         ds.params.leaf_size = args.leaf
-    elif not args.no_autotune and w.sys_offsets is None:
+    elif not args.no_autotune and offsets is None:
         best, ms = E.evol_autotune(ctx, ds.particles, ds.params, ds.outputs, candidates=[12, 16, 24, 32, 48], reps=3)
         ds.params.leaf_size = best
         # then the length solves' group size at that leaf size
@@ -646,8 +649,16 @@ def main():
         ds.params.length_group = bg
         autotune = {"leaf_size": best, "median_ms_by_leaf": ms, "length_group": bg,
                     "median_ms_by_length_group": msg}
-
-    offsets = [int(v) for v in w.sys_offsets] if w.sys_offsets is not None else None
+    elif not args.no_autotune:
+        # the batched step: the same two tuners, timing the batched step over all systems
+        best, ms = E.evol_autotune_batched(ctx, offsets, ds.particles, ds.params, ds.outputs,
+                                           which=E.EVOL_TUNE_LEAF_SIZE, candidates=[8, 12, 16, 24], reps=3)
+        ds.params.leaf_size = best
+        bg, msg = E.evol_autotune_batched(ctx, offsets, ds.particles, ds.params, ds.outputs,
+                                          which=E.EVOL_TUNE_LENGTH_GROUP, candidates=[8, 16, 32], reps=3)
+        ds.params.length_group = bg
+        autotune = {"leaf_size": best, "median_ms_by_leaf": ms, "length_group": bg,
+                    "median_ms_by_length_group": msg}
 
     kdk_initial = {k: t.clone() for k, t in ds.inp.items()} if args.kdk_steps > 0 else None
 
@@ -759,7 +770,7 @@ def main():
     if not args.no_forms:
         g_main = gpu_check_step(E, ctx, ds, offsets)
         rates, results = other_forms(torch, dev, stream, E, DeviceSet, w, max(2, min(args.steps, 5)), prec,
-                                     int(ds.params.leaf_size))
+                                     int(ds.params.leaf_size), int(ds.params.length_group))
         forms.update(rates)
         results[main_form] = g_main
         accuracy = {}

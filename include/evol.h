@@ -298,6 +298,18 @@ int evol_autotune(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol
 int evol_autotune_length_group(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_outputs *out,
                                const int *candidates, int ncand, int reps, int *best, float *ms_out);
 
+/* The autotuners for a batch of independent systems: the same protocol, timing
+ * evol_step_batched with these offsets (same rules as evol_step_batched; a bad offset array
+ * returns its EVOL_EINVAL from the first step).  which = EVOL_TUNE_LEAF_SIZE (candidates in 1..64,
+ * NULL: {4, 8, 12, 16, 24, 32}) or EVOL_TUNE_LENGTH_GROUP (candidates in 1..32, NULL:
+ * {4, 8, 16, 32}); any other value is EVOL_EINVAL.  *best receives the fastest candidate, ms_out
+ * (may be NULL) each candidate's median step time.  Synchronous. */
+#define EVOL_TUNE_LEAF_SIZE    0
+#define EVOL_TUNE_LENGTH_GROUP 1
+int evol_autotune_batched(evol_ctx *ctx, const int64_t *sys_offsets, int nsys, evol_particles *p,
+                          const evol_params *prm, evol_outputs *out, int which, const int *candidates, int ncand,
+                          int reps, int *best, float *ms_out);
+
 /* Wait for the context stream and return the first device-side error recorded since the
  * previous evol_sync (then clear it), or EVOL_OK. */
 int evol_sync(evol_ctx *ctx);

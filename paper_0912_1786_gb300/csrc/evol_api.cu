@@ -184,11 +184,12 @@ int record_phase(evol_ctx *c, int k, evol_particles *p, const evol_params *prm, 
 }  // namespace
 
 namespace {
-// Times evol_step for each candidate value of one cost parameter (set(q, v) writes it into a copy
-// of the parameters) and returns the fastest; see evol_autotune for the protocol.
-template <typename Set>
-int tune_param(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out, const int *candidates,
-               int ncand, int reps, int *best_out, float *ms_out, Set set)
+// Times the step (step(q) runs one: evol_step or evol_step_batched) for each candidate value of one
+// cost parameter (set(q, v) writes it into a copy of the parameters) and returns the fastest; see
+// evol_autotune for the protocol.
+template <typename Set, typename Step>
+int tune_param(evol_ctx *c, evol_particles *p, const evol_params *prm, const int *candidates, int ncand, int reps,
+               int *best_out, float *ms_out, Set set, Step step)
 {
     int rc = EVOL_OK;
     if (p->n == 0) {
@@ -220,19 +221,19 @@ int tune_param(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outp
         evol_params q = *prm;
         set(q, candidates[0]);
         restore();
-        rc = evol_step(c, p, &q, out);
+        rc = step(q);
         if (!rc) rc = evol_sync(c);
     }
     for (int k = 0; k < ncand && !rc; ++k) {
         evol_params q = *prm;
         set(q, candidates[k]);
         restore();
-        if ((rc = evol_step(c, p, &q, out))) break;           // records the graphs for this leaf size
+        if ((rc = step(q))) break;                           // records the graphs for this value
         if ((rc = evol_sync(c))) break;
         for (int r = 0; r < reps && !rc; ++r) {
             restore();
             cudaEventRecord(e0, c->stream);
-            rc = evol_step(c, p, &q, out);
+            rc = step(q);
             cudaEventRecord(e1, c->stream);
             if (!rc) rc = evol_sync(c);
             if (!rc && cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess) rc = EVOL_ECUDA;
@@ -960,8 +961,9 @@ int evol_autotune(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_o
     }
     for (int k = 0; k < ncand; ++k)
         if (candidates[k] < 1 || candidates[k] > 64) return EVOL_EINVAL;
-    return tune_param(c, p, prm, out, candidates, ncand, reps, best_leaf, ms_out,
-                      [](evol_params &q, int v) { q.leaf_size = v; });
+    return tune_param(c, p, prm, candidates, ncand, reps, best_leaf, ms_out,
+                      [](evol_params &q, int v) { q.leaf_size = v; },
+                      [&](const evol_params &q) { return evol_step(c, p, &q, out); });
 }
 
 int evol_autotune_length_group(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outputs *out,
@@ -977,8 +979,34 @@ int evol_autotune_length_group(evol_ctx *c, evol_particles *p, const evol_params
     }
     for (int k = 0; k < ncand; ++k)
         if (candidates[k] < 1 || candidates[k] > 32) return EVOL_EINVAL;
-    return tune_param(c, p, prm, out, candidates, ncand, reps, best, ms_out,
-                      [](evol_params &q, int v) { q.length_group = v; });
+    return tune_param(c, p, prm, candidates, ncand, reps, best, ms_out,
+                      [](evol_params &q, int v) { q.length_group = v; },
+                      [&](const evol_params &q) { return evol_step(c, p, &q, out); });
+}
+
+int evol_autotune_batched(evol_ctx *c, const int64_t *sys_offsets, int nsys, evol_particles *p,
+                          const evol_params *prm, evol_outputs *out, int which, const int *candidates, int ncand,
+                          int reps, int *best, float *ms_out)
+{
+    static const int leaf_defaults[6] = {4, 8, 12, 16, 24, 32};
+    static const int group_defaults[4] = {4, 8, 16, 32};
+    int rc = check_args(c, p, prm);
+    if (rc) return rc;
+    if (!sys_offsets || !best || reps < 1 || (candidates && ncand < 1)) return EVOL_EINVAL;
+    if (which != EVOL_TUNE_LEAF_SIZE && which != EVOL_TUNE_LENGTH_GROUP) return EVOL_EINVAL;
+    const bool leaf = which == EVOL_TUNE_LEAF_SIZE;
+    if (!candidates) {
+        candidates = leaf ? leaf_defaults : group_defaults;
+        ncand = leaf ? 6 : 4;
+    }
+    for (int k = 0; k < ncand; ++k)
+        if (candidates[k] < 1 || candidates[k] > (leaf ? 64 : 32)) return EVOL_EINVAL;
+    auto step = [&](const evol_params &q) { return evol_step_batched(c, sys_offsets, nsys, p, &q, out); };
+    if (leaf)
+        return tune_param(c, p, prm, candidates, ncand, reps, best, ms_out,
+                          [](evol_params &q, int v) { q.leaf_size = v; }, step);
+    return tune_param(c, p, prm, candidates, ncand, reps, best, ms_out,
+                      [](evol_params &q, int v) { q.length_group = v; }, step);
 }
 
 int evol_sync(evol_ctx *c)

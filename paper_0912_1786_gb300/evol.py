@@ -23,6 +23,7 @@ EVOL_VISC_MONAGHAN, EVOL_VISC_SIGNAL = 0, 1
 EVOL_COND_VSIG_SOUND, EVOL_COND_VSIG_PRESSURE = 0, 1
 EVOL_COND_SRC_SQRTU, EVOL_COND_SRC_LINEAR = 0, 1
 EVOL_SPH_LAGRANGIAN, EVOL_SPH_STANDARD = 0, 1
+EVOL_TUNE_LEAF_SIZE, EVOL_TUNE_LENGTH_GROUP = 0, 1
 
 _fp = C.POINTER(C.c_float)
 
@@ -89,6 +90,9 @@ def lib():
         for name in ("evol_autotune", "evol_autotune_length_group"):
             getattr(L, name).argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs), C.POINTER(C.c_int),
                                          C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
+        L.evol_autotune_batched.argtypes = [vp, C.POINTER(C.c_int64), C.c_int, pp(EvolParticles), pp(EvolParams),
+                                            pp(EvolOutputs), C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
+                                            C.POINTER(C.c_int), C.POINTER(C.c_float)]
         L.evol_kdk.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolOutputs), C.c_float, C.c_int]
         L.evol_run.argtypes = [vp, pp(EvolParticles), pp(EvolParams), pp(EvolIntegrator), pp(EvolOutputs), C.c_int,
                                pp(C.c_double), pp(C.c_float)]
@@ -241,6 +245,23 @@ def evol_autotune_length_group(ctx, particles, params, outputs, candidates=None,
     best = C.c_int()
     _check(lib().evol_autotune_length_group(ctx, C.byref(particles), C.byref(params), C.byref(outputs), carr,
                                             len(cand), int(reps), C.byref(best), ms), "evol_autotune_length_group")
+    return best.value, dict(zip(cand, list(ms)))
+
+
+def evol_autotune_batched(ctx, sys_offsets, particles, params, outputs, which=EVOL_TUNE_LEAF_SIZE, candidates=None,
+                          reps=3):
+    """Fastest leaf size (which = EVOL_TUNE_LEAF_SIZE) or length-solve group size
+    (EVOL_TUNE_LENGTH_GROUP) for a batched step over these systems; returns (best, {value: median ms})."""
+    if candidates is None:
+        candidates = [4, 8, 12, 16, 24, 32] if which == EVOL_TUNE_LEAF_SIZE else [4, 8, 16, 32]
+    cand = list(candidates)
+    offs = (C.c_int64 * len(sys_offsets))(*[int(v) for v in sys_offsets])
+    carr = (C.c_int * len(cand))(*cand)
+    ms = (C.c_float * len(cand))()
+    best = C.c_int()
+    _check(lib().evol_autotune_batched(ctx, offs, len(sys_offsets) - 1, C.byref(particles), C.byref(params),
+                                       C.byref(outputs), int(which), carr, len(cand), int(reps), C.byref(best), ms),
+           "evol_autotune_batched")
     return best.value, dict(zip(cand, list(ms)))
 
 

@@ -75,7 +75,9 @@ def test_batched_fullsize_ensemble_sampled():
     # the 64-sphere ensemble of the batched benchmark (N_k from 2^10 to 2^17, 1.76 M particles):
     # every system's keys and nodes bit-exact, and a seeded sample of each system's particles
     # against the oracle run on that system alone (all its lengths solved, forces on the sample)
-    w = W.ensemble(64, seed=5)
+    # at the leaf and length-solve group sizes the batched autotuner picks for it on GB300
+    p = W.Params(theta=0.5, n_nei_sph=50.0, n_nei_grav=50.0, leaf_size=16, length_group=16)
+    w = W.ensemble(64, seed=5, params=p)
     w.vx[:] = np.random.default_rng(7).normal(0, 0.1, w.n).astype(np.float32)
     offs = [int(v) for v in w.sys_offsets]
     assert max(np.diff(offs)) > 1 << 16
