@@ -36,7 +36,7 @@ import numpy as np  # noqa: E402
 # particle pair (r >= 2 max(eps_i, eps_j): point-mass force and potential); softened particle pair
 # (both softened kernels, potential, adaptive-softening correction); SPH pair (pressure with the
 # grad-h factors, Monaghan viscosity, du/dt).
-FLOPS_FAR = 54
+FLOPS_FAR = 53
 FLOPS_PP_NEWTON = 19
 FLOPS_PP_SOFT = 89
 FLOPS_SPH = 85
@@ -61,7 +61,7 @@ HBM_PEAK_GBS = _hbm_peak()
 # DRAM bytes per launch of the production walk (dram__bytes_read.sum + dram__bytes_write.sum of a
 # one-pass ncu capture of the full-size workload at that leaf size); other workloads and leaf sizes
 # report null
-WALK_TRAFFIC = {("c3", 16): 497.4e6 + 100.6e6, ("c3", 24): 453.7e6 + 94.8e6, ("c3", 32): 434.8e6 + 93.4e6}
+WALK_TRAFFIC = {("c3", 16): 497.0e6 + 100.1e6, ("c3", 24): 451.9e6 + 95.1e6, ("c3", 32): 434.1e6 + 93.0e6}
 
 
 def log(*a):

@@ -421,12 +421,13 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
                     const f32x2 qy = fma2(v4.y, dz, fma2(v2.y, dy, mul2(v3.y, dx)));
                     const f32x2 qz = fma2(v3.x, dz, fma2(v4.y, dy, mul2(v4.x, dx)));
                     const f32x2 dqd = fma2(dz, qz, fma2(dy, qy, mul2(dx, qx)));
+                    const f32x2 t5 = mul2(dqd, r5);                      // (d.Q.d)/d^5
                     // c1 = -M/d^3 - 5/2 (d.Q.d)/d^7
-                    const f32x2 c1 = fma2(mul2(dqd, mul2(rinv2, KM25)), r5, mul2(v1.y, r3));
+                    const f32x2 c1 = fma2(mul2(t5, rinv2), KM25, mul2(v1.y, r3));
                     fax = fma2(c1, dx, fma2(r5, qx, fax));
                     fay = fma2(c1, dy, fma2(r5, qy, fay));
                     faz = fma2(c1, dz, fma2(r5, qz, faz));
-                    fpot = fma2(v1.y, rinv, fma2(mul2(dqd, KM05), r5, fpot));
+                    fpot = fma2(v1.y, rinv, fma2(t5, KM05, fpot));
                 }
             }
             add_to(acc.ax, 0, lo2(fax) + hi2(fax));
