@@ -40,7 +40,7 @@ constexpr int LW_WARPS = LW_THREADS / 32;
 constexpr int HCAP = 96;              // leaves listed per pass of a particle's gather
 constexpr int PCAP = 336;             // neighbour entries of the particle being solved
 constexpr int SUB_DEFAULT = 8;        // particles sharing one group walk (evol_params.length_group = 0)
-constexpr int GCAP = 192;             // leaves in a group walk's list
+constexpr int GCAP = 240;             // leaves in a group walk's list
 constexpr int MAX_ITERS = 60;
 constexpr int MAX_WALKS = 24;
 constexpr float SEARCH_MARGIN = 1.1f;
@@ -53,9 +53,8 @@ constexpr float CONV_TOL = 1e-6f;
 enum { ST_DONE = 0, ST_ACTIVE = 1, ST_LAST = 2 };
 
 struct LenSmem {
-    float4 gc[LW_WARPS][GCAP];        // group list: leaf box centre (w unused)
-    float4 gh[LW_WARPS][GCAP];        // leaf box half widths
-    int2 gr[LW_WARPS][GCAP];          // leaf particle range [begin, end)
+    float4 gc[LW_WARPS][GCAP];        // group list: leaf box centre; w: first particle (int bits)
+    float4 gh[LW_WARPS][GCAP];        // leaf box half widths; w: end of its particle range (int bits)
     int hb[LW_WARPS][HCAP + 1];       // listed leaves: exclusive prefix of their particle counts
     int hs[LW_WARPS][HCAP];           // and the first particle of each
     float2 nb[LW_WARPS][PCAP];        // (distance, index bits) of the neighbours of the particle solved
@@ -253,7 +252,7 @@ __device__ int gather_ball(const evol_dev &d, const evol_kparams &kp, int *hb, i
 // leaves go to the group list; returns their number, GCAP + 1 when they do not fit, or -1 when
 // the walk had to stop (corrupt tree or stack overflow; the error word is set).
 template <int MODE, bool PER>
-__device__ int collect_leaves(const evol_dev &d, const evol_kparams &kp, float4 *gc, float4 *gh, int2 *gr, int lane,
+__device__ int collect_leaves(const evol_dev &d, const evol_kparams &kp, float4 *gc, float4 *gh, int lane,
                               int *stk, int stack_cap, long long pop_cap, float cx, float cy, float cz, float hx,
                               float hy, float hz, float R2, int myroot, bool seed)
 {
@@ -302,9 +301,8 @@ __device__ int collect_leaves(const evol_dev &d, const evol_kparams &kp, float4 
         if (open && leaf) {
             const int e = count + __popc(lv & ltmask);
             if (e < GCAP) {
-                gc[e] = B;
-                gh[e] = C;
-                gr[e] = make_int2(I.z, I.w);
+                gc[e] = make_float4(B.x, B.y, B.z, __int_as_float(I.z));
+                gh[e] = make_float4(C.x, C.y, C.z, __int_as_float(I.w));
             }
         }
         count += __popc(lv);
@@ -347,7 +345,7 @@ __device__ int collect_leaves(const evol_dev &d, const evol_kparams &kp, float4 
 // inside [sbeg, send)) whose box comes within sqrt(R2) of (px, py, pz), then their particles.
 template <int MODE, bool PER>
 __device__ int gather_from_list(const evol_dev &d, const evol_kparams &kp, const float4 *gc, const float4 *gh,
-                                const int2 *gr, int nleaf, int *hb, int *hs, float2 *nb, int lane, float px, float py,
+                                int nleaf, int *hb, int *hs, float2 *nb, int lane, float px, float py,
                                 float pz, float R2, int sbeg, int send)
 {
     const unsigned ltmask = (1u << lane) - 1u;
@@ -359,8 +357,8 @@ __device__ int gather_from_list(const evol_dev &d, const evol_kparams &kp, const
         bool hit = false;
         int2 r = make_int2(0, 0);
         if (l < nleaf) {
-            r = gr[l];
             const float4 B = gc[l], C = gh[l];
+            r = make_int2(__float_as_int(B.w), __float_as_int(C.w));
             const float ex = fmaxf(fabsf(evol_wrap(B.x - px, p0, pm & 1)) - C.x, 0.f);
             const float ey = fmaxf(fabsf(evol_wrap(B.y - py, p1, pm & 2)) - C.y, 0.f);
             const float ez = fmaxf(fabsf(evol_wrap(B.z - pz, p2, pm & 4)) - C.z, 0.f);
@@ -475,7 +473,7 @@ __global__ void __launch_bounds__(LW_THREADS, CURL ? 4 : 5) k_lengths(evol_dev d
               gz1 = fmaxf(gz1, __shfl_xor_sync(0xffffffffu, gz1, o));
               Rg = fmaxf(Rg, __shfl_xor_sync(0xffffffffu, Rg, o));
           }
-          const int nleaf = collect_leaves<MODE, PER>(d, kp, sm.gc[w], sm.gh[w], sm.gr[w], lane, stk, stack_cap, pop_cap,
+          const int nleaf = collect_leaves<MODE, PER>(d, kp, sm.gc[w], sm.gh[w], lane, stk, stack_cap, pop_cap,
                                                  0.5f * (gx0 + gx1), 0.5f * (gy0 + gy1), 0.5f * (gz0 + gz1),
                                                  0.5f * (gx1 - gx0), 0.5f * (gy1 - gy0), 0.5f * (gz1 - gz0), Rg * Rg,
                                                  root, insub);
@@ -543,7 +541,7 @@ __global__ void __launch_bounds__(LW_THREADS, CURL ? 4 : 5) k_lengths(evol_dev d
                     __syncwarp();
                     if (glist && Rc <= Rg) {
                         if (lane == 0) ++lc[0];
-                        cnt = gather_from_list<MODE, PER>(d, kp, sm.gc[w], sm.gh[w], sm.gr[w], nleaf, sm.hb[w], sm.hs[w], nb,
+                        cnt = gather_from_list<MODE, PER>(d, kp, sm.gc[w], sm.gh[w], nleaf, sm.hb[w], sm.hs[w], nb,
                                                      lane, px, py, pz, R2, sb, se);
                     } else {
                         if (lane == 0) ++lc[1];
