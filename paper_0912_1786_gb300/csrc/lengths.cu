@@ -57,7 +57,8 @@ struct LenSmem {
     float4 gh[LW_WARPS][GCAP];        // leaf box half widths; w: end of its particle range (int bits)
     int hb[LW_WARPS][HCAP + 1];       // listed leaves: exclusive prefix of their particle counts
     int hs[LW_WARPS][HCAP];           // and the first particle of each
-    float2 nb[LW_WARPS][PCAP];        // (distance, index bits) of the neighbours of the particle solved
+    float2 nb[LW_WARPS][PCAP];        // neighbours of the particle solved: (distance, index bits), or
+                                      // (distance, mass) when no velocity divergence is wanted
     unsigned lc[LW_WARPS][4];         // work counts of the warp's current item (kept by lane 0)
 };
 
@@ -78,8 +79,9 @@ __device__ __forceinline__ float kth_distance(const float2 *nb, int cnt, int k, 
 }
 
 // Particles of the listed leaves against the particle at (px, py, pz), 32 at a time across
-// leaves: those within R2 (gas only in mode 0) are appended to the neighbour list.  Returns the
-// new count (entries beyond PCAP are counted but not stored).
+// leaves: those within R2 (gas only in mode 0) are appended to the neighbour list with their
+// index (their mass when no velocity divergence is wanted, which spares the last evaluation its
+// reads).  Returns the new count (entries beyond PCAP are counted but not stored).
 template <int MODE, bool PER>
 __device__ __forceinline__ int gather_listed(const evol_dev &d, const evol_kparams &kp, const int *hb, const int *hs,
                                              int nh, float2 *nb, int cnt, float px, float py, float pz, float R2,
@@ -129,7 +131,7 @@ __device__ __forceinline__ int gather_listed(const evol_dev &d, const evol_kpara
             const unsigned bal = __ballot_sync(0xffffffffu, in);
             if (in) {
                 const int e = cnt + __popc(bal & ltmask);
-                if (e < PCAP) nb[e] = make_float2(sqrtf(r2), __int_as_float(jj[h]));
+                if (e < PCAP) nb[e] = make_float2(sqrtf(r2), kp.want_divv ? __int_as_float(jj[h]) : pj[h].w);
             }
             cnt += __popc(bal);
         }
@@ -605,14 +607,14 @@ __global__ void __launch_bounds__(LW_THREADS, CURL ? 4 : 5) k_lengths(evol_dev d
                         Suw += u * (-0.75f * a2 + 3.f * b2);                // u w'(u)
                     }
                 } else {
-                    // the neighbours' masses (and, for the continuity equation, positions and
-                    // velocities) are read from the sorted particle state
+                    // the neighbours' masses are in the list, or (for the continuity equation) read
+                    // with their positions and velocities from the sorted particle state
                     const int st = ACT ? __shfl_sync(0xffffffffu, s, t) : g * SUB + t;
                     const float4 vi = kp.want_divv ? d.vel[st] : make_float4(0.f, 0.f, 0.f, 0.f);
                     for (int e = lane; e < cnt; e += 32) {
                         const float2 rj = nb[e];
-                        const int j = __float_as_int(rj.y);
-                        const float4 pj = d.pos[j];
+                        const int j = kp.want_divv ? __float_as_int(rj.y) : 0;
+                        const float4 pj = kp.want_divv ? d.pos[j] : make_float4(0.f, 0.f, 0.f, rj.y);
                         const float u = rj.x * Linv;
                         float wv, dw;
                         evol_w_dw(u, wv, dw);      // zero for u >= 2
