@@ -1163,7 +1163,7 @@ __global__ void __launch_bounds__(WK_THREADS, CHECK ? 1 : (EWALD && !SPH && !MIX
 // particles of more than one system, or whose lists do not fit, is marked, and its groups walk
 // from the root.
 template <bool GRAV, bool SPH, bool EWALD>
-__global__ void __launch_bounds__(32, 16) k_super(evol_dev d, evol_kparams kp, int nsg)
+__global__ void __launch_bounds__(32, 24) k_super(evol_dev d, evol_kparams kp, int nsg)
 {
     const int lane = threadIdx.x;
     const int n = kp.n;
@@ -1376,7 +1376,7 @@ void launch_walk_pce(evol_ctx *c, const evol_kparams &kp, bool mixed, bool check
 {
     // the super-groups' top-of-tree walk first (one warp per block, 16 blocks per SM)
     const int nsg = (kp.n + 32 * SG_GROUPS - 1) / (32 * SG_GROUPS);
-    if (!EWALD && kp.super && nsg > 0) k_super<GRAV, SPH, EWALD><<<c->num_sms * 16, 32, 0, c->stream>>>(c->d, kp, nsg);
+    if (!EWALD && kp.super && nsg > 0) k_super<GRAV, SPH, EWALD><<<c->num_sms * 24, 32, 0, c->stream>>>(c->d, kp, nsg);
     if constexpr (SPH) {
         if (kp.diss) {
             launch_walk_pcd<GRAV, SPH, true, EWALD>(c, kp, mixed, check);
