@@ -196,7 +196,9 @@ int evol_step(evol_ctx *ctx, evol_particles *p, const evol_params *prm, evol_out
  * gas still means the first n_gas particles overall).  Each system gets its own root cube and
  * tree, exactly as evol_step would build for it alone; all systems go through the same kernel
  * launches (one per phase, CUDA-graph captured per nsys).  1 <= nsys <= 65536, else EVOL_EINVAL.
- * Synchronises the context stream on entry (the offsets are staged in pinned host memory). */
+ * Synchronises the context stream on entry when the offsets differ from those of the previous
+ * step on this context (they are staged in pinned host memory); repeated steps of one batch do
+ * not synchronise. */
 int evol_step_batched(evol_ctx *ctx, const int64_t *sys_offsets, int nsys, evol_particles *p,
                       const evol_params *prm, evol_outputs *out);
 

@@ -128,6 +128,7 @@ int ensure_tree(evol_ctx *c, const evol_particles *p, const evol_params *prm)
     if (c->built_n == p->n && c->built_ngas == p->n_gas && c->built_x == (const void *)p->x && c->nsys == 1)
         return EVOL_OK;
     c->nsys = 1;
+    c->staged_nsys = 0;
     int rc = evol_launch_build(c, p, prm);
     if (rc) return rc;
     c->built_n = p->n;
@@ -532,6 +533,7 @@ int evol_step(evol_ctx *c, evol_particles *p, const evol_params *prm, evol_outpu
     int rc = check_args(c, p, prm);
     if (rc || p->n == 0) return rc;
     c->nsys = 1;
+    c->staged_nsys = 0;
     return run_step(c, p, prm, out);
 }
 
@@ -546,12 +548,22 @@ int evol_step_batched(evol_ctx *c, const int64_t *sys_offsets, int nsys, evol_pa
     for (int k = 0; k < nsys; ++k)
         if (sys_offsets[k + 1] < sys_offsets[k]) return EVOL_EINVAL;
     if (p->n == 0) return EVOL_OK;
-    // the previous call's copy may still be in flight from the pinned staging buffer
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return set_err(c, EVOL_ECUDA);
-    for (int k = 0; k <= nsys; ++k) c->h_sys_off[k] = (int32_t)sys_offsets[k];
-    if (cudaMemcpyAsync(c->d.sys_off, c->h_sys_off, (nsys + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
-                        c->stream) != cudaSuccess)
-        return set_err(c, EVOL_ECUDA);
+    // offsets already on the device from the previous step on this context, itself a step of this
+    // batch (every single-system entry point sets nsys = 1 before its kernels rewrite the offsets),
+    // are not staged again, so that repeated steps of one batch need no host synchronisation
+    bool staged = c->staged_nsys == nsys && c->nsys == nsys;
+    for (int k = 0; staged && k <= nsys; ++k) staged = c->h_sys_off[k] == (int32_t)sys_offsets[k];
+    if (!staged) {
+        // the previous call's copy may still be in flight from the pinned staging buffer
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return set_err(c, EVOL_ECUDA);
+        for (int k = 0; k <= nsys; ++k) c->h_sys_off[k] = (int32_t)sys_offsets[k];
+        if (cudaMemcpyAsync(c->d.sys_off, c->h_sys_off, (nsys + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            c->stream) != cudaSuccess) {
+            c->staged_nsys = 0;
+            return set_err(c, EVOL_ECUDA);
+        }
+        c->staged_nsys = nsys;
+    }
     c->nsys = nsys;
     return run_step(c, p, prm, out);
 }

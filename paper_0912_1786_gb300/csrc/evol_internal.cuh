@@ -123,6 +123,7 @@ struct evol_ctx {
     int64_t built_n, built_ngas;
     int nsys;                // systems of the current particle set (1 unless batched)
     int nsys_cap;
+    int staged_nsys;         // systems whose offsets d.sys_off holds from h_sys_off (0: none)
     int32_t *h_sys_off;      // pinned host staging of the system offsets
     const void *built_x;
     int density_done, eps_done;

@@ -39,14 +39,14 @@ class DeviceSet:
             self.out[k] = torch.zeros(max(ln, 1), dtype=torch.float32, device=self.device)
         self.particles = E.make_particles(self.n, self.n_gas, self.inp)
         self.outputs = E.make_outputs(self.out)
+        # the starting guesses of h and eps, kept on the device: restoring them before a step is a
+        # device copy, which needs no host synchronisation between steps
+        self._start = {k: self.inp[k].clone() for k in ("h", "eps")}
 
     def reset_lengths(self):
         """Restore the caller's starting guesses for h and eps (the step overwrites them)."""
         for k in ("h", "eps"):
-            a = np.ascontiguousarray(getattr(self.w, k), np.float32)
-            if k == "h":
-                a = a[: max(self.n_gas, 1)]
-            self.inp[k].copy_(torch.from_numpy(a))
+            self.inp[k].copy_(self._start[k])
 
     def numpy(self) -> dict:
         res = {k: v.detach().cpu().numpy().astype(np.float64)[: (self.n_gas if k in OUT_LEN_GAS else self.n)]

@@ -140,3 +140,38 @@ def test_batched_rejects_bad_offsets():
             assert ei.value.code == E.EVOL_EINVAL
     finally:
         E.evol_destroy(ctx)
+
+
+def test_batched_offsets_restaged_after_other_steps():
+    # repeated steps of one batch skip staging their offsets; a single-system step or a batch with
+    # other offsets in between must not leave stale offsets behind
+    import torch
+    from paper_0912_1786_gb300 import build, evol as E
+    from paper_0912_1786_gb300.device import DeviceSet
+    build.build()
+    w = W.ensemble(5, seed=12, log2_min=8.0, log2_max=10.0)
+    offs = [int(v) for v in w.sys_offsets]
+    merged = [offs[0]] + offs[2:]                 # systems 0 and 1 as one
+    ds = DeviceSet(w)
+    ctx = E.evol_create(w.n, torch.cuda.current_stream().cuda_stream)
+    keys = ("ax", "ay", "az", "pot", "rho", "h", "eps")
+    try:
+        def batched(o):
+            ds.reset_lengths()
+            E.evol_step_batched(ctx, o, ds.particles, ds.params, ds.outputs)
+            assert E.evol_sync(ctx, raise_on_error=False) == 0
+            return ds.numpy()
+        g1 = batched(offs)
+        g2 = batched(offs)                        # offsets not staged again
+        ds.reset_lengths()
+        E.evol_step(ctx, ds.particles, ds.params, ds.outputs)
+        assert E.evol_sync(ctx, raise_on_error=False) == 0
+        g3 = batched(offs)                        # after a single-system step
+        gm = batched(merged)
+        g4 = batched(offs)                        # after a batch with other offsets
+    finally:
+        E.evol_destroy(ctx)
+    for g in (g2, g3, g4):
+        for k in keys:
+            assert np.array_equal(g[k], g1[k]), k
+    assert not np.array_equal(gm["ax"], g1["ax"])
